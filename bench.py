@@ -1,0 +1,338 @@
+#!/usr/bin/env python
+"""Benchmark of the in-memory aggregation hot path on GB300.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME] [--impl ours|reference]
+
+Prints ONE JSON line (rank 0). A step is one aggregation call over one batch of
+synthetic input already resident in HBM; `value` is input GB/s over all ranks
+(max-over-ranks time), `e2e` the same metric through the host-fed entry point
+with the host-to-device copy inside the timed region.
+
+Workloads (synthetic, seeded; they stand in for the paper's TPC-H
+lineitem.suppkey scan, which is not available here):
+  scan        ungrouped SUM/MIN/MAX/COUNT/AVG over a 2^30-row int32 column
+              (4 GiB, uniform in [-2^20, 2^20))
+
+Under torchrun each rank aggregates its own replica of the workload (weak
+scaling, no data-path collective); only the timing uses a MAX all-reduce.
+`--impl reference` times the CPU oracle (single thread) on a bounded sample of
+the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Input GB/s & % of GB300 HBM peak; batched+learned vs plain per-query kernels"
+UNIT = "GB/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": FALLBACK_HBM_GBS, "source": "fallback"}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks_", suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except FileNotFoundError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        self.proc.terminate()
+        self.proc.wait()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# Distributed plumbing (one process per GPU; weak scaling)
+# ---------------------------------------------------------------------------
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if backend == "nccl":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# Workloads
+# ---------------------------------------------------------------------------
+class ScanWorkload:
+    """Ungrouped SUM/MIN/MAX/COUNT/AVG over a 2^30-row int32 column (4 GiB)."""
+    name = "scan"
+    n = 1 << 30
+    dtype = "i32"
+    esize = 4
+    kernel = "reduce_scan"
+
+    def config(self):
+        return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30-row int32 column uniform in [-2^20, 2^20)",
+                "rows": self.n, "dtype": "int32", "input_bytes": self.n * self.esize,
+                "l2": "input (4 GiB) larger than L2 (129 MB); no flush needed"}
+
+    def bytes_per_step(self):
+        return self.n * self.esize
+
+    def setup(self, rank):
+        import torch
+
+        import paper_2606_10030_gb300 as agg
+        from datagen import cuda as dgc
+        self.agg = agg
+        self.col = dgc.values(self.dtype, self.n, seed=rank)
+        self.out = torch.empty(agg.SCALAR_BYTES, dtype=torch.uint8, device="cuda")
+        torch.cuda.synchronize()
+
+    def step(self):
+        self.agg.agg_reduce(self.col, self.agg.AGG_ALL, out=self.out)
+        return 1  # kernel launches
+
+    def setup_e2e(self):
+        self.host = self.col.cpu().pin_memory()
+
+    def step_e2e(self):
+        r = self.agg.agg_reduce_host(self.host, self.agg.AGG_ALL)
+        return r.count
+
+    def e2e_bytes(self):
+        return self.n * self.esize, 80
+
+    def cpu_sample(self, budget_s: float):
+        """Oracle on consecutive 2^24-row slices of the same column until budget_s elapses."""
+        import numpy as np
+
+        import datagen as dg
+        import oracle
+        oracle.build()
+        rows = 0
+        t0 = time.perf_counter()
+        chunk = 1 << 24
+        start = 0
+        t_compute = 0.0
+        while time.perf_counter() - t0 < budget_s and start < self.n:
+            x = dg.values(self.dtype, chunk, seed=0, start=start)
+            a = time.perf_counter()
+            oracle.reduce(x)
+            t_compute += time.perf_counter() - a
+            rows += chunk
+            start += chunk
+        return rows, t_compute, f"oracle.reduce over the first {rows} rows (2^24-row slices) of the column"
+
+
+WORKLOADS = {"scan": ScanWorkload}
+
+
+def kernel_traffic(kernel: str, workload: str):
+    """DRAM bytes per launch from a committed ncu summary, if it matches the current kernel source."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p)).get(f"{kernel}:{workload}")
+    except Exception:
+        return None
+    if not d:
+        return None
+    import hashlib
+    src = os.path.join(ROOT, d["source"])
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != d["source_sha256"]:
+        return None
+    return d["dram_bytes_per_launch"]
+
+
+def run_ours(args):
+    import torch
+
+    rank, world, local = dist_setup()
+    torch.cuda.set_device(local)
+    W = WORKLOADS[args.workload]()
+    if args.rows:
+        W.n = args.rows
+    W.setup(rank)
+    peaks = load_peaks()
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        W.step()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record(stream)
+    launches = 0
+    for i in range(args.steps):
+        evs[i][0].record(stream)
+        launches += W.step()
+        evs[i][1].record(stream)
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = sampler.stop()
+    ms = t0.elapsed_time(t1)
+    ms = max_over_ranks(ms, world)
+    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    bytes_step = W.bytes_per_step()
+    value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
+    achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
+
+    # end to end through the host-fed entry point
+    W.setup_e2e()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    W.step_e2e()
+    torch.cuda.synchronize()
+    barrier(world)
+    a = time.perf_counter()
+    for _ in range(e2e_steps):
+        W.step_e2e()
+    e2e_s = max_over_ranks(time.perf_counter() - a, world)
+    h2d, d2h = W.e2e_bytes()
+    e2e_value = world * h2d * e2e_steps / e2e_s / 1e9
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rows, t, sample = W.cpu_sample(args.cpu_budget)
+        cpu = {"value": rows * W.esize / t / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": W.dtype, "data": "synthetic (seeded SplitMix64)",
+            "config": W.config(),
+            "rows_per_s": world * W.n * args.steps / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": kernel_traffic(W.kernel, W.name),
+                         "kernel": W.kernel, "peak_source": peaks["source"] + " (hbm_gbs, burst copy)"},
+            "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "steps": e2e_steps},
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The CPU oracle, single-threaded, on a bounded sample of the same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    W = WORKLOADS[args.workload]()
+    per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        W.cpu_sample(per_step)
+    rows_t, t_t = 0, 0.0
+    sample = ""
+    for _ in range(args.steps):
+        rows, t, sample = W.cpu_sample(per_step)
+        rows_t += rows
+        t_t += t
+    v = rows_t * W.esize / t_t / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": round(v, 3), "unit": UNIT,
+            "n_gpus": int(os.environ.get("WORLD_SIZE", "1")), "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * t_t / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": W.dtype, "data": "synthetic (seeded SplitMix64)",
+            "config": W.config(),
+            "cpu_baseline": {"value": round(v, 3), "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": f"per step: {sample}"},
+            "e2e": {"value": round(v, 3), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--workload", default="scan", choices=sorted(WORKLOADS))
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=5)
+    ap.add_argument("--cpu-budget", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--rows", type=int, default=0, help="override the workload's row count (small profiling cases)")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,159 @@
+"""Python binding of libagg, the GB300 (sm_103a) in-memory aggregation library.
+
+The binding only marshals arguments: every step of an aggregation runs in the
+library's CUDA kernels behind the C ABI declared in ``include/agg.h``. PyTorch
+provides device memory and streams. There is no CPU fallback: if the compiled
+library is missing, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libagg.so")
+
+AGG_I32, AGG_I64, AGG_U32, AGG_F32, AGG_F64 = range(5)
+AGG_SUM, AGG_MIN, AGG_MAX, AGG_COUNT, AGG_AVG = 1, 2, 4, 8, 16
+AGG_ALL = 31
+AGG_OK, AGG_ERR_INVALID, AGG_ERR_OOM, AGG_ERR_CUDA, AGG_ERR_TABLE_FULL, AGG_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
+
+DTYPE_NAMES = {AGG_I32: "i32", AGG_I64: "i64", AGG_U32: "u32", AGG_F32: "f32", AGG_F64: "f64"}
+DTYPE_CODES = {v: k for k, v in DTYPE_NAMES.items()}
+NP_DTYPES = {AGG_I32: np.int32, AGG_I64: np.int64, AGG_U32: np.uint32, AGG_F32: np.float32, AGG_F64: np.float64}
+
+
+class AggError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"agg status {status}: {msg}")
+        self.status = status
+
+
+class AggScalar(ctypes.Structure):
+    """Mirror of ``agg_scalar`` (80 bytes)."""
+    _fields_ = [
+        ("count", ctypes.c_int64),
+        ("sum_i", ctypes.c_int64),
+        ("sum_f", ctypes.c_double),
+        ("avg", ctypes.c_double),
+        ("min_i", ctypes.c_int64),
+        ("max_i", ctypes.c_int64),
+        ("min_f", ctypes.c_double),
+        ("max_f", ctypes.c_double),
+        ("dtype", ctypes.c_uint32),
+        ("ops", ctypes.c_uint32),
+        ("reserved", ctypes.c_int64),
+    ]
+
+    def as_dict(self) -> dict:
+        fp = self.dtype in (AGG_F32, AGG_F64)
+        return {
+            "count": int(self.count),
+            "sum": float(self.sum_f) if fp else int(self.sum_i),
+            "min": float(self.min_f) if fp else int(self.min_i),
+            "max": float(self.max_f) if fp else int(self.max_i),
+            "avg": float(self.avg),
+        }
+
+
+SCALAR_BYTES = ctypes.sizeof(AggScalar)
+
+_lib = None
+
+# name -> (restype, argtypes) of every exported entry point
+_vp, _i64, _i32, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_uint32
+SIGNATURES = {
+    "agg_reduce": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
+    "agg_reduce_host": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
+    "agg_last_error": (ctypes.c_char_p, []),
+    "agg_version": (_i32, []),
+}
+
+
+def build(force: bool = False) -> str:
+    """Compile libagg.so for sm_103a (nvcc; cross-compiles without a GPU)."""
+    return _build.build(force=force)
+
+
+def lib():
+    """Load libagg.so. Raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2606_10030_gb300.build()")
+        try:
+            import torch  # noqa: F401  (load torch's CUDA runtime first so both share it)
+        except Exception:
+            pass
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def last_error() -> str:
+    return lib().agg_last_error().decode()
+
+
+def check(status: int) -> None:
+    if status != AGG_OK:
+        raise AggError(status, last_error())
+
+
+def _stream_ptr(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def dtype_code(t) -> int:
+    import torch
+    m = {torch.int32: AGG_I32, torch.int64: AGG_I64, torch.uint32: AGG_U32,
+         torch.float32: AGG_F32, torch.float64: AGG_F64}
+    if t.dtype not in m:
+        raise TypeError(f"unsupported column dtype {t.dtype}")
+    return m[t.dtype]
+
+
+def decode_scalar(buf) -> AggScalar:
+    """Decode an agg_scalar from an 80-byte uint8 tensor or bytes."""
+    if not isinstance(buf, (bytes, bytearray)):
+        buf = bytes(buf.cpu().numpy().tobytes())
+    return AggScalar.from_buffer_copy(buf[:SCALAR_BYTES])
+
+
+# ---------------------------------------------------------------------------
+# Entry points (same names as the C ABI)
+# ---------------------------------------------------------------------------
+
+def agg_reduce(col, ops: int = AGG_ALL, out=None, stream=None, n: int | None = None):
+    """Ungrouped aggregation of a 1-D device tensor; returns the 80-byte device result.
+
+    The result is written asynchronously on ``stream``; decode it with
+    ``decode_scalar(out)`` (which synchronises by copying to the host).
+    """
+    import torch
+    assert col.is_cuda and col.dim() == 1 and col.is_contiguous()
+    if out is None:
+        out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=col.device)
+    n = col.numel() if n is None else n
+    check(lib().agg_reduce(ctypes.c_void_p(col.data_ptr()), n, dtype_code(col), ops,
+                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def agg_reduce_host(col, ops: int = AGG_ALL, stream=None) -> AggScalar:
+    """End-to-end ungrouped aggregation of a (pinned) host tensor; synchronous."""
+    assert not col.is_cuda and col.dim() == 1 and col.is_contiguous()
+    out = AggScalar()
+    check(lib().agg_reduce_host(ctypes.c_void_p(col.data_ptr()), col.numel(), dtype_code(col), ops,
+                                ctypes.byref(out), _stream_ptr(stream)))
+    return out
