@@ -127,6 +127,29 @@ agg_status agg_reduce(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t 
 agg_status agg_reduce_host(const void* col_host, int64_t n, agg_dtype dtype, uint32_t ops,
                            agg_scalar* out_host, void* stream);
 
+/*
+ * agg_reduce_noalloc -- agg_reduce without any device allocation.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory, for example an engine that has reserved all
+ * of the GPU's memory for its own pool up front (so cudaMalloc would fail), or
+ * a latency-critical path that cannot afford the device-wide synchronisation
+ * that cudaMalloc and cudaFree can imply. Arguments, results and errors are
+ * those of agg_reduce; the caller still provides the column and out_dev.
+ *
+ * Scratch: a static device array of 82,176 bytes (the ticket plus 2048 block
+ * partials) that every GPU loading the library holds until the process exits.
+ * A launch that would need more blocks than that returns AGG_ERR_INVALID with
+ * a message; no call allocates (no cudaMalloc, cudaFree or allocating library
+ * routine). The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. All calls share the one array: each call clears
+ * the ticket it needs at zero, and calls whose work overlaps on the GPU (for
+ * example on two streams) race on the array and give wrong results.
+ */
+agg_status agg_reduce_noalloc(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t ops,
+                              agg_scalar* out_dev, void* stream);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* agg_last_error(void);
 

@@ -69,6 +69,7 @@ _vp, _i64, _i32, _u32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_
 SIGNATURES = {
     "agg_reduce": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_reduce_host": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
+    "agg_reduce_noalloc": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_last_error": (ctypes.c_char_p, []),
     "agg_version": (_i32, []),
 }
@@ -147,6 +148,21 @@ def agg_reduce(col, ops: int = AGG_ALL, out=None, stream=None, n: int | None = N
     n = col.numel() if n is None else n
     check(lib().agg_reduce(ctypes.c_void_p(col.data_ptr()), n, dtype_code(col), ops,
                            ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def agg_reduce_noalloc(col, ops: int = AGG_ALL, out=None, stream=None):
+    """agg_reduce without device allocation (static scratch inside the library).
+
+    For callers that cannot allocate device memory. Calls that overlap on the
+    GPU share the static scratch and race; issue them on one stream.
+    """
+    import torch
+    assert col.is_cuda and col.dim() == 1 and col.is_contiguous()
+    if out is None:
+        out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=col.device)
+    check(lib().agg_reduce_noalloc(ctypes.c_void_p(col.data_ptr()), col.numel(), dtype_code(col), ops,
+                                   ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
     return out
 
 

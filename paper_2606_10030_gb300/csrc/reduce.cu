@@ -492,3 +492,84 @@ extern "C" agg_status agg_reduce_host(const void* col_host, int64_t n, agg_dtype
   }
   return AGG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of agg_reduce.
+//
+// Its scratch (the ticket and one Partial per block) lives in a file-scope
+// __device__ array instead of library-allocated memory, so a call performs no
+// device allocation at all. Host code must not pass the array's name to a
+// kernel (on the host it names a stand-in object, not device memory); the
+// device address is looked up once per device with cudaGetSymbolAddress and
+// cached.
+// ---------------------------------------------------------------------------
+namespace agg {
+
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr size_t kNoAllocScratchBytes = kTicketBytes + (size_t)kNoAllocMaxBlocks * sizeof(Partial);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch on the current device (set up on first use).
+static void* noalloc_scratch_address(agg_status* st) {
+  static std::mutex mu;
+  static std::map<int, void*> addr;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) {
+    set_error("agg_reduce_noalloc: cudaGetDevice failed: %s", cudaGetErrorString(e));
+    *st = AGG_ERR_CUDA;
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = addr.find(dev);
+  if (it != addr.end()) {
+    *st = AGG_OK;
+    return it->second;
+  }
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr) {
+    set_error("agg_reduce_noalloc: cudaGetSymbolAddress of the static scratch failed on device %d: %s", dev,
+              cudaGetErrorString(e));
+    *st = AGG_ERR_CUDA;
+    return nullptr;
+  }
+  addr[dev] = p;
+  *st = AGG_OK;
+  return p;
+}
+
+}  // namespace agg
+
+extern "C" agg_status agg_reduce_noalloc(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t ops,
+                                         agg_scalar* out_dev, void* stream) {
+  clear_error();
+  agg_status st = check_reduce_args(col_dev, n, dtype, ops, out_dev);
+  if (st != AGG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  void* fn = pick_scan(dtype, need_sum(ops), need_mm(ops));
+  const size_t es = dtype_size(dtype);
+  int64_t head = (int64_t)(((16 - ((uintptr_t)col_dev & 15)) & 15) / es);
+  if (head > n) head = n;
+  const int grid = scan_grid(fn, n - head, dtype);
+  const size_t need = kTicketBytes + (size_t)grid * sizeof(Partial);
+  if (need > kNoAllocScratchBytes) {
+    set_error("agg_reduce_noalloc: this launch needs %zu bytes of scratch (%d blocks) but the static scratch "
+              "holds %zu bytes (%d blocks)",
+              need, grid, kNoAllocScratchBytes, kNoAllocMaxBlocks);
+    return AGG_ERR_INVALID;
+  }
+  char* scratch = (char*)noalloc_scratch_address(&st);
+  if (!scratch) return st;
+  unsigned* ticket = (unsigned*)scratch;
+  Partial* parts = (Partial*)(scratch + kTicketBytes);
+  // The array keeps the previous call's contents; the ticket must start at zero.
+  AGG_CUDA_TRY(cudaMemsetAsync(ticket, 0, sizeof(unsigned), s));
+  int part_base = 0, finalize = 1;
+  int64_t count = n;
+  void* args[] = {(void*)&col_dev, (void*)&n, (void*)&head, (void*)&parts, (void*)&part_base,
+                  (void*)&ticket, (void*)&out_dev, (void*)&ops, (void*)&count, (void*)&finalize};
+  AGG_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, 0, s));
+  return AGG_OK;
+}
