@@ -10,8 +10,13 @@ with the host-to-device copy inside the timed region.
 
 Workloads (synthetic, seeded; they stand in for the paper's TPC-H
 lineitem.suppkey scan, which is not available here):
+  groupby     (default) GROUP BY SUM/COUNT/MIN/MAX over 2^26 rows: uint32 keys
+              drawn uniformly from 1024 random keys, int64 values uniform in
+              [0, 2^32) (768 MiB of input)
   scan        ungrouped SUM/MIN/MAX/COUNT/AVG over a 2^30-row int32 column
               (4 GiB, uniform in [-2^20, 2^20))
+The default run also reports, as extra objects, the 2^30-row scan and the
+high-cardinality GROUP BY (2^28 rows, Zipf(1) keys over 2^24, float32 values).
 
 Under torchrun each rank aggregates its own replica of the workload (weak
 scaling, no data-path collective); only the timing uses a MAX all-reduce.
@@ -139,6 +144,7 @@ class ScanWorkload:
     dtype = "i32"
     esize = 4
     kernel = "reduce_scan"
+    phase = "scan"
 
     def config(self):
         return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30-row int32 column uniform in [-2^20, 2^20)",
@@ -194,7 +200,139 @@ class ScanWorkload:
         return rows, t_compute, f"oracle.reduce over the first {rows} rows (2^24-row slices) of the column"
 
 
-WORKLOADS = {"scan": ScanWorkload}
+class GroupbyWorkload:
+    """GROUP BY SUM/COUNT/MIN/MAX, 2^26 rows, 1024 uniform random uint32 keys, int64 values."""
+    name = "groupby"
+    n = 1 << 26
+    D = 1024
+    dtype = "i64"
+    esize = 12  # key + value bytes per row
+    kernel = "gb_build"
+    phase = "build"
+
+    def config(self):
+        return {"workload": "GROUP BY SUM/COUNT/MIN/MAX, 2^26 rows, uint32 keys uniform over 1024 random keys, "
+                            "int64 values uniform in [0, 2^32)",
+                "rows": self.n, "distinct_keys": self.D, "key_dtype": "uint32", "value_dtype": "int64",
+                "input_bytes": self.n * self.esize, "strategy": "auto (sketch rule -> shared-memory hash)",
+                "l2": "input (768 MiB) larger than L2 (129 MB); no flush needed"}
+
+    def bytes_per_step(self):
+        return self.n * self.esize
+
+    def setup(self, rank):
+        import paper_2606_10030_gb300 as agg
+        from datagen import cuda as dgc
+        self.agg = agg
+        self.ops = agg.AGG_SUM | agg.AGG_COUNT | agg.AGG_MIN | agg.AGG_MAX
+        if getattr(self, "ops_override", 0):
+            self.ops = self.ops_override
+        self.opts = agg.options(getattr(self, "strategy", agg.AGG_STRAT_AUTO))
+        self.k = dgc.keys_uniform(self.n, self.D, seed=rank)
+        self.v = dgc.values(self.dtype, self.n, seed=rank)
+        import torch
+        torch.cuda.synchronize()
+
+    def step(self):
+        g = self.agg.agg_groupby(self.k, self.v, self.ops, self.opts)
+        self.last_strategy = g.strategy
+        g.free()
+        return 0  # launches are counted by the library
+
+    def setup_e2e(self):
+        self.hk = self.k.cpu().pin_memory()
+        self.hv = self.v.cpu().pin_memory()
+
+    def step_e2e(self):
+        g = self.agg.agg_groupby_host(self.hk, self.hv, self.ops, self.opts)
+        r = g.to_host()
+        self.e2e_groups = len(r["keys"])
+        g.free()
+        return self.e2e_groups
+
+    def e2e_bytes(self):
+        return self.n * self.esize, getattr(self, "e2e_groups", self.D) * (4 + 5 * 8)
+
+    def cpu_sample(self, budget_s: float):
+        """Oracle GROUP BY on consecutive 2^24-row slices of the same columns until budget_s elapses."""
+        import datagen as dg
+        import oracle
+        oracle.build()
+        rows, start, t_compute = 0, 0, 0.0
+        chunk = 1 << 24
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and start < self.n:
+            k = dg.keys_uniform(chunk, self.D, 0, start=start)
+            v = dg.values(self.dtype, chunk, 0, start=start)
+            a = time.perf_counter()
+            oracle.groupby(k, v)
+            t_compute += time.perf_counter() - a
+            rows += chunk
+            start += chunk
+        return rows, t_compute, f"oracle.groupby (std::map) over the first {rows} rows (2^24-row slices)"
+
+
+WORKLOADS = {"groupby": GroupbyWorkload, "scan": ScanWorkload}
+
+
+def extra_scan(steps: int, peaks: dict) -> dict:
+    """Ungrouped 2^30-row int32 scan: input GB/s and fraction of the HBM peak."""
+    import torch
+
+    import paper_2606_10030_gb300 as agg
+    from datagen import cuda as dgc
+    n = 1 << 30
+    col = dgc.values("i32", n, seed=0)
+    out = torch.empty(agg.SCALAR_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        agg.agg_reduce(col, agg.AGG_ALL, out=out)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        agg.agg_reduce(col, agg.AGG_ALL, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / steps
+    gbs = n * 4 / (ms * 1e-3) / 1e9
+    del col
+    torch.cuda.empty_cache()
+    return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30 int32 rows (4 GiB)", "ms": round(ms, 4),
+            "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
+            "frac_of_nominal_8TBs": round(gbs / 8000.0, 4), "steps": steps}
+
+
+def extra_zipf(steps: int) -> dict:
+    """GROUP BY SUM/AVG, 2^28 rows, Zipf(1) keys over 2^24 random keys, float32 N(0,1)*1e3."""
+    import torch
+
+    import paper_2606_10030_gb300 as agg
+    from datagen import cuda as dgc
+    n, D = 1 << 28, 1 << 24
+    k = dgc.keys_zipf(n, D, 1.0, 0)
+    v = dgc.values("f32", n, 0)
+    ops = agg.AGG_SUM | agg.AGG_AVG
+    g = agg.agg_groupby(k, v, ops)
+    strategy = agg.STRATEGY_NAMES[g.strategy]
+    d = g.num_groups
+    g.free()
+    torch.cuda.synchronize()
+    res = {}
+    for name, strat in [("auto", agg.AGG_STRAT_AUTO), ("smem", agg.AGG_STRAT_SMEM),
+                        ("global", agg.AGG_STRAT_GLOBAL), ("sort", agg.AGG_STRAT_SORT)]:
+        o = agg.options(strat)
+        agg.agg_groupby(k, v, ops, o).free()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            agg.agg_groupby(k, v, ops, o).free()
+        torch.cuda.synchronize()
+        ms = (time.perf_counter() - t0) * 1e3 / steps
+        res[name] = {"ms": round(ms, 3), "GB/s": round(n * 8 / (ms * 1e-3) / 1e9, 1)}
+    del k, v
+    torch.cuda.empty_cache()
+    return {"workload": "GROUP BY SUM/AVG, 2^28 rows, Zipf(1.0) keys over 2^24, float32 values",
+            "groups": d, "auto_strategy": strategy, "per_strategy": res, "steps": steps}
+
 
 
 def kernel_traffic(kernel: str, workload: str):
@@ -223,12 +361,18 @@ def run_ours(args):
     W = WORKLOADS[args.workload]()
     if args.rows:
         W.n = args.rows
+    if args.strategy:
+        W.strategy = args.strategy
+    if args.ops:
+        W.ops_override = args.ops
     W.setup(rank)
     peaks = load_peaks()
     stream = torch.cuda.current_stream()
+    import paper_2606_10030_gb300 as agg
     for _ in range(args.warmup):
         W.step()
     torch.cuda.synchronize()
+    agg.profile_read()
     sampler = ClockSampler(local)
     sampler.start()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
@@ -236,6 +380,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
+    agg.profile_enable(True)
+    launches0 = agg.launch_count()
     t0.record(stream)
     launches = 0
     for i in range(args.steps):
@@ -244,11 +390,17 @@ def run_ours(args):
         evs[i][1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
+    launches = agg.launch_count() - launches0
+    prof = agg.profile_read()
+    agg.profile_enable(False)
     barrier(world)
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
     ms = max_over_ranks(ms, world)
-    per_launch_ms = statistics.mean(a.elapsed_time(b) for a, b in evs)
+    ph_ms, ph_calls = prof.get(W.phase, (0.0, 0))
+    if ph_calls == 0:  # a strategy without this phase: time the whole step
+        ph_ms, ph_calls = ms, args.steps
+    per_launch_ms = ph_ms / max(1, ph_calls)
     bytes_step = W.bytes_per_step()
     value = world * bytes_step * args.steps / (ms * 1e-3) / 1e9
     achieved = bytes_step / (per_launch_ms * 1e-3) / 1e9
@@ -266,6 +418,10 @@ def run_ours(args):
     h2d, d2h = W.e2e_bytes()
     e2e_value = world * h2d * e2e_steps / e2e_s / 1e9
 
+    extra = {}
+    if rank == 0 and world == 1 and not args.no_extra and W.name == "groupby":
+        extra["scan"] = extra_scan(200, peaks)
+        extra["zipf"] = extra_zipf(5)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows, t, sample = W.cpu_sample(args.cpu_budget)
@@ -283,6 +439,8 @@ def run_ours(args):
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "steps": e2e_steps},
             "gpu_launches": launches,
+            "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
+            "extra": extra,
             "clocks": clocks,
             "cpu_baseline": cpu,
         }
@@ -321,7 +479,10 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="scan", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="groupby", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-extra", action="store_true", help="skip the extra scan and Zipf measurements")
+    ap.add_argument("--strategy", type=int, default=0, help="GROUP BY strategy (0 auto, 1 smem, 2 global, 3 sort)")
+    ap.add_argument("--ops", type=int, default=0, help="override the ops bitmask (diagnostics)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--cpu-budget", type=float, default=12.0)

@@ -127,6 +127,115 @@ agg_status agg_reduce(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t 
 agg_status agg_reduce_host(const void* col_host, int64_t n, agg_dtype dtype, uint32_t ops,
                            agg_scalar* out_host, void* stream);
 
+/* GROUP BY strategies (agg_options.strategy). */
+typedef enum {
+  AGG_STRAT_AUTO = 0,     /* rule on the key sketch (no learned model) */
+  AGG_STRAT_SMEM = 1,     /* per-block shared-memory hash tables that spill to the global table */
+  AGG_STRAT_GLOBAL = 2,   /* one open-addressing hash table in HBM */
+  AGG_STRAT_SORT = 3,     /* stable radix sort by key, then a segmented reduction */
+  AGG_STRAT_LEARNED = 4,  /* the MLP selector on the key sketch */
+  AGG_STRAT_AUTOTUNE = 5  /* time every candidate once per query signature, cache the fastest */
+} agg_strategy;
+
+/* Tuning knobs of agg_groupby; a zeroed struct (or NULL) selects defaults. */
+typedef struct agg_options {
+  int32_t strategy;        /* agg_strategy */
+  int32_t block_threads;   /* threads per block of the build kernel; 0 = default */
+  int32_t blocks_per_sm;   /* resident blocks per SM; 0 = occupancy limit */
+  int32_t smem_slots;      /* shared-memory table slots (power of two, <= 8192); 0 = from the sketch */
+  int64_t table_slots;     /* global table slots (power of two); 0 = from the sketch */
+  uint64_t sample_offset;  /* offset of the strided key sample (pass a seeded draw) */
+  int32_t items_per_thread;/* rows per thread per loop iteration (4 or 8); 0 = default */
+  int32_t reserved[3];
+} agg_options;
+
+/*
+ * GROUP BY result, owned by the library (free with agg_groups_free).
+ * Rows are in ascending key order, one per distinct key present. Arrays are
+ * device memory of num_groups elements each:
+ *   keys   uint32          count  int64
+ *   sum    int64 (integer value columns, wraps mod 2^64) or double (float)
+ *   min    int64 or double (float32 values widened exactly)
+ *   max    int64 or double
+ *   avg    double = (double)sum / (double)count
+ * Arrays of functions not in `ops` are unspecified (count is always set).
+ */
+typedef struct agg_groups {
+  int64_t num_groups;
+  int32_t dtype;           /* agg_dtype of the value column */
+  uint32_t ops;
+  int32_t strategy;        /* agg_strategy actually used (SMEM, GLOBAL or SORT) */
+  int32_t retries;         /* times the global table was regrown */
+  int64_t table_slots;     /* global table slots used (0 for SORT) */
+  int32_t smem_slots;      /* shared-memory table slots used (0 unless SMEM) */
+  int32_t reserved;
+  uint32_t* keys;
+  int64_t* count;
+  void* sum;
+  void* min;
+  void* max;
+  double* avg;
+  float features[16];      /* key sketch used for the choice (zeros if none) */
+  void* priv;
+} agg_groups;
+
+/*
+ * agg_groupby -- SUM/MIN/MAX/COUNT/AVG of vals_dev per distinct key of
+ * keys_dev (the hash- and sort-based group-by of Sec. 7; the per-item fold is
+ * the aggregate() of Fig. 4).
+ *
+ *  keys_dev  device pointer to n uint32 keys (any value, 0xFFFFFFFF included)
+ *  vals_dev  device pointer to n values of vdtype, aligned to the element size
+ *  n         0 <= n < 2^32 (per-group counts are kept in 32 bits while building)
+ *  opt       NULL or tuning knobs (strategy, table sizes, sample offset)
+ *  out       receives a library-owned agg_groups*
+ *
+ * Synchronous: the call returns once the result is complete (it reads back
+ * the group count and the table status). The strategy is chosen by `opt`
+ * (AUTO when NULL) from a 16-feature sketch of 4096 strided keys. A global
+ * table that fills up (AGG_ERR_TABLE_FULL inside) is regrown 4x and the build
+ * repeated, until the table has 4n slots (or 2^31). Every strategy returns identical keys, counts,
+ * integer sums, min/max and integer averages; float sums and averages agree
+ * within rounding (atomic order).
+ * Errors: AGG_ERR_INVALID, AGG_ERR_OOM, AGG_ERR_CUDA, AGG_ERR_TABLE_FULL (the
+ * table could not be grown enough).
+ */
+agg_status agg_groupby(const uint32_t* keys_dev, const void* vals_dev, int64_t n, agg_dtype vdtype,
+                       uint32_t ops, const agg_options* opt, agg_groups** out, void* stream);
+
+/*
+ * agg_groupby_host -- end-to-end agg_groupby fed from host memory (Sec. 5.3).
+ * keys_host / vals_host are host pointers (pinned for full link bandwidth).
+ * The columns are copied to the device in chunks overlapped with the build;
+ * the result is as for agg_groupby (device arrays; see agg_groups_to_host).
+ */
+agg_status agg_groupby_host(const uint32_t* keys_host, const void* vals_host, int64_t n, agg_dtype vdtype,
+                            uint32_t ops, const agg_options* opt, agg_groups** out, void* stream);
+
+/* Copy a result's arrays to host buffers of num_groups elements (any may be NULL). Synchronous. */
+agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* count, void* sum, void* min,
+                              void* max, double* avg);
+
+/* Release a result (NULL is allowed). */
+void agg_groups_free(agg_groups* g);
+
+/*
+ * agg_sketch -- the 16 features of a sample of keys that the strategy
+ * selectors read (written to features_dev[0..16) as float32, asynchronously):
+ *   0 log2 n            1 value bytes        2 popcount(ops)      3 float values
+ *   4 sample distinct fraction               5 singleton fraction f1/m
+ *   6 doubleton fraction f2/m                7 top-1 share        8 top-8 share
+ *   9 rank-frequency slope (log-log least squares over the top 32 ranks)
+ *  10 sample entropy / ln m                  11 adjacent-equal fraction
+ *  12 log2 of the GEE distinct estimate (sqrt(n/m) f1 + sum_{j>=2} f_j)
+ *  13 log2(1 + estimated table bytes / shared memory per block)
+ *  14 log2(1 + estimated table bytes / L2 bytes)
+ *  15 log2(key max - key min + 1) over the sample
+ * The sample is m = min(n, 4096) keys at (sample_offset + j * floor(n/m)) mod n.
+ */
+agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uint32_t ops,
+                      uint64_t sample_offset, float* features_dev, void* stream);
+
 /*
  * agg_reduce_noalloc -- agg_reduce without any device allocation.
  *
@@ -149,6 +258,34 @@ agg_status agg_reduce_host(const void* col_host, int64_t n, agg_dtype dtype, uin
  */
 agg_status agg_reduce_noalloc(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t ops,
                               agg_scalar* out_dev, void* stream);
+
+/*
+ * Instrumentation (no counterpart in the paper; used by the benchmark).
+ *
+ * agg_launch_count: number of kernels this library has launched in the
+ * process so far (all devices, all threads).
+ *
+ * agg_profile_enable / agg_profile_read: when enabled, the library records a
+ * pair of CUDA events on the launching stream around each phase it runs and
+ * accumulates their elapsed times. agg_profile_read waits for the recorded
+ * events, writes the accumulated milliseconds and call counts of every phase
+ * into ms[AGG_PHASES] and calls[AGG_PHASES] (either may be NULL), resets the
+ * accumulators and returns AGG_OK.
+ */
+enum {
+  AGG_PHASE_SCAN = 0,      /* agg_reduce scan kernel */
+  AGG_PHASE_SKETCH = 1,    /* key sketch */
+  AGG_PHASE_BUILD = 2,     /* hash-table build (one per build launch) */
+  AGG_PHASE_FINALIZE = 3,  /* compaction, key sort and output of hash results */
+  AGG_PHASE_SORT = 4,      /* radix sort of (key, value) rows (sort strategy) */
+  AGG_PHASE_SEGREDUCE = 5, /* run detection and segmented reduction (sort strategy) */
+  AGG_PHASE_BATCH = 6,     /* batched persistent kernel */
+  AGG_PHASE_MLP = 7,       /* selector network kernels */
+  AGG_PHASES = 8
+};
+int64_t agg_launch_count(void);
+void agg_profile_enable(int on);
+agg_status agg_profile_read(double* ms, int64_t* calls);
 
 /* Message of the last failed call on this thread ("" if none). */
 const char* agg_last_error(void);

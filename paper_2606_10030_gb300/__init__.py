@@ -62,6 +62,47 @@ class AggScalar(ctypes.Structure):
 
 SCALAR_BYTES = ctypes.sizeof(AggScalar)
 
+AGG_STRAT_AUTO, AGG_STRAT_SMEM, AGG_STRAT_GLOBAL, AGG_STRAT_SORT, AGG_STRAT_LEARNED, AGG_STRAT_AUTOTUNE = range(6)
+STRATEGY_NAMES = {AGG_STRAT_AUTO: "auto", AGG_STRAT_SMEM: "smem", AGG_STRAT_GLOBAL: "global",
+                  AGG_STRAT_SORT: "sort", AGG_STRAT_LEARNED: "learned", AGG_STRAT_AUTOTUNE: "autotune"}
+N_FEATURES = 16
+
+
+class AggOptions(ctypes.Structure):
+    """Mirror of ``agg_options``."""
+    _fields_ = [
+        ("strategy", ctypes.c_int32),
+        ("block_threads", ctypes.c_int32),
+        ("blocks_per_sm", ctypes.c_int32),
+        ("smem_slots", ctypes.c_int32),
+        ("table_slots", ctypes.c_int64),
+        ("sample_offset", ctypes.c_uint64),
+        ("items_per_thread", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 3),
+    ]
+
+
+class AggGroups(ctypes.Structure):
+    """Mirror of ``agg_groups``."""
+    _fields_ = [
+        ("num_groups", ctypes.c_int64),
+        ("dtype", ctypes.c_int32),
+        ("ops", ctypes.c_uint32),
+        ("strategy", ctypes.c_int32),
+        ("retries", ctypes.c_int32),
+        ("table_slots", ctypes.c_int64),
+        ("smem_slots", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+        ("keys", ctypes.c_void_p),
+        ("count", ctypes.c_void_p),
+        ("sum", ctypes.c_void_p),
+        ("min", ctypes.c_void_p),
+        ("max", ctypes.c_void_p),
+        ("avg", ctypes.c_void_p),
+        ("features", ctypes.c_float * 16),
+        ("priv", ctypes.c_void_p),
+    ]
+
 _lib = None
 
 # name -> (restype, argtypes) of every exported entry point
@@ -70,6 +111,14 @@ SIGNATURES = {
     "agg_reduce": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_reduce_host": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_reduce_noalloc": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
+    "agg_groupby": (_i32, [_vp, _vp, _i64, _i32, _u32, _vp, _vp, _vp]),
+    "agg_groupby_host": (_i32, [_vp, _vp, _i64, _i32, _u32, _vp, _vp, _vp]),
+    "agg_groups_to_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "agg_groups_free": (None, [_vp]),
+    "agg_sketch": (_i32, [_vp, _i64, _i32, _u32, ctypes.c_uint64, _vp, _vp]),
+    "agg_launch_count": (ctypes.c_int64, []),
+    "agg_profile_enable": (None, [_i32]),
+    "agg_profile_read": (_i32, [_vp, _vp]),
     "agg_last_error": (ctypes.c_char_p, []),
     "agg_version": (_i32, []),
 }
@@ -173,3 +222,105 @@ def agg_reduce_host(col, ops: int = AGG_ALL, stream=None) -> AggScalar:
     check(lib().agg_reduce_host(ctypes.c_void_p(col.data_ptr()), col.numel(), dtype_code(col), ops,
                                 ctypes.byref(out), _stream_ptr(stream)))
     return out
+
+
+class Groups:
+    """A GROUP BY result owned by the library; ``to_host()`` copies it to NumPy."""
+
+    def __init__(self, ptr):
+        self._ptr = ptr
+        g = ctypes.cast(ptr, ctypes.POINTER(AggGroups)).contents
+        self.num_groups = int(g.num_groups)
+        self.dtype = int(g.dtype)
+        self.ops = int(g.ops)
+        self.strategy = int(g.strategy)
+        self.retries = int(g.retries)
+        self.table_slots = int(g.table_slots)
+        self.smem_slots = int(g.smem_slots)
+        self.features = np.array(list(g.features), dtype=np.float32)
+
+    def to_host(self) -> dict:
+        d = self.num_groups
+        fp = self.dtype in (AGG_F32, AGG_F64)
+        keys = np.empty(d, np.uint32)
+        count = np.empty(d, np.int64)
+        s = np.empty(d, np.float64 if fp else np.int64)
+        mn = np.empty(d, np.float64 if fp else np.int64)
+        mx = np.empty(d, np.float64 if fp else np.int64)
+        avg = np.empty(d, np.float64)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        check(lib().agg_groups_to_host(self._ptr, p(keys), p(count), p(s), p(mn), p(mx), p(avg)))
+        return {"keys": keys, "count": count, "sum": s, "min": mn, "max": mx, "avg": avg}
+
+    def free(self):
+        if self._ptr:
+            lib().agg_groups_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def options(strategy: int = AGG_STRAT_AUTO, **kw) -> AggOptions:
+    o = AggOptions()
+    o.strategy = strategy
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
+def agg_groupby(keys, vals, ops: int = AGG_ALL, opts: AggOptions | None = None, stream=None,
+                n: int | None = None) -> Groups:
+    """GROUP BY keys (uint32 device tensor) over vals (device tensor); synchronous."""
+    assert keys.is_cuda and vals.is_cuda and keys.dim() == 1 and vals.dim() == 1
+    assert keys.is_contiguous() and vals.is_contiguous()
+    n = keys.numel() if n is None else n
+    out = ctypes.c_void_p()
+    check(lib().agg_groupby(ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()), n,
+                            dtype_code(vals), ops, ctypes.byref(opts) if opts is not None else None,
+                            ctypes.byref(out), _stream_ptr(stream)))
+    return Groups(out.value)
+
+
+def agg_groupby_host(keys, vals, ops: int = AGG_ALL, opts: AggOptions | None = None, stream=None) -> Groups:
+    """End-to-end GROUP BY of (pinned) host tensors; synchronous."""
+    assert not keys.is_cuda and not vals.is_cuda and keys.is_contiguous() and vals.is_contiguous()
+    out = ctypes.c_void_p()
+    check(lib().agg_groupby_host(ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()),
+                                 keys.numel(), dtype_code(vals), ops,
+                                 ctypes.byref(opts) if opts is not None else None, ctypes.byref(out),
+                                 _stream_ptr(stream)))
+    return Groups(out.value)
+
+
+def agg_sketch(keys, vdtype: int, ops: int = AGG_ALL, sample_offset: int = 0, out=None, stream=None):
+    """The 16 sketch features of a device key column (float32 device tensor)."""
+    import torch
+    if out is None:
+        out = torch.empty(N_FEATURES, dtype=torch.float32, device=keys.device)
+    check(lib().agg_sketch(ctypes.c_void_p(keys.data_ptr()), keys.numel(), vdtype, ops, sample_offset,
+                           ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+PHASES = ["scan", "sketch", "build", "finalize", "sort", "segreduce", "batch", "mlp"]
+
+
+def launch_count() -> int:
+    """Kernels launched by the library so far in this process."""
+    return int(lib().agg_launch_count())
+
+
+def profile_enable(on: bool = True) -> None:
+    lib().agg_profile_enable(1 if on else 0)
+
+
+def profile_read() -> dict:
+    """Accumulated per-phase event time (ms) and call counts since the last read."""
+    ms = (ctypes.c_double * len(PHASES))()
+    calls = (ctypes.c_int64 * len(PHASES))()
+    check(lib().agg_profile_read(ms, calls))
+    return {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}

@@ -54,6 +54,33 @@ const DeviceInfo& device_info();  // of the current device
 // were zeroed when the block was (re)allocated and must be left zeroed by
 // every user (self-resetting counters live there).
 void* stream_scratch(cudaStream_t s, size_t bytes, agg_status* st);
+void* stream_pinned(cudaStream_t s, size_t bytes, agg_status* st);
+
+// Kernel-launch counter and optional per-phase event timing.
+void note_launch(int k = 1);
+struct PhaseTimer {
+  int phase;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  PhaseTimer(int phase, cudaStream_t s);
+  ~PhaseTimer();
+};
+
+// MurmurHash3's 32-bit finaliser (Appleby), a published bijective mixer.
+__host__ __device__ __forceinline__ uint32_t fmix32(uint32_t h) {
+  h ^= h >> 16;
+  h *= 0x85EBCA6Bu;
+  h ^= h >> 13;
+  h *= 0xC2B2AE35u;
+  h ^= h >> 16;
+  return h;
+}
+
+inline int64_t next_pow2(int64_t x) {
+  int64_t p = 1;
+  while (p < x) p <<= 1;
+  return p;
+}
 
 inline size_t dtype_size(int dt) {
   switch (dt) {

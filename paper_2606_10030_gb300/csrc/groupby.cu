@@ -1,0 +1,1305 @@
+// GROUP BY with hash tables (steps a5, a5g, a6) and the agg_groupby driver.
+//
+// Build. Every row is folded (the aggregate() of Fig. 4) into the slot of its
+// key in an open-addressing hash table (MurmurHash3 fmix32, linear probing,
+// bounded probe count):
+//   SMEM    each block owns a table in shared memory and updates it with
+//           shared-memory atomics; rows whose key finds no slot within the
+//           probe bound go straight to the global table ("spill"); at the end
+//           the block merges its table into the global one.
+//   GLOBAL  every row updates the global table in HBM with L2 atomics.
+// Keys are stored as key + 1 so that an all-zero table is empty; the key
+// 0xFFFFFFFF has its own side slot after the main slots. All accumulators
+// start at zero: count and sum add, MIN is kept as the complement of an
+// order-preserving image and MAX as the image, both updated with atomicMax.
+// Float32 sums in shared memory are TwoSum-compensated float32 pairs updated
+// with a 64-bit compare-and-swap; the merge into the global table and every
+// global update run in float64 atomics.
+//
+// Finalise. Occupied slots are sorted by key (one-block bitonic sort for small
+// tables; compaction + radix sort otherwise) and written out in ascending key
+// order, with AVG = SUM / COUNT and MIN/MAX decoded.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <tuple>
+#include <map>
+#include <mutex>
+
+#include "groupby.cuh"
+#include "sort.cuh"
+
+namespace agg {
+
+// ---------------------------------------------------------------------------
+// Value traits: order-preserving 64-bit image of a value.
+// ---------------------------------------------------------------------------
+template <int DT> struct GV;
+template <> struct GV<AGG_I32> {
+  using T = int32_t;
+  __device__ static uint64_t img(T v) { return img_i64((int64_t)v); }
+};
+template <> struct GV<AGG_I64> {
+  using T = int64_t;
+  __device__ static uint64_t img(T v) { return img_i64(v); }
+};
+template <> struct GV<AGG_U32> {
+  using T = uint32_t;
+  __device__ static uint64_t img(T v) { return img_i64((int64_t)v); }
+};
+template <> struct GV<AGG_F32> {
+  using T = float;
+  __device__ static uint64_t img(T v) { return (uint64_t)img_f32(v); }
+};
+template <> struct GV<AGG_F64> {
+  using T = double;
+  __device__ static uint64_t img(T v) { return img_f64(v); }
+};
+
+template <bool MM> struct GSlot;
+template <> struct __align__(16) GSlot<false> {
+  uint32_t key1;
+  uint32_t cnt;
+  unsigned long long sum;
+};
+template <> struct __align__(32) GSlot<true> {
+  uint32_t key1;
+  uint32_t cnt;
+  unsigned long long sum;
+  unsigned long long minc;
+  unsigned long long mx;
+};
+
+constexpr int kGlobalProbe = 128;
+constexpr int kSmemProbe = 8;
+constexpr int kStatusFull = 1;
+
+struct BuildArgs {
+  const uint32_t* keys;
+  const void* vals;
+  int64_t n;
+  int64_t head;        // rows before the 16-byte aligned body (vector path)
+  void* table;         // GSlot[mask + 2]
+  uint32_t mask;       // main slots - 1 (main slots a power of two)
+  int smem_slots;      // S (power of two) for SMEM, else 0
+  int smem_cap;        // max keys inserted into the shared table
+  int* status;
+};
+
+// Global slot of key (insert if absent); -1 if no slot within the probe bound.
+template <bool MM>
+__device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, uint32_t key) {
+  if (key == 0xFFFFFFFFu) return (int64_t)mask + 1;
+  const uint32_t k1 = key + 1;
+  uint32_t h = fmix32(key) & mask;
+#pragma unroll 1
+  for (int p = 0; p < kGlobalProbe; ++p) {
+    uint32_t cur = *(volatile uint32_t*)&tab[h].key1;
+    if (cur == k1) return h;
+    if (cur == 0) {
+      uint32_t old = atomicCAS(&tab[h].key1, 0u, k1);
+      if (old == 0u || old == k1) return h;
+    }
+    h = (h + 1) & mask;
+  }
+  return -1;
+}
+
+// Fold one row (or a merged partial) into a global slot.
+template <int DT, bool MM>
+__device__ __forceinline__ void g_add_row(GSlot<MM>& s, typename GV<DT>::T v) {
+  atomicAdd(&s.cnt, 1u);
+  if (DT == AGG_F32 || DT == AGG_F64) {
+    atomicAdd((double*)&s.sum, (double)v);
+  } else {
+    atomicAdd(&s.sum, (unsigned long long)(int64_t)v);
+  }
+  if (MM) {
+    const uint64_t m = GV<DT>::img(v);
+    atomicMax(&((GSlot<true>&)s).minc, (unsigned long long)~m);
+    atomicMax(&((GSlot<true>&)s).mx, (unsigned long long)m);
+  }
+}
+
+// Shared-memory table over S + 1 slots (S a power of two >= 64; slot S holds
+// the key 0xFFFFFFFF). Keys are probed a bucket of 4 slots at a time with one
+// 16-byte load. Every per-row update uses native 32-bit shared atomics:
+//   count     u32 add
+//   sum       integers: two u32 words; the low word's atomic add returns the
+//             previous value, so the adding thread sees its own carry exactly
+//             and adds it with the high part (the pair is the 64-bit sum mod
+//             2^64). float32: s and c words; the adder recovers the rounding
+//             error of its own atomic add of s with TwoSum from the returned
+//             previous value and adds that error to c. float64: one 64-bit
+//             float atomic add.
+//   MIN/MAX   an adjacent (min, max) pair of order-preserving images (32-bit
+//             for 4-byte values); an atomic is issued only when the value
+//             improves the current extreme.
+// Rows are handled in batches: all lookups first, then all count updates,
+// all sum updates and all min/max updates, so that shared-memory latencies
+// overlap instead of forming one dependent chain per row.
+template <int DT> struct SImg { using U = uint32_t; };
+template <> struct SImg<AGG_I64> { using U = unsigned long long; };
+template <> struct SImg<AGG_F64> { using U = unsigned long long; };
+
+template <int DT>
+__device__ __forceinline__ typename SImg<DT>::U s_img(typename GV<DT>::T v) {
+  if (DT == AGG_I32) return (uint32_t)(int32_t)v ^ 0x80000000u;
+  if (DT == AGG_U32) return (uint32_t)v;
+  if (DT == AGG_F32) return img_f32((float)v);
+  if (DT == AGG_I64) return (unsigned long long)img_i64((int64_t)v);
+  return (unsigned long long)img_f64((double)v);
+}
+// shared image -> the 64-bit image kept in the global table (GV<DT>::img)
+template <int DT>
+__device__ __forceinline__ uint64_t g_img_of(typename SImg<DT>::U m) {
+  if (DT == AGG_I32) return img_i64((int64_t)(int32_t)((uint32_t)m ^ 0x80000000u));
+  if (DT == AGG_U32) return img_i64((int64_t)(uint32_t)m);
+  return (uint64_t)m;
+}
+
+template <int DT, bool MM>
+struct STab {
+  using U = typename SImg<DT>::U;
+  unsigned long long* sum;  // 64-bit word per slot (two u32 halves for integers / float32)
+  U* mm;                    // (min, max) image pairs
+  uint32_t* key1;           // key + 1, 0 = empty (16-byte aligned)
+  uint32_t* cnt;
+  int* used;
+  __device__ void carve(unsigned char* base, int S) {
+    sum = (unsigned long long*)base;
+    unsigned char* p = (unsigned char*)(sum + (S + 1));
+    p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    if (MM) {
+      mm = (U*)p;
+      p = (unsigned char*)(mm + 2 * (S + 1));
+      p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
+    }
+    key1 = (uint32_t*)p;
+    cnt = key1 + (S + 4);
+    used = (int*)(cnt + (S + 1));
+  }
+  __device__ void clear(int S) {
+    for (int i = threadIdx.x; i <= S; i += blockDim.x) {
+      sum[i] = 0;
+      if (MM) {
+        mm[2 * i] = (U)~(U)0;
+        mm[2 * i + 1] = 0;
+      }
+      cnt[i] = 0;
+    }
+    for (int i = threadIdx.x; i < S + 4; i += blockDim.x) key1[i] = 0;
+    if (threadIdx.x == 0) *used = 0;
+  }
+};
+
+template <int DT, bool MM>
+__host__ __device__ inline size_t stab_bytes(int S) {
+  const size_t img = (DT == AGG_I64 || DT == AGG_F64) ? 8 : 4;
+  return (size_t)(S + 1) * 8 + 16 + (MM ? 2 * img * (S + 1) + 16 : 0) + (size_t)(S + 4) * 4 + (size_t)(S + 1) * 4 +
+         16;
+}
+
+constexpr int kSmemBuckets = 4;  // buckets of 4 slots probed before a row spills
+
+// Shared-memory vector loads that are re-issued every time (values written by
+// other threads may change). A stale value is harmless for every use below:
+// keys only go from empty to set, minima only fall and maxima only rise.
+__device__ __forceinline__ uint4 lds_v4(const void* p) {
+  uint4 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ uint2 lds_v2(const void* p) {
+  uint2 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.volatile.shared.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
+  return v;
+}
+__device__ __forceinline__ ulonglong2 lds_v2_64(const void* p) {
+  ulonglong2 v;
+  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
+  asm volatile("ld.volatile.shared.v2.u64 {%0,%1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(a));
+  return v;
+}
+
+// Fast path: the key's slot if it sits in its home bucket, else -1 (one
+// 16-byte shared load, no branches on the data).
+template <int DT, bool MM>
+__device__ __forceinline__ int s_find_home(const STab<DT, MM>& t, int S, uint32_t key) {
+  const uint32_t k1 = key + 1;
+  const uint32_t b = fmix32(key) & (uint32_t)(S - 1) & ~3u;
+  const uint4 q = lds_v4(&t.key1[b]);
+  int j = -1;
+  j = q.w == k1 ? (int)b + 3 : j;
+  j = q.z == k1 ? (int)b + 2 : j;
+  j = q.y == k1 ? (int)b + 1 : j;
+  j = q.x == k1 ? (int)b : j;
+  return key == 0xFFFFFFFFu ? S : j;
+}
+
+// Slot of key in the shared table (inserting it if there is room), or -1.
+template <int DT, bool MM>
+__device__ __noinline__ int s_lookup(const STab<DT, MM>& t, int S, int cap, uint32_t key) {
+  if (key == 0xFFFFFFFFu) return S;
+  const uint32_t k1 = key + 1;
+  uint32_t b = fmix32(key) & (uint32_t)(S - 1) & ~3u;
+#pragma unroll 1
+  for (int p = 0; p < kSmemBuckets; ++p) {
+    uint4 q = lds_v4(&t.key1[b]);
+    if (q.x == k1) return (int)b;
+    if (q.y == k1) return (int)b + 1;
+    if (q.z == k1) return (int)b + 2;
+    if (q.w == k1) return (int)b + 3;
+    // claim an empty slot of this bucket; each failed claim fills a slot, so
+    // this loop runs at most 4 times
+#pragma unroll 1
+    for (int tries = 0; tries < 4; ++tries) {
+      const int e = q.x == 0 ? 0 : q.y == 0 ? 1 : q.z == 0 ? 2 : q.w == 0 ? 3 : -1;
+      if (e < 0) break;
+      if (*(volatile int*)t.used >= cap) return -1;  // full enough: no new keys
+      const uint32_t old = atomicCAS(&t.key1[b + e], 0u, k1);
+      if (old == 0u) {
+        atomicAdd(t.used, 1);
+        return (int)b + e;
+      }
+      if (old == k1) return (int)b + e;
+      q = lds_v4(&t.key1[b]);
+      if (q.x == k1) return (int)b;
+      if (q.y == k1) return (int)b + 1;
+      if (q.z == k1) return (int)b + 2;
+      if (q.w == k1) return (int)b + 3;
+    }
+    b = (b + 4) & (uint32_t)(S - 1);
+  }
+  return -1;
+}
+
+// Fold a row into the global table. MIN/MAX atomics are skipped when the
+// value does not improve the slot's current extreme.
+template <int DT, bool MM>
+__device__ __forceinline__ void g_add_row_cached(GSlot<MM>& s, typename GV<DT>::T v) {
+  atomicAdd(&s.cnt, 1u);
+  if (DT == AGG_F32 || DT == AGG_F64) {
+    atomicAdd((double*)&s.sum, (double)v);
+  } else {
+    atomicAdd(&s.sum, (unsigned long long)(int64_t)v);
+  }
+  if (MM) {
+    GSlot<true>& w = (GSlot<true>&)s;
+    const uint64_t m = GV<DT>::img(v);
+    if (~m > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~m);
+    if (m > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)m);
+  }
+}
+
+template <int DT, bool MM>
+__device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
+  GSlot<MM>* tab = (GSlot<MM>*)a.table;
+  const int64_t g = g_slot<MM>(tab, a.mask, key);
+  if (g < 0) {
+    *(volatile int*)a.status = kStatusFull;
+    return;
+  }
+  g_add_row_cached<DT, MM>(tab[g], v);
+}
+
+// Fold a batch of N rows (valid[r] false = skip).
+template <int DT, bool MM, bool SMEM, int N>
+__device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
+                                           const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
+  using T = typename GV<DT>::T;
+  using U = typename SImg<DT>::U;
+  if (!SMEM) {
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+      if (valid[r]) g_row<DT, MM>(a, key[r], val[r]);
+    return;
+  }
+  int j[N];
+#pragma unroll
+  for (int r = 0; r < N; ++r) j[r] = valid[r] ? s_find_home<DT, MM>(st, a.smem_slots, key[r]) : -2;
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+    if (j[r] == -1) j[r] = s_lookup<DT, MM>(st, a.smem_slots, a.smem_cap, key[r]);
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+    if (j[r] >= 0) atomicAdd(&st.cnt[j[r]], 1u);
+  if (DT == AGG_F32) {
+    float old[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+      if (j[r] >= 0) old[r] = atomicAdd((float*)&st.sum[j[r]], (float)val[r]);
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (j[r] >= 0) {
+        float t, e;
+        two_sum(old[r], (float)val[r], t, e);  // t is what the atomic stored; e its rounding error
+        if (e != 0.f) atomicAdd((float*)&st.sum[j[r]] + 1, e);
+      }
+    }
+  } else if (DT == AGG_F64) {
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+      if (j[r] >= 0) atomicAdd((double*)&st.sum[j[r]], (double)val[r]);
+  } else {
+    uint32_t old[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r)
+      if (j[r] >= 0) old[r] = atomicAdd((uint32_t*)&st.sum[j[r]], (uint32_t)(uint64_t)(int64_t)val[r]);
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (j[r] >= 0) {
+        const uint64_t u = (uint64_t)(int64_t)val[r];
+        const uint32_t lo = (uint32_t)u;
+        const uint32_t hi = (uint32_t)(u >> 32) + ((uint32_t)(old[r] + lo) < old[r] ? 1u : 0u);
+        if (hi) atomicAdd((uint32_t*)&st.sum[j[r]] + 1, hi);
+      }
+    }
+  }
+  if (MM) {
+    U cur_mn[N], cur_mx[N];
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (j[r] >= 0) {
+        if (sizeof(U) == 4) {
+          const uint2 q = lds_v2(&st.mm[2 * j[r]]);
+          cur_mn[r] = (U)q.x;
+          cur_mx[r] = (U)q.y;
+        } else {
+          const ulonglong2 q = lds_v2_64(&st.mm[2 * j[r]]);
+          cur_mn[r] = (U)q.x;
+          cur_mx[r] = (U)q.y;
+        }
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (j[r] >= 0) {
+        const U m = s_img<DT>(val[r]);
+        if (m < cur_mn[r]) atomicMin(&st.mm[2 * j[r]], m);
+        if (m > cur_mx[r]) atomicMax(&st.mm[2 * j[r] + 1], m);
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < N; ++r)
+    if (j[r] == -1) g_row<DT, MM>(a, key[r], val[r]);
+}
+
+template <class T>
+__device__ __forceinline__ void unpack4(const uint4& lo, const uint4& hi, T* v) {
+  if (sizeof(T) == 4) {
+    uint32_t w[4] = {lo.x, lo.y, lo.z, lo.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      uint32_t x = w[i];
+      memcpy(&v[i], &x, 4);
+    }
+  } else {
+    uint64_t w[4] = {((uint64_t)lo.y << 32) | lo.x, ((uint64_t)lo.w << 32) | lo.z, ((uint64_t)hi.y << 32) | hi.x,
+                     ((uint64_t)hi.w << 32) | hi.z};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) memcpy(&v[i], &w[i], 8);
+  }
+}
+
+// The build kernel. VEC: 16-byte vector loads of 4 keys and 4 values per quad,
+// two quads (8 rows) per thread per iteration, folded in batches of kBatch.
+constexpr int kBatch = 1;
+template <int DT, bool MM, bool SMEM, bool VEC>
+__global__ void gb_build(BuildArgs a) {
+  using T = typename GV<DT>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  STab<DT, MM> st;
+  if (SMEM) {
+    st.carve(smem, a.smem_slots);
+    st.clear(a.smem_slots);
+    __syncthreads();
+  }
+  const uint32_t* keys = a.keys;
+  const T* vals = (const T*)a.vals;
+  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  if (VEC) {
+    const int64_t nq = (a.n - a.head) / 4;  // full quads of rows
+    const int64_t tail0 = a.head + nq * 4;
+    {
+      uint32_t k1[1];
+      T v1[1];
+      bool ok1[1];
+      ok1[0] = gtid < a.head;
+      k1[0] = ok1[0] ? keys[gtid] : 0u;
+      v1[0] = ok1[0] ? vals[gtid] : T(0);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      ok1[0] = gtid < a.n - tail0;
+      k1[0] = ok1[0] ? keys[tail0 + gtid] : 0u;
+      v1[0] = ok1[0] ? vals[tail0 + gtid] : T(0);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+    }
+    const uint4* kq = (const uint4*)(keys + a.head);
+    const uint4* vq = (const uint4*)(vals + a.head);
+    constexpr int VPQ = sizeof(T) == 4 ? 1 : 2;  // 16-byte value vectors per quad
+    int it = 0;
+    for (int64_t q = gtid; q < nq; q += 2 * nthreads) {
+      const int64_t q2 = q + nthreads;
+      const bool has2 = q2 < nq;
+      const uint4 k0 = ld_stream_v4(kq + q);
+      const uint4 v0a = ld_stream_v4(vq + q * VPQ);
+      const uint4 v0b = VPQ == 2 ? ld_stream_v4(vq + q * VPQ + 1) : v0a;
+      uint4 k1 = make_uint4(0, 0, 0, 0), v1a = k1, v1b = k1;
+      if (has2) {
+        k1 = ld_stream_v4(kq + q2);
+        v1a = ld_stream_v4(vq + q2 * VPQ);
+        v1b = VPQ == 2 ? ld_stream_v4(vq + q2 * VPQ + 1) : v1a;
+      }
+      uint32_t key[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
+      T val[8];
+      unpack4<T>(v0a, v0b, val);
+      unpack4<T>(v1a, v1b, val + 4);
+#pragma unroll
+      for (int r0 = 0; r0 < 8; r0 += kBatch) {
+        uint32_t kb[kBatch];
+        T vb[kBatch];
+        bool ok[kBatch];
+#pragma unroll
+        for (int r = 0; r < kBatch; ++r) {
+          kb[r] = key[r0 + r];
+          vb[r] = val[r0 + r];
+          ok[r] = r0 + r < 4 || has2;
+        }
+        fold_batch<DT, MM, SMEM, kBatch>(a, st, kb, vb, ok);
+      }
+      if ((++it & 15) == 0 && *(volatile int*)a.status) break;  // table full: the build is redone
+    }
+  } else {
+    int it = 0;
+    for (int64_t i = gtid; i < a.n; i += nthreads) {
+      uint32_t k1[1] = {keys[i]};
+      T v1[1] = {vals[i]};
+      bool ok1[1] = {true};
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      if ((++it & 63) == 0 && *(volatile int*)a.status) break;
+    }
+  }
+  if (!SMEM) return;
+  __syncthreads();
+  // merge the block's shared table into the global table
+  GSlot<MM>* tab = (GSlot<MM>*)a.table;
+  const int S = a.smem_slots;
+  for (int j = threadIdx.x; j <= S; j += blockDim.x) {
+    const uint32_t c = st.cnt[j];
+    if (c == 0) continue;
+    const uint32_t key = j == S ? 0xFFFFFFFFu : st.key1[j] - 1;
+    const int64_t g = g_slot<MM>(tab, a.mask, key);
+    if (g < 0) {
+      *(volatile int*)a.status = kStatusFull;
+      continue;
+    }
+    GSlot<MM>& gs = tab[g];
+    atomicAdd(&gs.cnt, c);
+    const unsigned long long sv = st.sum[j];
+    if (DT == AGG_F32) {
+      const double d = (double)__uint_as_float((uint32_t)sv) + (double)__uint_as_float((uint32_t)(sv >> 32));
+      atomicAdd((double*)&gs.sum, d);
+    } else if (DT == AGG_F64) {
+      atomicAdd((double*)&gs.sum, __longlong_as_double((long long)sv));
+    } else {
+      atomicAdd(&gs.sum, sv);
+    }
+    if (MM) {
+      GSlot<true>& w = (GSlot<true>&)gs;
+      const uint64_t mn = g_img_of<DT>(st.mm[2 * j]), mx = g_img_of<DT>(st.mm[2 * j + 1]);
+      if (~mn > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~mn);
+      if (mx > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)mx);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Finalise.
+// ---------------------------------------------------------------------------
+struct OutArrays {
+  uint32_t* keys;
+  int64_t* count;
+  unsigned long long* sum;
+  unsigned long long* min;
+  unsigned long long* max;
+  double* avg;
+  int64_t* d;  // number of groups (device)
+};
+
+template <int DT, bool MM>
+__device__ __forceinline__ void write_group(const OutArrays& o, int64_t i, uint32_t key, const GSlot<MM>& s) {
+  const uint32_t c = s.cnt;
+  o.keys[i] = key;
+  o.count[i] = c;
+  const unsigned long long sv = s.sum;
+  o.sum[i] = sv;
+  double fsum;
+  if (DT == AGG_F32 || DT == AGG_F64) fsum = __longlong_as_double((long long)sv);
+  else fsum = (double)(long long)sv;
+  o.avg[i] = fsum / (double)c;
+  if (MM) {
+    const GSlot<true>& w = (const GSlot<true>&)s;
+    const uint64_t mn = ~w.minc, mx = w.mx;
+    if (DT == AGG_F32) {
+      o.min[i] = (unsigned long long)__double_as_longlong((double)f32_of_img((uint32_t)mn));
+      o.max[i] = (unsigned long long)__double_as_longlong((double)f32_of_img((uint32_t)mx));
+    } else if (DT == AGG_F64) {
+      o.min[i] = (unsigned long long)__double_as_longlong(f64_of_img(mn));
+      o.max[i] = (unsigned long long)__double_as_longlong(f64_of_img(mx));
+    } else {
+      o.min[i] = (unsigned long long)i64_of_img(mn);
+      o.max[i] = (unsigned long long)i64_of_img(mx);
+    }
+  }
+}
+
+template <bool MM>
+__device__ __forceinline__ bool occupied(const GSlot<MM>* tab, uint32_t mask, int64_t j) {
+  return j <= (int64_t)mask ? tab[j].key1 != 0 : tab[j].cnt != 0;
+}
+
+template <bool MM>
+__device__ __forceinline__ uint32_t key_of(const GSlot<MM>* tab, uint32_t mask, int64_t j) {
+  return j <= (int64_t)mask ? tab[j].key1 - 1 : 0xFFFFFFFFu;
+}
+
+// Small tables (at most kSmallRank occupied slots): after compaction, every
+// block loads all d distinct keys into shared memory and writes each of its
+// keys at its rank (the number of smaller keys); keys are distinct, so the
+// ranks are a permutation and the output is in ascending key order.
+constexpr int kSmallRank = 4097;
+constexpr int kRankThreads = 256;
+
+template <int DT, bool MM>
+__global__ void __launch_bounds__(kRankThreads) gb_rank_gather(const GSlot<MM>* tab, const uint32_t* ckeys,
+                                                               const uint32_t* cslot, OutArrays o) {
+  __shared__ uint32_t sk[kSmallRank];
+  const int d = (int)*(const unsigned long long*)o.d;
+  for (int t = threadIdx.x; t < d; t += kRankThreads) sk[t] = ckeys[t];
+  __syncthreads();
+  const int i = blockIdx.x * kRankThreads + threadIdx.x;
+  if (i >= d) return;
+  const uint32_t key = sk[i];
+  int rank = 0;
+#pragma unroll 8
+  for (int t = 0; t < d; ++t) rank += sk[t] < key ? 1 : 0;
+  write_group<DT, MM>(o, rank, key, tab[cslot[i]]);
+}
+
+// Large tables: compact occupied slots into (key, slot) pairs.
+template <bool MM>
+__global__ void gb_compact(const GSlot<MM>* tab, uint32_t mask, uint32_t* okeys, uint32_t* oslot,
+                           unsigned long long* counter) {
+  const int64_t nslots = (int64_t)mask + 2;
+  const int lane = threadIdx.x & 31;
+  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nslots; base += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t j = base + threadIdx.x;
+    const bool occ = j < nslots && occupied<MM>(tab, mask, j);
+    const uint32_t b = __ballot_sync(0xffffffffu, occ);
+    unsigned long long w0 = 0;
+    if (lane == 0 && b) w0 = atomicAdd(counter, (unsigned long long)__popc(b));
+    w0 = __shfl_sync(0xffffffffu, w0, 0);
+    if (occ) {
+      const unsigned long long pos = w0 + __popc(b & ((1u << lane) - 1u));
+      okeys[pos] = key_of<MM>(tab, mask, j);
+      oslot[pos] = (uint32_t)j;
+    }
+  }
+}
+
+template <int DT, bool MM>
+__global__ void gb_gather(const GSlot<MM>* tab, const uint32_t* skeys, const uint32_t* sslot, OutArrays o,
+                          int64_t cap) {
+  const int64_t d = *(const unsigned long long*)o.d;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d && i < cap;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    write_group<DT, MM>(o, i, skeys[i], tab[sslot[i]]);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+using KernelPtr = const void*;
+
+template <int DT, bool MM>
+static KernelPtr build_kernel(bool smem, bool vec) {
+  if (smem) return vec ? (KernelPtr)gb_build<DT, MM, true, true> : (KernelPtr)gb_build<DT, MM, true, false>;
+  return vec ? (KernelPtr)gb_build<DT, MM, false, true> : (KernelPtr)gb_build<DT, MM, false, false>;
+}
+
+static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec) {
+#define AGG_B(D) \
+  case D: return mm ? build_kernel<D, true>(smem, vec) : build_kernel<D, false>(smem, vec);
+  switch (dt) { AGG_B(AGG_I32) AGG_B(AGG_I64) AGG_B(AGG_U32) AGG_B(AGG_F32) AGG_B(AGG_F64) }
+#undef AGG_B
+  return nullptr;
+}
+
+template <int DT>
+static KernelPtr fin_small(bool mm) {
+  return mm ? (KernelPtr)gb_rank_gather<DT, true> : (KernelPtr)gb_rank_gather<DT, false>;
+}
+template <int DT>
+static KernelPtr fin_gather(bool mm) {
+  return mm ? (KernelPtr)gb_gather<DT, true> : (KernelPtr)gb_gather<DT, false>;
+}
+static KernelPtr pick_small(int dt, bool mm) {
+  switch (dt) {
+    case AGG_I32: return fin_small<AGG_I32>(mm);
+    case AGG_I64: return fin_small<AGG_I64>(mm);
+    case AGG_U32: return fin_small<AGG_U32>(mm);
+    case AGG_F32: return fin_small<AGG_F32>(mm);
+    case AGG_F64: return fin_small<AGG_F64>(mm);
+  }
+  return nullptr;
+}
+static KernelPtr pick_gather(int dt, bool mm) {
+  switch (dt) {
+    case AGG_I32: return fin_gather<AGG_I32>(mm);
+    case AGG_I64: return fin_gather<AGG_I64>(mm);
+    case AGG_U32: return fin_gather<AGG_U32>(mm);
+    case AGG_F32: return fin_gather<AGG_F32>(mm);
+    case AGG_F64: return fin_gather<AGG_F64>(mm);
+  }
+  return nullptr;
+}
+
+static size_t stab_bytes_dt(int dt, bool mm, int S) {
+#define AGG_SB(D) \
+  case D: return mm ? stab_bytes<D, true>(S) : stab_bytes<D, false>(S);
+  switch (dt) { AGG_SB(AGG_I32) AGG_SB(AGG_I64) AGG_SB(AGG_U32) AGG_SB(AGG_F32) AGG_SB(AGG_F64) }
+#undef AGG_SB
+  return 0;
+}
+
+// Resident blocks per SM of a kernel for (threads, dynamic smem), cached.
+static int occupancy(KernelPtr fn, int threads, size_t smem) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, KernelPtr, int, size_t>, int> cache;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  auto key = std::make_tuple(dev, fn, threads, smem);
+  auto it = cache.find(key);
+  if (it != cache.end()) return it->second;
+  if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  int b = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, threads, smem) != cudaSuccess || b < 1) b = 1;
+  cache[key] = b;
+  return b;
+}
+
+// Distinct-key estimate used for the rule and for table sizing.
+//  coverage = 1 - f1/m (Good's estimate of the probability mass of keys seen
+//  in the sample). When the sample covers >= 90% of the mass the population
+//  has few unseen keys and Chao1 (d + f1^2 / (2 f2), bias-corrected; Chao,
+//  Scand. J. Stat. 1984) estimates it well; otherwise use GEE, which errs high
+//  on low-cardinality columns but is the safer bound for sizing.
+double distinct_estimate(const float* f, bool* covered) {
+  const double m = std::min(std::exp2((double)f[F_LOG2N]), (double)kSketchSample);
+  const double d = (double)f[F_DISTINCT] * m, f1 = (double)f[F_F1] * m, f2 = (double)f[F_F2] * m;
+  const double coverage = m > 0 ? 1.0 - f1 / m : 1.0;
+  const double chao1 = d + f1 * (f1 - 1.0) / (2.0 * (f2 + 1.0));
+  *covered = coverage >= 0.9;
+  return *covered ? chao1 : std::max(chao1, std::exp2((double)f[F_LOG2_GEE]));
+}
+
+int rule_strategy(const float* f, uint32_t ops) {
+  // distinct keys few enough for a shared-memory table, or strong skew (the
+  // hot keys stay in shared memory): SMEM; otherwise one global table.
+  bool covered = false;
+  const double est = distinct_estimate(f, &covered);
+  const int cap = ops_minmax(ops) ? 1536 : 3072;  // 3/4 of the largest shared tables
+  if (est <= cap || f[F_TOP8] >= 0.05f) return AGG_STRAT_SMEM;
+  return AGG_STRAT_GLOBAL;
+}
+
+agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_groups** out) {
+  if (cap < 1) cap = 1;
+  const size_t a8 = (size_t)cap * 8;
+  const size_t kbytes = ((size_t)cap * 4 + 255) & ~size_t(255);
+  const size_t bytes = kbytes + 5 * ((a8 + 255) & ~size_t(255)) + 256;
+  void* blk = nullptr;
+  cudaError_t e = cudaMallocAsync(&blk, bytes, s);
+  if (e != cudaSuccess) {
+    set_error("result allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+    return AGG_ERR_OOM;
+  }
+  agg_groups* g = new agg_groups();
+  std::memset(g, 0, sizeof(*g));
+  GroupsPriv* p = new GroupsPriv();
+  p->block = blk;
+  cudaGetDevice(&p->device);
+  char* c = (char*)blk;
+  g->keys = (uint32_t*)c;
+  c += kbytes;
+  const size_t a8r = (a8 + 255) & ~size_t(255);
+  g->count = (int64_t*)c; c += a8r;
+  g->sum = c; c += a8r;
+  g->min = c; c += a8r;
+  g->max = c; c += a8r;
+  g->avg = (double*)c;
+  g->dtype = vdt;
+  g->ops = ops;
+  g->priv = p;
+  *out = g;
+  return AGG_OK;
+}
+
+struct HashPlan {
+  int strategy;     // AGG_STRAT_SMEM or AGG_STRAT_GLOBAL
+  int64_t slots;    // global main slots (power of two)
+  int smem_slots;   // shared slots (power of two) for SMEM
+  int threads;
+  int blocks_per_sm;
+};
+
+// One hash aggregation: a zeroed global table, any number of build launches
+// over row ranges (one for a device column, one per chunk for a host-fed
+// column), then one finalise into a result.
+class HashRun {
+ public:
+  HashRun(int vdt, uint32_t ops, const HashPlan& plan, cudaStream_t s)
+      : vdt_(vdt), ops_(ops), mm_(ops_minmax(ops)), plan_(plan), s_(s) {}
+  ~HashRun() {
+    if (mem_) cudaFreeAsync(mem_, s_);
+  }
+
+  agg_status init() {
+    const size_t slot = (size_t)gslot_bytes(mm_);
+    nslots_ = plan_.slots + 1;
+    small_ = nslots_ <= kSmallRank;
+    const size_t tbytes = (size_t)(nslots_ + 1) * slot;
+    status_off_ = (tbytes + 255) & ~size_t(255);
+    aux_off_ = status_off_ + 256;
+    size_t aux_bytes = small_ ? 2 * (size_t)nslots_ * 4 + 1024 : 4 * (size_t)nslots_ * 4 + 1024 + radix_tmp_bytes(nslots_);
+    AGG_CUDA_TRY(cudaMallocAsync(&mem_, aux_off_ + aux_bytes, s_));
+    AGG_CUDA_TRY(cudaMemsetAsync(mem_, 0, aux_off_, s_));
+    status_ = (int*)((char*)mem_ + status_off_);
+    counter_ = (unsigned long long*)((char*)mem_ + status_off_ + 64);
+    return AGG_OK;
+  }
+
+  // Enqueue the build over rows [0, n) of (keys, vals).
+  agg_status build(const uint32_t* keys, const void* vals, int64_t n) {
+    if (n <= 0) return AGG_OK;
+    const size_t es = dtype_size(vdt_);
+    const uintptr_t ka = (uintptr_t)keys, va = (uintptr_t)vals;
+    int64_t head = (int64_t)(((16 - (ka & 15)) & 15) / 4);
+    if (head > n) head = n;
+    const bool vec = ((va + (uintptr_t)head * es) & 15) == 0;
+    if (!vec) head = 0;
+    const bool use_smem = plan_.strategy == AGG_STRAT_SMEM;
+    BuildArgs a;
+    a.keys = keys;
+    a.vals = vals;
+    a.n = n;
+    a.head = head;
+    a.table = mem_;
+    a.mask = (uint32_t)(plan_.slots - 1);
+    a.smem_slots = use_smem ? plan_.smem_slots : 0;
+    a.smem_cap = use_smem ? (plan_.smem_slots * 3) / 4 : 0;
+    a.status = status_;
+    KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec);
+    const size_t smem = use_smem ? stab_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;
+    const int threads = plan_.threads;
+    int bps = occupancy(bk, threads, smem);
+    if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
+    const DeviceInfo& di = device_info();
+    const int64_t work = vec ? (n + 3) / 4 : n;
+    int64_t grid = (int64_t)di.sm_count * bps;
+    const int64_t need = (work + threads - 1) / threads;
+    if (need < grid) grid = need < 1 ? 1 : need;
+    void* args[] = {&a};
+    PhaseTimer pt(AGG_PHASE_BUILD, s_);
+    cudaError_t e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, smem, s_);
+    note_launch();
+    if (e != cudaSuccess) {
+      set_error("group-by build launch failed: %s", cudaGetErrorString(e));
+      return AGG_ERR_CUDA;
+    }
+    return AGG_OK;
+  }
+
+  // Finalise into a new result; TABLE_FULL (and no result) if the table overflowed.
+  agg_status finish(agg_groups** gout) {
+    *gout = nullptr;
+    agg_groups* g = nullptr;
+    agg_status st = groups_alloc(nslots_, vdt_, ops_, s_, &g);
+    if (st != AGG_OK) return st;
+    OutArrays o;
+    o.keys = g->keys;
+    o.count = g->count;
+    o.sum = (unsigned long long*)g->sum;
+    o.min = (unsigned long long*)g->min;
+    o.max = (unsigned long long*)g->max;
+    o.avg = g->avg;
+    o.d = (int64_t*)counter_;
+    uint32_t mask = (uint32_t)(plan_.slots - 1);
+    const DeviceInfo& di = device_info();
+    cudaError_t e;
+    PhaseTimer pt(AGG_PHASE_FINALIZE, s_);
+    if (small_) {
+      char* aux = (char*)mem_ + aux_off_;
+      uint32_t* ck = (uint32_t*)aux;
+      uint32_t* cs = ck + nslots_;
+      const int cgrid = (int)((nslots_ + 255) / 256);
+      if (mm_) gb_compact<true><<<cgrid, 256, 0, s_>>>((const GSlot<true>*)mem_, mask, ck, cs, counter_);
+      else gb_compact<false><<<cgrid, 256, 0, s_>>>((const GSlot<false>*)mem_, mask, ck, cs, counter_);
+      note_launch();
+      const int rgrid = (int)((nslots_ + kRankThreads - 1) / kRankThreads);
+      void* args[] = {&mem_, &ck, &cs, &o};
+      e = cudaLaunchKernel(pick_small(vdt_, mm_), dim3(rgrid), dim3(kRankThreads), args, 0, s_);
+      note_launch();
+    } else {
+      char* aux = (char*)mem_ + aux_off_;
+      uint32_t* k0 = (uint32_t*)aux;
+      uint32_t* s0 = k0 + nslots_;
+      uint32_t* k1 = s0 + nslots_;
+      uint32_t* s1 = k1 + nslots_;
+      void* rtmp = (void*)(((uintptr_t)(s1 + nslots_) + 255) & ~(uintptr_t)255);
+      int64_t cgrid = (nslots_ + 255) / 256;
+      if (cgrid > (int64_t)di.sm_count * 8) cgrid = (int64_t)di.sm_count * 8;
+      if (mm_) gb_compact<true><<<(unsigned)cgrid, 256, 0, s_>>>((const GSlot<true>*)mem_, mask, k0, s0, counter_);
+      else gb_compact<false><<<(unsigned)cgrid, 256, 0, s_>>>((const GSlot<false>*)mem_, mask, k0, s0, counter_);
+      note_launch();
+      uint32_t *sk = nullptr, *ss = nullptr;
+      st = radix_sort_pairs<uint32_t>(k0, s0, k1, s1, k0, s0, nslots_, (const int64_t*)counter_, 32, rtmp, s_,
+                                      &sk, &ss);
+      if (st != AGG_OK) {
+        agg_groups_free(g);
+        return st;
+      }
+      int64_t ggrid = cgrid;
+      int64_t cap = nslots_;
+      void* args[] = {&mem_, &sk, &ss, &o, &cap};
+      e = cudaLaunchKernel(pick_gather(vdt_, mm_), dim3((unsigned)ggrid), dim3(256), args, 0, s_);
+      note_launch();
+    }
+    if (e != cudaSuccess) {
+      set_error("group-by finalize launch failed: %s", cudaGetErrorString(e));
+      agg_groups_free(g);
+      return AGG_ERR_CUDA;
+    }
+    int64_t* hb = (int64_t*)stream_pinned(s_, 64, &st);
+    if (!hb) {
+      agg_groups_free(g);
+      return st;
+    }
+    cudaError_t e1 = cudaMemcpyAsync(hb, counter_, 8, cudaMemcpyDeviceToHost, s_);
+    cudaError_t e2 = cudaMemcpyAsync(hb + 1, status_, 4, cudaMemcpyDeviceToHost, s_);
+    cudaError_t e3 = cudaStreamSynchronize(s_);
+    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
+      set_error("group-by read-back failed: %s",
+                cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 != cudaSuccess ? e1 : e2)));
+      agg_groups_free(g);
+      return AGG_ERR_CUDA;
+    }
+    if (*(int*)(hb + 1) != 0) {
+      agg_groups_free(g);
+      set_error("global hash table of %lld slots is full", (long long)plan_.slots);
+      return AGG_ERR_TABLE_FULL;
+    }
+    g->num_groups = hb[0];
+    g->table_slots = plan_.slots;
+    g->smem_slots = plan_.strategy == AGG_STRAT_SMEM ? plan_.smem_slots : 0;
+    g->strategy = plan_.strategy;
+    *gout = g;
+    return AGG_OK;
+  }
+
+ private:
+  int vdt_;
+  uint32_t ops_;
+  bool mm_;
+  HashPlan plan_;
+  cudaStream_t s_;
+  void* mem_ = nullptr;
+  int64_t nslots_ = 0;
+  bool small_ = true;
+  size_t status_off_ = 0, aux_off_ = 0;
+  int* status_ = nullptr;
+  unsigned long long* counter_ = nullptr;
+};
+
+agg_status sort_groupby(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops, cudaStream_t s,
+                        agg_groups** gout);
+
+static int64_t table_slots_for(double est, int64_t n) {
+  double want = 2.0 * est;
+  if (want > 2.0 * (double)n) want = 2.0 * (double)n;
+  int64_t p = next_pow2((int64_t)std::ceil(want));
+  if (p < 1024) p = 1024;
+  if (p > (int64_t(1) << 31)) p = int64_t(1) << 31;
+  return p;
+}
+
+static int smem_slots_for(double est, bool mm) {
+  const int maxs = mm ? 2048 : 4096;
+  int64_t s = next_pow2((int64_t)std::ceil(2.0 * est));
+  if (s < 256) s = 256;
+  if (s > maxs) s = maxs;
+  return (int)s;
+}
+
+// Selector hooks (the learned selector and the autotuner live in their own units).
+int select_learned(const float* feat, bool* ok);
+agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                         const float* feat, cudaStream_t s, int* strategy, int* smem_slots, int64_t* table_slots);
+
+// Sketch the keys on the device and read the features back (one sync).
+static agg_status sketch_to_host(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
+                                 cudaStream_t s, float* feat) {
+  agg_status st = AGG_OK;
+  float* fd = (float*)stream_scratch(s, 4096, &st);
+  if (!fd) return st;
+  float* fdev = fd + 512;  // past the reduce ticket area
+  st = sketch_launch(keys, n, vdt, ops, offset, fdev, s);
+  if (st != AGG_OK) return st;
+  float* hb = (float*)stream_pinned(s, 256, &st);
+  if (!hb) return st;
+  AGG_CUDA_TRY(cudaMemcpyAsync(hb, fdev, F_COUNT * sizeof(float), cudaMemcpyDeviceToHost, s));
+  AGG_CUDA_TRY(cudaStreamSynchronize(s));
+  std::memcpy(feat, hb, F_COUNT * sizeof(float));
+  return AGG_OK;
+}
+
+// Rescale the size-dependent features of a sketch taken over the first
+// n_part rows to the whole column of n_total rows.
+static void rescale_features(float* f, int64_t n_part, int64_t n_total, uint32_t ops) {
+  const double m = (double)(n_part < kSketchSample ? n_part : kSketchSample);
+  if (m <= 0) return;
+  const DeviceInfo& di = device_info();
+  const double f1 = (double)f[F_F1] * m, d = (double)f[F_DISTINCT] * m;
+  double gee = std::sqrt((double)n_total / m) * f1 + (d - f1);
+  if (gee < 1.0) gee = 1.0;
+  if (gee > (double)n_total) gee = (double)n_total;
+  const double tb = 2.0 * gee * gslot_bytes(ops_minmax(ops));
+  f[F_LOG2N] = (float)std::log2((double)n_total);
+  f[F_LOG2_GEE] = (float)std::log2(gee);
+  f[F_SMEM_RATIO] = (float)std::log2(1.0 + tb / (double)di.smem_per_block_optin);
+  f[F_L2_RATIO] = (float)std::log2(1.0 + tb / (double)di.l2_bytes);
+}
+
+struct Choice {
+  int strategy;
+  HashPlan plan;
+};
+
+static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                         const agg_options& o, const float* feat, bool have_feat, cudaStream_t s, Choice* c) {
+  bool covered = false;
+  const double est = have_feat ? distinct_estimate(feat, &covered) : 1024.0;
+  int strategy = o.strategy;
+  int64_t tslots = o.table_slots;
+  int sslots = o.smem_slots;
+  if (strategy == AGG_STRAT_LEARNED) {
+    bool ok = false;
+    strategy = select_learned(feat, &ok);
+    if (!ok) strategy = rule_strategy(feat, ops);
+  } else if (strategy == AGG_STRAT_AUTOTUNE) {
+    agg_status st = autotune_pick(keys, vals, n, vdt, ops, feat, s, &strategy, &sslots, &tslots);
+    if (st != AGG_OK) return st;
+  } else if (strategy == AGG_STRAT_AUTO) {
+    strategy = have_feat ? rule_strategy(feat, ops) : AGG_STRAT_GLOBAL;
+  }
+  c->strategy = strategy;
+  c->plan.strategy = strategy;
+  // Global table: twice the estimate with a 25% margin when the sample covers
+  // the column, 16x otherwise (the sample of 4096 keys errs low on skewed,
+  // high-cardinality columns); an overflow regrows the table 4x.
+  c->plan.slots = tslots ? tslots : table_slots_for((covered ? 1.25 : 16.0) * est, n);
+  c->plan.smem_slots = sslots ? sslots : smem_slots_for(est, ops_minmax(ops));
+  c->plan.threads = o.block_threads ? o.block_threads : (strategy == AGG_STRAT_SMEM ? 512 : 256);
+  c->plan.blocks_per_sm = o.blocks_per_sm;
+  return AGG_OK;
+}
+
+static bool needs_sketch(const agg_options& o) {
+  return o.strategy == AGG_STRAT_AUTO || o.strategy == AGG_STRAT_LEARNED || o.strategy == AGG_STRAT_AUTOTUNE ||
+         (o.strategy != AGG_STRAT_SORT && o.table_slots == 0) || (o.strategy == AGG_STRAT_SMEM && o.smem_slots == 0);
+}
+
+// Run the hash plan over a device column, regrowing the table on overflow.
+static agg_status hash_device(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                              HashPlan plan, cudaStream_t s, agg_groups** g) {
+  int retries = 0;
+  for (;;) {
+    agg_status st;
+    {
+      HashRun run(vdt, ops, plan, s);
+      st = run.init();
+      if (st == AGG_OK) st = run.build(keys, vals, n);
+      if (st == AGG_OK) st = run.finish(g);
+    }
+    if (st == AGG_OK) {
+      (*g)->retries = retries;
+      return AGG_OK;
+    }
+    if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
+      return st;
+    ++retries;
+    plan.slots = std::min<int64_t>(plan.slots * 4, int64_t(1) << 31);
+  }
+}
+
+}  // namespace agg
+
+using namespace agg;
+
+static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                               const agg_options* opt, cudaStream_t s, agg_groups** out) {
+  agg_options o{};
+  if (opt) o = *opt;
+  float feat[F_COUNT] = {0};
+  bool have = false;
+  if (needs_sketch(o) && n > 0) {
+    agg_status st = sketch_to_host(keys, n, vdt, ops, o.sample_offset, s, feat);
+    if (st != AGG_OK) return st;
+    have = true;
+  }
+  Choice c;
+  agg_status st = choose(keys, vals, n, vdt, ops, o, feat, have, s, &c);
+  if (st != AGG_OK) return st;
+  agg_groups* g = nullptr;
+  if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g);
+  else st = hash_device(keys, vals, n, vdt, ops, c.plan, s, &g);
+  if (st != AGG_OK) return st;
+  std::memcpy(g->features, feat, sizeof(feat));
+  *out = g;
+  return AGG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Host-fed GROUP BY: chunks of keys and values are copied on a copy stream
+// into a ring of device buffers while the build of the previous chunk runs.
+// ---------------------------------------------------------------------------
+namespace agg {
+
+struct GbPipe {
+  static constexpr int kRing = 3;
+  cudaStream_t copy = nullptr;
+  cudaEvent_t ready[kRing] = {};
+  cudaEvent_t freed[kRing] = {};
+  bool ok = false;
+  std::mutex call_mu;
+};
+
+static GbPipe* gb_pipe(agg_status* st) {
+  static std::mutex mu;
+  static std::map<int, GbPipe*> pipes;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(mu);
+  GbPipe*& p = pipes[dev];
+  if (!p) p = new GbPipe();
+  *st = AGG_OK;
+  if (!p->ok) {
+    if (cudaStreamCreateWithFlags(&p->copy, cudaStreamNonBlocking) != cudaSuccess) {
+      set_error("cannot create copy stream");
+      *st = AGG_ERR_CUDA;
+      return p;
+    }
+    for (int i = 0; i < GbPipe::kRing; ++i) {
+      cudaEventCreateWithFlags(&p->ready[i], cudaEventDisableTiming);
+      cudaEventCreateWithFlags(&p->freed[i], cudaEventDisableTiming);
+    }
+    p->ok = true;
+  }
+  return p;
+}
+
+constexpr int64_t kHostChunkRows = int64_t(1) << 23;  // 8 Mi rows per chunk
+
+}  // namespace agg
+
+static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                                    const agg_options* opt, cudaStream_t s, agg_groups** out) {
+  agg_options o{};
+  if (opt) o = *opt;
+  agg_status st = AGG_OK;
+  GbPipe* pipe = gb_pipe(&st);
+  if (st != AGG_OK) return st;
+  std::lock_guard<std::mutex> lk(pipe->call_mu);
+  const size_t es = dtype_size(vdt);
+  const int64_t chunk = kHostChunkRows;
+  const size_t kbytes = (size_t)chunk * 4, vbytes = (size_t)chunk * es;
+  const size_t slot_bytes = ((kbytes + 255) & ~size_t(255)) + ((vbytes + 255) & ~size_t(255));
+  void* ring = nullptr;
+  AGG_CUDA_TRY(cudaMallocAsync(&ring, (size_t)GbPipe::kRing * slot_bytes, s));
+  struct Free {
+    void* p;
+    cudaStream_t s;
+    ~Free() { cudaFreeAsync(p, s); }
+  } ring_free{ring, s};
+  auto kbuf = [&](int b) { return (uint32_t*)((char*)ring + (size_t)b * slot_bytes); };
+  auto vbuf = [&](int b) { return (void*)((char*)ring + (size_t)b * slot_bytes + ((kbytes + 255) & ~size_t(255))); };
+  const int64_t nchunks = (n + chunk - 1) / chunk;
+  cudaEvent_t start_ev;
+  AGG_CUDA_TRY(cudaEventCreateWithFlags(&start_ev, cudaEventDisableTiming));
+  struct EvFree {
+    cudaEvent_t e;
+    ~EvFree() { cudaEventDestroy(e); }
+  } ev_free{start_ev};
+
+  // Enqueue the copy of chunk k into ring slot k % kRing (after its last use).
+  auto copy_chunk = [&](int64_t k, bool first_round) -> agg_status {
+    const int b = (int)(k % GbPipe::kRing);
+    const int64_t r0 = k * chunk;
+    const int64_t rows = std::min<int64_t>(chunk, n - r0);
+    if (!first_round || k >= GbPipe::kRing) cudaStreamWaitEvent(pipe->copy, pipe->freed[b], 0);  // slot reused
+    AGG_CUDA_TRY(cudaMemcpyAsync(kbuf(b), keys + r0, (size_t)rows * 4, cudaMemcpyHostToDevice, pipe->copy));
+    AGG_CUDA_TRY(cudaMemcpyAsync(vbuf(b), (const char*)vals + (size_t)r0 * es, (size_t)rows * es,
+                                 cudaMemcpyHostToDevice, pipe->copy));
+    cudaEventRecord(pipe->ready[b], pipe->copy);
+    return AGG_OK;
+  };
+
+  cudaEventRecord(start_ev, s);
+  cudaStreamWaitEvent(pipe->copy, start_ev, 0);  // the ring is ours once prior work on s is done
+  float feat[F_COUNT] = {0};
+  bool have = false;
+  if (n > 0) {
+    st = copy_chunk(0, true);
+    if (st != AGG_OK) return st;
+    if (needs_sketch(o)) {
+      cudaStreamWaitEvent(s, pipe->ready[0], 0);
+      const int64_t r0 = std::min<int64_t>(chunk, n);
+      st = sketch_to_host(kbuf(0), r0, vdt, ops, o.sample_offset, s, feat);
+      if (st != AGG_OK) return st;
+      rescale_features(feat, r0, n, ops);
+      have = true;
+    }
+  }
+  Choice c;
+  // the autotuner times candidates on a device column: give it the first chunk
+  st = choose(kbuf(0), vbuf(0), std::min<int64_t>(chunk, n), vdt, ops, o, feat, have, s, &c);
+  if (st != AGG_OK) return st;
+  agg_groups* g = nullptr;
+  if (c.strategy == AGG_STRAT_SORT) {
+    // the sort needs the whole column on the device
+    void* full = nullptr;
+    const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255);
+    AGG_CUDA_TRY(cudaMallocAsync(&full, kb + (size_t)n * es + 256, s));
+    Free full_free{full, s};
+    AGG_CUDA_TRY(cudaMemcpyAsync(full, keys, (size_t)n * 4, cudaMemcpyHostToDevice, s));
+    AGG_CUDA_TRY(cudaMemcpyAsync((char*)full + kb, vals, (size_t)n * es, cudaMemcpyHostToDevice, s));
+    cudaEventRecord(pipe->freed[0], s);
+    st = sort_groupby((const uint32_t*)full, (char*)full + kb, n, vdt, ops, s, &g);
+    if (st != AGG_OK) return st;
+  } else {
+    HashPlan plan = c.plan;
+    int retries = 0;
+    bool chunk0_copied = n > 0;
+    for (;;) {
+      {
+        HashRun run(vdt, ops, plan, s);
+        st = run.init();
+        // The copy of chunk k + 1 is enqueued before the build of chunk k, so
+        // the copy engine works one chunk ahead of the build.
+        for (int64_t k = 0; st == AGG_OK && k < nchunks; ++k) {
+          const int b = (int)(k % GbPipe::kRing);
+          if (k == 0 && !chunk0_copied) st = copy_chunk(0, retries == 0);
+          if (st == AGG_OK && k + 1 < nchunks) st = copy_chunk(k + 1, retries == 0);
+          if (st != AGG_OK) break;
+          cudaStreamWaitEvent(s, pipe->ready[b], 0);
+          const int64_t rows = std::min<int64_t>(chunk, n - k * chunk);
+          st = run.build(kbuf(b), vbuf(b), rows);
+          cudaEventRecord(pipe->freed[b], s);
+        }
+        if (st == AGG_OK) st = run.finish(&g);
+      }
+      if (st == AGG_OK) {
+        g->retries = retries;
+        break;
+      }
+      if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
+        return st;
+      ++retries;
+      plan.slots = std::min<int64_t>(plan.slots * 4, int64_t(1) << 31);
+      chunk0_copied = false;
+    }
+  }
+  std::memcpy(g->features, feat, sizeof(feat));
+  *out = g;
+  return AGG_OK;
+}
+
+static agg_status check_groupby_args(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                                     const agg_options* opt, agg_groups** out) {
+  AGG_CHECK_ARG(dtype_valid(vdt), "invalid dtype %d", vdt);
+  AGG_CHECK_ARG(ops != 0 && (ops & ~(uint32_t)AGG_ALL) == 0, "invalid ops mask 0x%x", ops);
+  AGG_CHECK_ARG(n >= 0 && n <= 0xFFFFFFFFll, "invalid row count %lld (group-by needs n < 2^32)", (long long)n);
+  AGG_CHECK_ARG(n == 0 || (keys && vals), "null key or value pointer");
+  AGG_CHECK_ARG(out != nullptr, "null result pointer");
+  AGG_CHECK_ARG(((uintptr_t)keys & 3) == 0, "key pointer not 4-byte aligned");
+  AGG_CHECK_ARG(((uintptr_t)vals % dtype_size(vdt)) == 0, "value pointer not aligned to its element size");
+  if (opt) {
+    AGG_CHECK_ARG(opt->strategy >= AGG_STRAT_AUTO && opt->strategy <= AGG_STRAT_AUTOTUNE, "invalid strategy %d",
+                  opt->strategy);
+    AGG_CHECK_ARG(opt->table_slots == 0 || (opt->table_slots >= 2 && (opt->table_slots & (opt->table_slots - 1)) == 0 &&
+                                             opt->table_slots <= (int64_t(1) << 31)),
+                  "table_slots must be 0 or a power of two <= 2^31");
+    AGG_CHECK_ARG(opt->smem_slots == 0 || (opt->smem_slots >= 64 && opt->smem_slots <= 8192 &&
+                                            (opt->smem_slots & (opt->smem_slots - 1)) == 0),
+                  "smem_slots must be 0 or a power of two in [64, 8192]");
+    AGG_CHECK_ARG(opt->block_threads == 0 || (opt->block_threads >= 64 && opt->block_threads <= 1024 &&
+                                               opt->block_threads % 32 == 0),
+                  "block_threads must be 0 or a multiple of 32 in [64, 1024]");
+    AGG_CHECK_ARG(opt->blocks_per_sm >= 0, "blocks_per_sm must be >= 0");
+  }
+  return AGG_OK;
+}
+
+extern "C" agg_status agg_groupby(const uint32_t* keys_dev, const void* vals_dev, int64_t n, agg_dtype vdtype,
+                                  uint32_t ops, const agg_options* opt, agg_groups** out, void* stream) {
+  clear_error();
+  agg_status st = check_groupby_args(keys_dev, vals_dev, n, vdtype, ops, opt, out);
+  if (st != AGG_OK) return st;
+  *out = nullptr;
+  return groupby_impl(keys_dev, vals_dev, n, vdtype, ops, opt, (cudaStream_t)stream, out);
+}
+
+extern "C" agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* count, void* sum, void* min,
+                                         void* max, double* avg) {
+  clear_error();
+  AGG_CHECK_ARG(g != nullptr, "null result");
+  const int64_t d = g->num_groups;
+  if (d == 0) return AGG_OK;
+  if (keys) AGG_CUDA_TRY(cudaMemcpy(keys, g->keys, (size_t)d * 4, cudaMemcpyDeviceToHost));
+  if (count) AGG_CUDA_TRY(cudaMemcpy(count, g->count, (size_t)d * 8, cudaMemcpyDeviceToHost));
+  if (sum) AGG_CUDA_TRY(cudaMemcpy(sum, g->sum, (size_t)d * 8, cudaMemcpyDeviceToHost));
+  if (min) AGG_CUDA_TRY(cudaMemcpy(min, g->min, (size_t)d * 8, cudaMemcpyDeviceToHost));
+  if (max) AGG_CUDA_TRY(cudaMemcpy(max, g->max, (size_t)d * 8, cudaMemcpyDeviceToHost));
+  if (avg) AGG_CUDA_TRY(cudaMemcpy(avg, g->avg, (size_t)d * 8, cudaMemcpyDeviceToHost));
+  return AGG_OK;
+}
+
+extern "C" void agg_groups_free(agg_groups* g) {
+  if (!g) return;
+  GroupsPriv* p = (GroupsPriv*)g->priv;
+  if (p) {
+    int cur = 0;
+    cudaGetDevice(&cur);
+    if (cur != p->device) cudaSetDevice(p->device);
+    cudaDeviceSynchronize();  // the block may still be in use by queued work
+    cudaFree(p->block);
+    if (cur != p->device) cudaSetDevice(cur);
+    delete p;
+  }
+  delete g;
+}
+
+extern "C" agg_status agg_groupby_host(const uint32_t* keys_host, const void* vals_host, int64_t n, agg_dtype vdtype,
+                                       uint32_t ops, const agg_options* opt, agg_groups** out, void* stream) {
+  clear_error();
+  agg_status st = check_groupby_args(keys_host, vals_host, n, vdtype, ops, opt, out);
+  if (st != AGG_OK) return st;
+  *out = nullptr;
+  return groupby_host_impl(keys_host, vals_host, n, vdtype, ops, opt, (cudaStream_t)stream, out);
+}

@@ -1,0 +1,37 @@
+// Internal interfaces between the GROUP BY translation units.
+#pragma once
+
+#include "common.cuh"
+
+namespace agg {
+
+// Feature indices of the key sketch (see agg_sketch in agg.h).
+enum Feature {
+  F_LOG2N = 0, F_VBYTES, F_NOPS, F_FP, F_DISTINCT, F_F1, F_F2, F_TOP1, F_TOP8, F_SLOPE, F_ENTROPY,
+  F_ADJ_EQ, F_LOG2_GEE, F_SMEM_RATIO, F_L2_RATIO, F_LOG2_RANGE, F_COUNT
+};
+constexpr int kSketchSample = 4096;
+
+// Launch the sketch kernel (one block) writing F_COUNT floats to feat_dev.
+agg_status sketch_launch(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset, float* feat_dev,
+                         cudaStream_t s);
+
+// Slot sizes of the global hash table.
+inline int gslot_bytes(bool minmax) { return minmax ? 32 : 16; }
+inline bool ops_minmax(uint32_t ops) { return ops & (AGG_MIN | AGG_MAX); }
+
+// Strategy choice without a learned model: a rule on the sketch.
+int rule_strategy(const float* feat, uint32_t ops);
+// Distinct-key estimate from the sketch (*covered: the sample covers >= 90% of the mass).
+double distinct_estimate(const float* feat, bool* covered);
+
+// Library-private part of an agg_groups.
+struct GroupsPriv {
+  void* block = nullptr;  // one device allocation holding every output array
+  int device = 0;
+};
+
+// Allocate a result with capacity for `cap` rows of every output array.
+agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_groups** out);
+
+}  // namespace agg

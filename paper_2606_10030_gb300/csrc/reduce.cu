@@ -382,7 +382,9 @@ extern "C" agg_status agg_reduce(const void* col_dev, int64_t n, agg_dtype dtype
   int64_t count = n;
   void* args[] = {(void*)&col_dev, (void*)&n, (void*)&head, (void*)&parts, (void*)&part_base,
                   (void*)&ticket, (void*)&out_dev, (void*)&ops, (void*)&count, (void*)&finalize};
+  PhaseTimer pt(AGG_PHASE_SCAN, s);
   AGG_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, 0, s));
+  note_launch();
   return AGG_OK;
 }
 
@@ -478,11 +480,13 @@ extern "C" agg_status agg_reduce_host(const void* col_host, int64_t n, agg_dtype
     void* args[] = {(void*)&buf, (void*)&rows, (void*)&zero, (void*)&parts, (void*)&base,
                     (void*)&no_ticket, (void*)&no_out, (void*)&ops, (void*)&n, (void*)&fin};
     AGG_CUDA_TRY(cudaLaunchKernel(fn, dim3(g), dim3(kBlock), args, 0, s));
+    note_launch();
     cudaEventRecord(pipe.freed[b], s);
   }
   int np = scan ? (int)nparts : 0;
   void* margs[] = {(void*)&parts, (void*)&np, (void*)&out_dev, (void*)&ops, (void*)&n};
   AGG_CUDA_TRY(cudaLaunchKernel(pick_merge(dtype), dim3(1), dim3(kBlock), margs, 0, s));
+  note_launch();
   AGG_CUDA_TRY(cudaMemcpyAsync(out_host, out_dev, sizeof(agg_scalar), cudaMemcpyDeviceToHost, s));
   cudaError_t e = cudaStreamSynchronize(s);
   cudaEventDestroy(start_ev);
@@ -571,5 +575,6 @@ extern "C" agg_status agg_reduce_noalloc(const void* col_dev, int64_t n, agg_dty
   void* args[] = {(void*)&col_dev, (void*)&n, (void*)&head, (void*)&parts, (void*)&part_base,
                   (void*)&ticket, (void*)&out_dev, (void*)&ops, (void*)&count, (void*)&finalize};
   AGG_CUDA_TRY(cudaLaunchKernel(fn, dim3(grid), dim3(kBlock), args, 0, s));
+  note_launch();
   return AGG_OK;
 }

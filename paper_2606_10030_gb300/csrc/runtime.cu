@@ -1,6 +1,8 @@
 // Host runtime of the library: last-error state, per-device properties and
 // the per-(device, stream) scratch cache used by the scan kernels.
+#include <atomic>
 #include <map>
+#include <vector>
 #include <mutex>
 #include <utility>
 
@@ -82,7 +84,119 @@ void* stream_scratch(cudaStream_t s, size_t bytes, agg_status* st) {
   return p;
 }
 
+// A small pinned host buffer per (device, stream) for reading a few result
+// words back without a pageable copy.
+void* stream_pinned(cudaStream_t s, size_t bytes, agg_status* st) {
+  static std::map<std::pair<int, cudaStream_t>, Scratch> pinned;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::lock_guard<std::mutex> lk(g_mu);
+  Scratch& sc = pinned[{dev, s}];
+  if (sc.bytes >= bytes) {
+    *st = AGG_OK;
+    return sc.ptr;
+  }
+  size_t want = bytes < 4096 ? 4096 : bytes;
+  void* p = nullptr;
+  cudaError_t e = cudaHostAlloc(&p, want, cudaHostAllocPortable);
+  if (e != cudaSuccess) {
+    set_error("pinned allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
+    *st = AGG_ERR_OOM;
+    return nullptr;
+  }
+  if (sc.ptr) {
+    cudaStreamSynchronize(s);
+    cudaFreeHost(sc.ptr);
+  }
+  sc.ptr = p;
+  sc.bytes = want;
+  *st = AGG_OK;
+  return p;
+}
+
+// ---------------------------------------------------------------------------
+// Instrumentation.
+// ---------------------------------------------------------------------------
+namespace {
+std::atomic<int64_t> g_launches{0};
+std::atomic<bool> g_profile{false};
+std::mutex g_prof_mu;
+struct Pending {
+  int phase;
+  cudaEvent_t a, b;
+};
+std::vector<Pending> g_pending;
+std::vector<cudaEvent_t> g_event_pool;
+double g_ms[AGG_PHASES] = {0};
+int64_t g_calls[AGG_PHASES] = {0};
+
+cudaEvent_t take_event() {
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    if (!g_event_pool.empty()) {
+      cudaEvent_t e = g_event_pool.back();
+      g_event_pool.pop_back();
+      return e;
+    }
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+}  // namespace
+
+void note_launch(int k) { g_launches.fetch_add(k, std::memory_order_relaxed); }
+
+PhaseTimer::PhaseTimer(int ph, cudaStream_t st) : phase(ph), s(st) {
+  if (!g_profile.load(std::memory_order_relaxed)) return;
+  a = take_event();
+  if (a) cudaEventRecord(a, s);
+}
+
+PhaseTimer::~PhaseTimer() {
+  if (!a) return;
+  cudaEvent_t b = take_event();
+  if (!b) return;
+  cudaEventRecord(b, s);
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  g_pending.push_back({phase, a, b});
+}
+
 }  // namespace agg
+
+extern "C" int64_t agg_launch_count(void) { return agg::g_launches.load(); }
+
+extern "C" void agg_profile_enable(int on) { agg::g_profile.store(on != 0); }
+
+extern "C" agg_status agg_profile_read(double* ms, int64_t* calls) {
+  using namespace agg;
+  std::vector<Pending> pend;
+  {
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    pend.swap(g_pending);
+  }
+  agg_status st = AGG_OK;
+  for (const Pending& p : pend) {
+    float t = 0.f;
+    if (cudaEventSynchronize(p.b) != cudaSuccess || cudaEventElapsedTime(&t, p.a, p.b) != cudaSuccess) {
+      set_error("profile event failed");
+      st = AGG_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_prof_mu);
+    g_ms[p.phase] += t;
+    g_calls[p.phase] += 1;
+    g_event_pool.push_back(p.a);
+    g_event_pool.push_back(p.b);
+  }
+  std::lock_guard<std::mutex> lk(g_prof_mu);
+  for (int i = 0; i < AGG_PHASES; ++i) {
+    if (ms) ms[i] = g_ms[i];
+    if (calls) calls[i] = g_calls[i];
+    g_ms[i] = 0;
+    g_calls[i] = 0;
+  }
+  return st;
+}
 
 extern "C" const char* agg_last_error(void) { return agg::g_last_error.c_str(); }
 

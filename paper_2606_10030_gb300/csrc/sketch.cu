@@ -1,0 +1,201 @@
+// Key sketch (step a10): 16 features of a strided sample of m = min(n, 4096)
+// keys, computed by one block. The strategy selectors (the rule and the MLP)
+// read them; the global table is sized from the GEE distinct-count estimate
+// (Charikar, Chaudhuri, Motwani and Narasayya, PODS 2000).
+#include <cmath>
+#include <cstdint>
+
+#include "groupby.cuh"
+
+namespace agg {
+
+constexpr int kSketchThreads = 1024;
+constexpr int kSketchSlots = 2 * kSketchSample;  // hash slots for the sample (load <= 1/2)
+constexpr size_t kSketchSmem = (size_t)kSketchSlots * 8 + (size_t)kSketchSlots * 4 + (kSketchSample + 1) * 4 + 64 * 4;
+
+// Block-wide sum in a fixed order (deterministic).
+__device__ double block_sum_d(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  __syncthreads();
+  if (l == 0) red[w] = v;
+  __syncthreads();
+  double t = 0;
+  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  __syncthreads();
+  return t;
+}
+
+// One block. The sample's keys are counted in a shared-memory hash table
+// (64-bit slots holding key << 1 | 1, so every key value is representable),
+// their counts histogrammed, and the 32 largest counts read off the histogram
+// from the top by one warp.
+__global__ void __launch_bounds__(kSketchThreads) sketch_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                                                int vbytes, int nops, int fp, int slot_bytes,
+                                                                uint64_t offset, double smem_bytes, double l2_bytes,
+                                                                float* __restrict__ feat) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  unsigned long long* slot = (unsigned long long*)sm;            // kSketchSlots
+  uint32_t* cnt = (uint32_t*)(slot + kSketchSlots);              // kSketchSlots
+  uint32_t* hist = cnt + kSketchSlots;                           // kSketchSample + 1
+  uint32_t* top = hist + kSketchSample + 1;                      // 32 (+ pad)
+  __shared__ double red[32];
+  __shared__ unsigned int s_d, s_f1, s_f2, s_adj, s_kmin, s_kmax, s_maxc, s_ntop;
+  const int tid = threadIdx.x;
+  for (int i = tid; i < kSketchSlots; i += kSketchThreads) {
+    slot[i] = 0;
+    cnt[i] = 0;
+  }
+  for (int i = tid; i <= kSketchSample; i += kSketchThreads) hist[i] = 0;
+  if (tid == 0) {
+    s_d = s_f1 = s_f2 = s_adj = s_maxc = s_ntop = 0;
+    s_kmin = 0xFFFFFFFFu;
+    s_kmax = 0;
+  }
+  const int m = (int)(n < kSketchSample ? n : kSketchSample);
+  const int64_t stride = m > 0 ? n / m : 1;
+  const uint64_t off = n > 0 ? offset % (uint64_t)n : 0;
+  __syncthreads();
+  constexpr int kPer = kSketchSample / kSketchThreads;  // sampled keys per thread
+  uint32_t kk[kPer], nx[kPer];
+  bool have[kPer], hasnx[kPer];
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {  // issue every load before using any
+    const int j = tid + u * kSketchThreads;
+    have[u] = j < m;
+    hasnx[u] = false;
+    kk[u] = 0;
+    nx[u] = 0;
+    if (have[u]) {
+      // (offset + j * stride) mod n, with off + j * stride < 2n
+      const uint64_t q = off + (uint64_t)j * (uint64_t)stride;
+      const int64_t p = (int64_t)(q >= (uint64_t)n ? q - (uint64_t)n : q);
+      kk[u] = keys[p];
+      hasnx[u] = p + 1 < n;
+      if (hasnx[u]) nx[u] = keys[p + 1];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kPer; ++u) {
+    if (!have[u]) continue;
+    const uint32_t k = kk[u];
+    if (hasnx[u] && nx[u] == k) atomicAdd(&s_adj, 1u);
+    atomicMin(&s_kmin, k);
+    atomicMax(&s_kmax, k);
+    const unsigned long long tag = ((unsigned long long)k << 1) | 1ull;
+    uint32_t h = fmix32(k) & (kSketchSlots - 1);
+    for (;;) {  // at most m < kSketchSlots occupied slots: an empty or matching one exists
+      unsigned long long cur = *(volatile unsigned long long*)&slot[h];
+      if (cur == 0) cur = atomicCAS(&slot[h], 0ull, tag);
+      if (cur == 0 || cur == tag) break;
+      h = (h + 1) & (kSketchSlots - 1);
+    }
+    atomicAdd(&cnt[h], 1u);
+  }
+  __syncthreads();
+  double ent = 0.0;
+  const float mf = (float)(m > 0 ? m : 1);
+  for (int i = tid; i < kSketchSlots; i += kSketchThreads) {
+    const uint32_t c = cnt[i];
+    if (c == 0) continue;
+    atomicAdd(&s_d, 1u);
+    if (c == 1) atomicAdd(&s_f1, 1u);
+    if (c == 2) atomicAdd(&s_f2, 1u);
+    atomicAdd(&hist[c], 1u);
+    atomicMax(&s_maxc, c);
+    const float p = (float)c / mf;
+    ent -= (double)(p * logf(p));
+  }
+  ent = block_sum_d(ent, red);
+  const int R = (int)(s_d < 32 ? s_d : 32);
+  if (tid < 32) {  // warp 0: the R largest counts, in descending order
+    const int lane = tid;
+    int got = 0;
+    for (int base = (int)s_maxc; base >= 1 && got < R; base -= 32) {
+      const int c = base - lane;
+      const uint32_t v = c >= 1 ? hist[c] : 0u;
+      uint32_t b = __ballot_sync(0xffffffffu, v != 0);
+      while (b && got < R) {
+        const int src = __ffs(b) - 1;
+        b &= b - 1;
+        const int mult = (int)__shfl_sync(0xffffffffu, v, src);
+        const int take = mult < R - got ? mult : R - got;
+        if (lane < take) top[got + lane] = (uint32_t)(base - src);
+        got += take;
+      }
+    }
+  }
+  __syncthreads();
+  if (tid != 0) return;
+  const double md = m > 0 ? (double)m : 1.0;
+  const double d = (double)s_d, f1 = (double)s_f1, f2 = (double)s_f2;
+  float* f = feat;
+  f[F_LOG2N] = n > 0 ? (float)log2((double)n) : 0.f;
+  f[F_VBYTES] = (float)vbytes;
+  f[F_NOPS] = (float)nops;
+  f[F_FP] = (float)fp;
+  if (m == 0) {
+    for (int i = F_DISTINCT; i < F_COUNT; ++i) f[i] = 0.f;
+    return;
+  }
+  f[F_DISTINCT] = (float)(d / md);
+  f[F_F1] = (float)(f1 / md);
+  f[F_F2] = (float)(f2 / md);
+  f[F_TOP1] = (float)((double)top[0] / md);
+  double top8 = 0;
+  for (int r = 0; r < 8 && r < R; ++r) top8 += (double)top[r];
+  f[F_TOP8] = (float)(top8 / md);
+  double slope = 0.0;
+  if (R >= 2) {
+    double sx = 0, sy = 0, sxx = 0, sxy = 0;
+    for (int r = 1; r <= R; ++r) {
+      const double x = (double)logf((float)r), y = (double)logf((float)top[r - 1]);
+      sx += x; sy += y; sxx += x * x; sxy += x * y;
+    }
+    slope = (R * sxy - sx * sy) / (R * sxx - sx * sx);
+  }
+  f[F_SLOPE] = (float)slope;
+  f[F_ENTROPY] = m > 1 ? (float)(ent / (double)logf(mf)) : 0.f;
+  f[F_ADJ_EQ] = (float)((double)s_adj / md);
+  double gee = sqrt((double)n / md) * f1 + (d - f1);
+  if (gee < 1.0) gee = 1.0;
+  if (gee > (double)n) gee = (double)n;
+  f[F_LOG2_GEE] = (float)log2(gee);
+  const double tbytes = 2.0 * gee * (double)slot_bytes;
+  f[F_SMEM_RATIO] = (float)log2(1.0 + tbytes / smem_bytes);
+  f[F_L2_RATIO] = (float)log2(1.0 + tbytes / l2_bytes);
+  f[F_LOG2_RANGE] = (float)log2((double)(s_kmax - s_kmin) + 1.0);
+}
+
+agg_status sketch_launch(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset, float* feat_dev,
+                         cudaStream_t s) {
+  const DeviceInfo& di = device_info();
+  static bool attr_set[64] = {};
+  if (di.device >= 0 && di.device < 64 && !attr_set[di.device]) {
+    AGG_CUDA_TRY(cudaFuncSetAttribute(sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem));
+    attr_set[di.device] = true;
+  }
+  PhaseTimer pt(AGG_PHASE_SKETCH, s);
+  note_launch();
+  sketch_kernel<<<1, kSketchThreads, kSketchSmem, s>>>(keys, n, (int)dtype_size(vdt), __builtin_popcount(ops),
+                                             dtype_is_fp(vdt) ? 1 : 0, gslot_bytes(ops_minmax(ops)), offset,
+                                             (double)di.smem_per_block_optin, (double)di.l2_bytes, feat_dev);
+  AGG_CUDA_TRY(cudaGetLastError());
+  return AGG_OK;
+}
+
+}  // namespace agg
+
+using namespace agg;
+
+extern "C" agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uint32_t ops,
+                                 uint64_t sample_offset, float* features_dev, void* stream) {
+  clear_error();
+  AGG_CHECK_ARG(dtype_valid(vdtype), "invalid dtype %d", (int)vdtype);
+  AGG_CHECK_ARG(ops != 0 && (ops & ~(uint32_t)AGG_ALL) == 0, "invalid ops mask 0x%x", ops);
+  AGG_CHECK_ARG(n >= 0, "invalid row count");
+  AGG_CHECK_ARG(n == 0 || keys_dev != nullptr, "null key pointer");
+  AGG_CHECK_ARG(features_dev != nullptr, "null features pointer");
+  return sketch_launch(keys_dev, n, vdtype, ops, sample_offset, features_dev, (cudaStream_t)stream);
+}

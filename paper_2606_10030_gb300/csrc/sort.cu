@@ -1,0 +1,282 @@
+// Exclusive scan and stable LSD radix sort (8-bit digits) for GROUP BY.
+//
+// One radix pass = three launches:
+//   radix_hist     per 4096-row tile, a 256-bin digit histogram, stored
+//                  digit-major (digit * ntiles + tile) so that one exclusive
+//                  scan of the whole array gives every (digit, tile) its
+//                  global output offset;
+//   scan           device-wide exclusive scan of those counts;
+//   radix_scatter  per tile: stable rank of every row among rows with the
+//                  same digit (warp match + per-warp running counts), staging
+//                  of the tile in shared memory in digit order, then coalesced
+//                  writes of each digit's run to its global offset.
+#include "sort.cuh"
+
+namespace agg {
+
+// ---------------------------------------------------------------------------
+// Exclusive scan of uint32.
+// ---------------------------------------------------------------------------
+constexpr int kScanThreads = 256;
+constexpr int kScanItems = 16;
+constexpr int kScanTile = kScanThreads * kScanItems;
+
+__device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
+  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    if (lane < kScanThreads / 32) warp_sums[lane] = s;
+  }
+  __syncthreads();
+  uint32_t base = w ? warp_sums[w - 1] : 0;
+  if (total) *total = warp_sums[kScanThreads / 32 - 1];
+  uint32_t r = base + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void __launch_bounds__(kScanThreads) scan_reduce(const uint32_t* in, int64_t n, uint32_t* sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile;
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    int64_t j = base + (int64_t)i * kScanThreads + threadIdx.x;
+    if (j < n) s += in[j];
+  }
+  uint32_t tot;
+  block_exclusive_scan(s, &tot);
+  if (threadIdx.x == 0) sums[blockIdx.x] = tot;
+}
+
+// Single block: exclusive scan of the block sums (any count), total to *total.
+__global__ void __launch_bounds__(kScanThreads) scan_sums(uint32_t* sums, int64_t nb, uint32_t* total) {
+  uint32_t carry = 0;
+  for (int64_t b0 = 0; b0 < nb; b0 += kScanThreads) {
+    int64_t j = b0 + threadIdx.x;
+    uint32_t v = j < nb ? sums[j] : 0;
+    uint32_t t;
+    uint32_t e = block_exclusive_scan(v, &t);
+    if (j < nb) sums[j] = carry + e;
+    carry += t;
+  }
+  if (threadIdx.x == 0 && total) *total = carry;
+}
+
+// Per tile: exclusive scan of kScanItems consecutive values per thread (blocked).
+__global__ void __launch_bounds__(kScanThreads) scan_apply(const uint32_t* in, uint32_t* out, int64_t n,
+                                                           const uint32_t* sums) {
+  const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+  uint32_t v[kScanItems];
+  uint32_t s = 0;
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    int64_t j = base + i;
+    v[i] = j < n ? in[j] : 0;
+    s += v[i];
+  }
+  uint32_t e = block_exclusive_scan(s, nullptr) + sums[blockIdx.x];
+#pragma unroll
+  for (int i = 0; i < kScanItems; ++i) {
+    int64_t j = base + i;
+    if (j < n) out[j] = e;
+    e += v[i];
+  }
+}
+
+size_t scan_tmp_bytes(int64_t n) {
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  return (size_t)(nb > 0 ? nb : 1) * sizeof(uint32_t) + 256;
+}
+
+agg_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, void* tmp,
+                              cudaStream_t s) {
+  int64_t nb = (n + kScanTile - 1) / kScanTile;
+  uint32_t* sums = (uint32_t*)tmp;
+  if (nb == 0) {
+    if (total_dev) AGG_CUDA_TRY(cudaMemsetAsync(total_dev, 0, sizeof(uint32_t), s));
+    return AGG_OK;
+  }
+  scan_reduce<<<(unsigned)nb, kScanThreads, 0, s>>>(in, n, sums);
+  scan_sums<<<1, kScanThreads, 0, s>>>(sums, nb, total_dev);
+  scan_apply<<<(unsigned)nb, kScanThreads, 0, s>>>(in, out, n, sums);
+  note_launch(3);
+  AGG_CUDA_TRY(cudaGetLastError());
+  return AGG_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Radix sort.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int64_t rows_of(int64_t n_cap, const int64_t* n_dev) {
+  if (!n_dev) return n_cap;
+  int64_t n = *n_dev;
+  return n < n_cap ? n : n_cap;
+}
+
+__global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __restrict__ keys, int64_t n_cap,
+                                                           const int64_t* n_dev, int shift, int64_t ntiles,
+                                                           uint32_t* __restrict__ counts) {
+  __shared__ uint32_t h[256];
+  h[threadIdx.x] = 0;
+  __syncthreads();
+  const int64_t n = rows_of(n_cap, n_dev);
+  const int64_t base = (int64_t)blockIdx.x * kSortTile;
+#pragma unroll 4
+  for (int i = 0; i < kSortItems; ++i) {
+    int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
+    if (j < n) atomicAdd(&h[(keys[j] >> shift) & 0xFF], 1u);
+  }
+  __syncthreads();
+  counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+}
+
+template <class P>
+__global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __restrict__ keys,
+                                                              const P* __restrict__ vals, uint32_t* __restrict__ okeys,
+                                                              P* __restrict__ ovals, int64_t n_cap,
+                                                              const int64_t* n_dev, int shift, int64_t ntiles,
+                                                              const uint32_t* __restrict__ offsets) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  P* stage_v = (P*)sm_raw;                                           // kSortTile
+  uint32_t* stage_k = (uint32_t*)(stage_v + kSortTile);              // kSortTile
+  uint32_t* whist = stage_k + kSortTile;                             // 8 x 256
+  uint32_t* tstart = whist + (kSortThreads / 32) * 256;              // 256
+  uint32_t* gbase = tstart + 256;                                    // 256
+
+  const int64_t n = rows_of(n_cap, n_dev);
+  const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
+  if (tile0 >= n) return;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) whist[i] = 0;
+  gbase[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  __syncthreads();
+
+  uint32_t k[kSortItems];
+  P v[kSortItems];
+  uint32_t lr[kSortItems];
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t j = wbase + r * 32 + lane;
+    const bool ok = j < n;
+    k[r] = ok ? keys[j] : 0u;
+    v[r] = ok ? vals[j] : P(0);
+    const uint32_t d = (k[r] >> shift) & 0xFFu;
+    const uint32_t tag = ok ? d : (0x100u | (uint32_t)lane);
+    const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+    const uint32_t before = ok ? whist[w * 256 + d] : 0u;
+    lr[r] = before + __popc(peers & lt);
+    __syncwarp();
+    if (ok && (peers & lt) == 0) whist[w * 256 + d] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  {  // per digit: prefix over warps, then exclusive scan over digits
+    const int d = threadIdx.x;
+    uint32_t run = 0;
+#pragma unroll
+    for (int ww = 0; ww < kSortThreads / 32; ++ww) {
+      uint32_t c = whist[ww * 256 + d];
+      whist[ww * 256 + d] = run;
+      run += c;
+    }
+    uint32_t e = block_exclusive_scan(run, nullptr);
+    tstart[d] = e;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t j = wbase + r * 32 + lane;
+    if (j < n) {
+      const uint32_t d = (k[r] >> shift) & 0xFFu;
+      const uint32_t lp = tstart[d] + whist[w * 256 + d] + lr[r];
+      stage_k[lp] = k[r];
+      stage_v[lp] = v[r];
+    }
+  }
+  __syncthreads();
+  const int cnt = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
+  for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
+    const uint32_t key = stage_k[i];
+    const uint32_t d = (key >> shift) & 0xFFu;
+    const int64_t pos = (int64_t)gbase[d] + (i - (int64_t)tstart[d]);
+    okeys[pos] = key;
+    ovals[pos] = stage_v[i];
+  }
+}
+
+template <class P>
+static size_t scatter_smem() {
+  return (size_t)kSortTile * (sizeof(P) + 4) + ((kSortThreads / 32) * 256 + 512) * 4;
+}
+
+size_t radix_tmp_bytes(int64_t n_cap) {
+  int64_t ntiles = (n_cap + kSortTile - 1) / kSortTile;
+  if (ntiles < 1) ntiles = 1;
+  size_t counts = (size_t)256 * ntiles * sizeof(uint32_t);
+  return ((counts + 255) & ~size_t(255)) + scan_tmp_bytes(256 * ntiles);
+}
+
+template <class P>
+agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* va, uint32_t* kb, P* vb,
+                            int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
+                            uint32_t** kout, P** vout) {
+  *kout = const_cast<uint32_t*>(kin);
+  *vout = const_cast<P*>(vin);
+  const int64_t ntiles = (n_cap + kSortTile - 1) / kSortTile;
+  if (ntiles == 0) return AGG_OK;
+  uint32_t* counts = (uint32_t*)tmp;
+  size_t cbytes = ((size_t)256 * ntiles * sizeof(uint32_t) + 255) & ~size_t(255);
+  void* stmp = (char*)tmp + cbytes;
+  const size_t sm = scatter_smem<P>();
+  static bool attr_set[64] = {};  // per device; the attribute belongs to the function on a device
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev >= 64 || !attr_set[dev]) {
+    AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    if (dev < 64) attr_set[dev] = true;
+  }
+  const uint32_t* ki = kin;
+  const P* vi = vin;
+  int pass = 0;
+  for (int shift = 0; shift < bits; shift += 8, ++pass) {
+    uint32_t* ko = (pass & 1) ? kb : ka;
+    P* vo = (pass & 1) ? vb : va;
+    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ntiles, counts);
+    agg_status st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
+    if (st != AGG_OK) return st;
+    radix_scatter<P><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ntiles,
+                                                                 counts);
+    note_launch(2);
+    AGG_CUDA_TRY(cudaGetLastError());
+    ki = ko;
+    vi = vo;
+    *kout = ko;
+    *vout = vo;
+  }
+  return AGG_OK;
+}
+
+template agg_status radix_sort_pairs<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                                               uint32_t*, int64_t, const int64_t*, int, void*, cudaStream_t,
+                                               uint32_t**, uint32_t**);
+template agg_status radix_sort_pairs<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, uint32_t*,
+                                               uint64_t*, int64_t, const int64_t*, int, void*, cudaStream_t,
+                                               uint32_t**, uint64_t**);
+
+}  // namespace agg

@@ -1,0 +1,35 @@
+// Device-wide primitives used by GROUP BY: exclusive scan of uint32 counts and
+// a stable LSD radix sort of (uint32 key, payload) pairs.
+#pragma once
+
+#include "common.cuh"
+
+namespace agg {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;
+constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 rows per tile
+
+// Exclusive scan of n uint32 values (in may equal out). If total_dev is not
+// null the sum of all values is written there. tmp must hold
+// scan_tmp_bytes(n) bytes.
+size_t scan_tmp_bytes(int64_t n);
+agg_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, void* tmp,
+                              cudaStream_t s);
+
+// Stable LSD radix sort by key bits [0, bits) (bits a multiple of 8, <= 32).
+// Sorts n_cap pairs, or, if n_dev is not null, the first *n_dev of them (the
+// count is read on the device; n_cap bounds it). The first pass reads
+// (kin, vin); passes then alternate between the buffers (ka, va) and
+// (kb, vb), which may alias (kin, vin) but not each other. *kout / *vout point
+// to the buffers holding the result. tmp must hold radix_tmp_bytes(n_cap).
+size_t radix_tmp_bytes(int64_t n_cap);
+template <class P>
+agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* va, uint32_t* kb, P* vb,
+                            int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
+                            uint32_t** kout, P** vout);
+
+// Small-sort capacity of the single-block bitonic sorter used for small tables.
+constexpr int kSmallSort = 8192;
+
+}  // namespace agg

@@ -1,0 +1,239 @@
+"""Parity of GROUP BY (agg_groupby, agg_groupby_host, agg_sketch) with the CPU oracle.
+
+Keys, counts, integer sums and averages, and MIN/MAX must be bit-identical to
+the oracle for every strategy; float sums and averages within the 1e-6 bar.
+"""
+import numpy as np
+import pytest
+import torch
+
+import datagen as dg
+import oracle
+import paper_2606_10030_gb300 as agg
+from oracle.sketch import sketch as oracle_sketch
+from tests.common import FP_REL
+
+pytestmark = pytest.mark.gpu
+
+STRATS = [agg.AGG_STRAT_SMEM, agg.AGG_STRAT_GLOBAL, agg.AGG_STRAT_SORT, agg.AGG_STRAT_AUTO]
+DTS = ["i32", "i64", "u32", "f32", "f64"]
+NP = {"i32": np.int32, "i64": np.int64, "u32": np.uint32, "f32": np.float32, "f64": np.float64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    agg.build()
+    agg.lib()
+
+
+def make_case(case: str, dt: str, seed: int = 0):
+    rng = np.random.default_rng(seed)
+    if case == "empty":
+        keys = np.array([], dtype=np.uint32)
+    elif case == "one":
+        keys = np.array([123], dtype=np.uint32)
+    elif case == "few":
+        keys = dg.keys_uniform(1000, 7, seed)
+    elif case == "uniform1k":
+        keys = dg.keys_uniform(100_003, 1000, seed)
+    elif case == "uniform50k":
+        keys = dg.keys_uniform(300_007, 50_000, seed)
+    elif case == "zipf":
+        keys = dg.keys_zipf(200_003, 100_000, 1.0, seed)
+    elif case == "distinct":
+        keys = dg.domain_keys(seed, rng.permutation(70_001))
+    elif case == "sentinel":
+        keys = dg.keys_uniform(50_001, 5, seed)
+        keys[::3] = 0xFFFFFFFF
+        keys[1::7] = 0
+    else:
+        raise ValueError(case)
+    n = keys.size
+    if dt in ("f32", "f64"):
+        vals = dg.values(dt, n, seed + 1)
+    elif dt == "i32":
+        vals = rng.integers(-(2 ** 31), 2 ** 31, n, dtype=np.int64).astype(np.int32)
+    elif dt == "u32":
+        vals = rng.integers(0, 2 ** 32, n, dtype=np.uint64).astype(np.uint32)
+    else:
+        vals = rng.integers(-(2 ** 62), 2 ** 62, n, dtype=np.int64)
+    return keys.astype(np.uint32), vals.astype(NP[dt])
+
+
+def check_groups(res: dict, keys: np.ndarray, vals: np.ndarray, ops=agg.AGG_ALL):
+    ref = oracle.groupby(keys, vals)
+    assert np.array_equal(res["keys"], ref.keys)
+    assert np.array_equal(res["count"], ref.count)
+    fp = vals.dtype.kind == "f"
+    if ops & (agg.AGG_SUM | agg.AGG_AVG):
+        if fp:
+            a = oracle.groupby(keys, np.abs(vals)).sum
+            bar = FP_REL * np.maximum(np.abs(ref.sum), 2.0 ** -24 * a)
+            assert np.all(np.abs(res["sum"] - ref.sum) <= bar)
+            assert np.all(np.abs(res["avg"] - ref.avg) <= bar / ref.count)
+        else:
+            assert np.array_equal(res["sum"], ref.sum)
+            assert np.array_equal(res["avg"].view(np.int64), ref.avg.view(np.int64))
+    if ops & (agg.AGG_MIN | agg.AGG_MAX):
+        if fp:
+            assert np.array_equal(res["min"].view(np.int64), ref.min.view(np.int64))
+            assert np.array_equal(res["max"].view(np.int64), ref.max.view(np.int64))
+        else:
+            assert np.array_equal(res["min"], ref.min) and np.array_equal(res["max"], ref.max)
+    return ref
+
+
+def run(keys, vals, strategy, ops=agg.AGG_ALL, **kw):
+    k = torch.from_numpy(keys).cuda()
+    v = torch.from_numpy(vals).cuda()
+    g = agg.agg_groupby(k, v, ops, agg.options(strategy, **kw))
+    res = g.to_host()
+    meta = (g.strategy, g.retries, g.table_slots)
+    g.free()
+    return res, meta
+
+
+CASES = ["empty", "one", "few", "uniform1k", "uniform50k", "zipf", "distinct", "sentinel"]
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("dt", DTS)
+@pytest.mark.parametrize("case", CASES)
+def test_groupby_parity(strategy, dt, case):
+    keys, vals = make_case(case, dt, seed=len(case))
+    res, meta = run(keys, vals, strategy)
+    if strategy != agg.AGG_STRAT_AUTO:
+        assert meta[0] == strategy
+    check_groups(res, keys, vals)
+
+
+@pytest.mark.parametrize("dt", DTS)
+@pytest.mark.parametrize("ops", [agg.AGG_SUM, agg.AGG_COUNT, agg.AGG_MIN | agg.AGG_MAX, agg.AGG_AVG,
+                                 agg.AGG_SUM | agg.AGG_COUNT | agg.AGG_MIN | agg.AGG_MAX])
+def test_groupby_op_subsets(dt, ops):
+    keys, vals = make_case("uniform1k", dt, seed=3)
+    for s in STRATS[:3]:
+        res, _ = run(keys, vals, s, ops)
+        check_groups(res, keys, vals, ops)
+
+
+@pytest.mark.parametrize("dt", DTS)
+def test_strategies_return_identical_results(dt):
+    keys, vals = make_case("zipf", dt, seed=11)
+    outs = [run(keys, vals, s)[0] for s in STRATS[:3]]
+    for o in outs[1:]:
+        for f in ("keys", "count", "min", "max"):
+            assert np.array_equal(o[f].view(np.int64) if o[f].dtype == np.float64 else o[f],
+                                  outs[0][f].view(np.int64) if outs[0][f].dtype == np.float64 else outs[0][f])
+        if dt in ("f32", "f64"):
+            a = oracle.groupby(keys, np.abs(vals)).sum
+            assert np.all(np.abs(o["sum"] - outs[0]["sum"]) <= 2 * FP_REL * np.maximum(np.abs(outs[0]["sum"]),
+                                                                                     2.0 ** -24 * a))
+        else:
+            assert np.array_equal(o["sum"], outs[0]["sum"]) and np.array_equal(o["avg"], outs[0]["avg"])
+
+
+def test_table_regrows_when_undersized():
+    keys, vals = make_case("uniform50k", "i64", seed=5)
+    res, meta = run(keys, vals, agg.AGG_STRAT_GLOBAL, table_slots=1024)
+    assert meta[1] >= 1 and meta[2] >= 65536
+    check_groups(res, keys, vals)
+    res, meta = run(keys, vals, agg.AGG_STRAT_SMEM, table_slots=2048, smem_slots=256)
+    assert meta[1] >= 1
+    check_groups(res, keys, vals)
+
+
+@pytest.mark.parametrize("strategy", STRATS[:3])
+def test_unaligned_columns_use_the_scalar_path(strategy):
+    keys, vals = make_case("uniform1k", "i64", seed=6)
+    k = torch.from_numpy(keys).cuda()
+    v = torch.from_numpy(vals).cuda()
+    g = agg.agg_groupby(k[1:], v[:-1], agg.AGG_ALL, agg.options(strategy))
+    check_groups(g.to_host(), keys[1:], vals[:-1])
+    g.free()
+    g = agg.agg_groupby(k[3:], v[3:], agg.AGG_ALL, agg.options(strategy))
+    check_groups(g.to_host(), keys[3:], vals[3:])
+    g.free()
+
+
+def test_config_2p26_rows_1024_keys_int64_bit_exact():
+    """2^26 rows, uint32 keys uniform over 1024 random keys, int64 values in [0, 2^32):
+    GROUP BY SUM/COUNT/MIN/MAX bit-exact (the shared-memory hash path)."""
+    from datagen import cuda as dgc
+    n = 1 << 26
+    k = dgc.keys_uniform(n, 1024, 0)
+    v = dgc.values("i64", n, 0)
+    ops = agg.AGG_SUM | agg.AGG_COUNT | agg.AGG_MIN | agg.AGG_MAX
+    g = agg.agg_groupby(k, v, ops)
+    assert g.strategy == agg.AGG_STRAT_SMEM and g.num_groups == 1024
+    res = g.to_host()
+    g.free()
+    kh, vh = k.cpu().numpy(), v.cpu().numpy()
+    assert np.array_equal(kh, dg.keys_uniform(n, 1024, 0)[:n]) if n <= (1 << 20) else True
+    check_groups(res, kh, vh, ops)
+
+
+def test_config_2p28_rows_zipf_float32_sampled():
+    """2^28 rows, keys Zipf(1.0) over 2^24 random keys, float32 N(0,1)*1e3, SUM/AVG.
+    Checked on sampled groups against the oracle (hot keys and random ones) and on
+    properties that hold at any size."""
+    from datagen import cuda as dgc
+    n, D = 1 << 28, 1 << 24
+    k = dgc.keys_zipf(n, D, 1.0, 0)
+    v = dgc.values("f32", n, 0)
+    ops = agg.AGG_SUM | agg.AGG_AVG
+    g = agg.agg_groupby(k, v, ops)
+    res = g.to_host()
+    g.free()
+    d = res["keys"].size
+    assert 0.5 * D < d <= D
+    assert np.all(np.diff(res["keys"].astype(np.int64)) > 0)
+    assert res["count"].sum() == n
+    kh, vh = k.cpu().numpy(), v.cpu().numpy()
+    total = oracle.exact_sum(vh)
+    abs_total = float(np.abs(vh.astype(np.float64)).sum())
+    assert abs(res["sum"].sum() - total) <= FP_REL * max(abs(total), 2.0 ** -24 * abs_total) + 1e-9 * abs_total
+    rng = np.random.default_rng(0)
+    hot = np.argsort(res["count"])[::-1][:40]
+    pick = np.unique(np.concatenate([hot, rng.integers(0, d, 160)]))
+    sel = res["keys"][pick]
+    ref = oracle.groupby_selected(kh, vh, sel)
+    refa = oracle.groupby_selected(kh, np.abs(vh), sel)
+    assert np.array_equal(ref.keys, sel) and np.array_equal(ref.count, res["count"][pick])
+    bar = FP_REL * np.maximum(np.abs(ref.sum), 2.0 ** -24 * refa.sum)
+    assert np.all(np.abs(res["sum"][pick] - ref.sum) <= bar)
+    assert np.all(np.abs(res["avg"][pick] - ref.avg) <= bar / ref.count)
+
+
+@pytest.mark.parametrize("dt", ["i64", "f32"])
+@pytest.mark.parametrize("strategy", STRATS)
+def test_host_fed_groupby(dt, strategy):
+    n = 20_000_017  # three 8 Mi-row chunks
+    keys = dg.keys_uniform(n, 3000, 2)
+    vals = dg.values(dt, n, 2)
+    g = agg.agg_groupby_host(torch.from_numpy(keys).pin_memory(), torch.from_numpy(vals).pin_memory(),
+                             agg.AGG_ALL, agg.options(strategy))
+    res = g.to_host()
+    g.free()
+    check_groups(res, keys, vals)
+
+
+def _dev_consts():
+    p = torch.cuda.get_device_properties(0)
+    return float(p.shared_memory_per_block_optin), float(p.L2_cache_size)
+
+
+@pytest.mark.parametrize("case", ["uniform1k", "zipf", "distinct", "sentinel", "few", "sorted", "tiny"])
+@pytest.mark.parametrize("offset", [0, 12345, 2 ** 63 + 17])
+def test_sketch_parity(case, offset):
+    if case == "sorted":
+        keys = np.sort(dg.keys_uniform(500_000, 3000, 1))
+    elif case == "tiny":
+        keys = dg.keys_uniform(1000, 40, 1)
+    else:
+        keys, _ = make_case(case, "i32", seed=2)
+    smem, l2 = _dev_consts()
+    ops = agg.AGG_SUM | agg.AGG_MIN
+    got = agg.agg_sketch(torch.from_numpy(keys).cuda(), agg.AGG_F64, ops, offset).cpu().numpy()
+    ref = oracle_sketch(keys, 8, 2, 1, 32, offset, smem, l2)
+    assert np.allclose(got, ref, rtol=1e-5, atol=1e-6), (got, ref)

@@ -1,0 +1,72 @@
+"""Pins for the key-sketch oracle: closed forms on constructed samples."""
+import math
+
+import numpy as np
+
+from oracle.sketch import SAMPLE, sample_positions, sketch
+
+ARGS = dict(vbytes=8, nops=4, fp=0, slot_bytes=32, offset=0, smem_bytes=232448.0, l2_bytes=132120576.0)
+
+
+def test_all_distinct_sample():
+    keys = np.arange(SAMPLE, dtype=np.uint32) * np.uint32(7)
+    f = sketch(keys, **ARGS)
+    assert f[0] == 12 and f[4] == 1 and f[5] == 1 and f[6] == 0
+    assert f[7] == 1 / SAMPLE and f[8] == 8 / SAMPLE
+    assert f[9] == 0                         # all counts 1: flat rank-frequency
+    assert abs(f[10] - 1.0) < 1e-12          # uniform over m keys: entropy ln m
+    assert f[11] == 0
+    assert f[12] == 12                       # GEE = sqrt(1) * m + 0 = m
+    assert f[15] == math.log2(7 * (SAMPLE - 1) + 1)
+
+
+def test_constant_column():
+    keys = np.full(100000, 5, dtype=np.uint32)
+    f = sketch(keys, **ARGS)
+    assert f[4] == 1 / SAMPLE and f[5] == 0 and f[7] == 1 and f[8] == 1
+    assert f[9] == 0 and f[10] == 0 and f[11] == 1
+    assert f[12] == 0                        # GEE = 0 + (1 - 0) = 1
+    assert f[15] == 0
+    assert f[13] == math.log2(1 + 2 * 32 / 232448.0)
+
+
+def test_two_equal_halves_entropy_and_gee():
+    keys = np.repeat(np.array([1, 9], dtype=np.uint32), SAMPLE // 2)
+    f = sketch(keys, **ARGS)
+    assert abs(f[10] - math.log(2) / math.log(SAMPLE)) < 1e-12
+    assert f[7] == 0.5 and f[8] == 1.0
+    # two counts of m/2: the slope over R=2 ranks is ln(1)/ln(2) = 0
+    assert f[9] == 0
+    assert f[15] == math.log2(9)
+
+
+def test_gee_scales_singletons_by_sqrt_n_over_m():
+    n = SAMPLE * 64                          # stride 64: each sampled key distinct
+    keys = np.arange(n, dtype=np.uint32)
+    f = sketch(keys, **ARGS)
+    assert f[12] == math.log2(math.sqrt(64) * SAMPLE)
+
+
+def test_known_slope_on_constructed_frequencies():
+    # counts 512/r for r = 1..32 (a Zipf(1) profile): slope -1 up to rounding of the counts
+    counts = [int(round(512 / r)) for r in range(1, 33)]
+    keys = np.concatenate([np.full(c, r, dtype=np.uint32) for r, c in enumerate(counts)])
+    keys = np.concatenate([keys, np.arange(10 ** 6, 10 ** 6 + SAMPLE - keys.size, dtype=np.uint32)])
+    assert keys.size == SAMPLE
+    f = sketch(keys, **ARGS)
+    x = np.log(np.arange(1, 33))
+    top = np.sort(np.array(counts + [1] * (SAMPLE - sum(counts))))[::-1][:32].astype(float)
+    y = np.log(top)
+    expect = np.polyfit(x, y, 1)[0]
+    assert abs(f[9] - expect) < 1e-12 and -1.1 < f[9] < -0.9
+
+
+def test_sample_positions_wrap_and_small_n():
+    assert list(sample_positions(10, 3)) == list(range(3, 10)) + [0, 1, 2]
+    p = sample_positions(SAMPLE * 3 + 5, 2 ** 63)
+    assert p.size == SAMPLE and p.max() < SAMPLE * 3 + 5
+
+
+def test_empty():
+    f = sketch(np.array([], dtype=np.uint32), **ARGS)
+    assert f[1] == 8 and f[2] == 4 and f[0] == 0 and np.all(f[4:] == 0)
