@@ -237,6 +237,76 @@ agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uin
                       uint64_t sample_offset, float* features_dev, void* stream);
 
 /*
+ * Autotuner (step a8; the paper's related work tunes the configuration
+ * parameters of GPU hash group-by, Sec. 7). Candidates: SMEM with the
+ * sketch-sized and the largest shared table at 256 and 512 threads, GLOBAL at
+ * 256 and 512 threads, and SORT. Each is run on the actual query and timed
+ * with CUDA events; the fastest is cached by query signature (value dtype,
+ * ops, round(log2 n), rounded log2 of the distinct estimate, top-8 share
+ * decile, sortedness half). AGG_STRAT_AUTOTUNE uses the cache and tunes on a
+ * miss.
+ */
+#define AGG_TUNE_MAX 8
+typedef struct agg_tune_result {
+  int32_t ncand;                    /* candidates timed */
+  int32_t best;                     /* index of the fastest */
+  int32_t strategy[AGG_TUNE_MAX];   /* AGG_STRAT_SMEM / GLOBAL / SORT */
+  int32_t threads[AGG_TUNE_MAX];
+  int32_t smem_slots[AGG_TUNE_MAX];
+  float ms[AGG_TUNE_MAX];           /* device time of the whole agg_groupby call */
+  float best_ms_per_strategy[3];    /* fastest SMEM, GLOBAL, SORT candidate */
+  float features[16];               /* sketch of the query */
+} agg_tune_result;
+
+/* Time every candidate on the query (reps runs each, minimum kept); fills out and the cache. */
+agg_status agg_autotune(const uint32_t* keys_dev, const void* vals_dev, int64_t n, agg_dtype vdtype, uint32_t ops,
+                        int reps, agg_tune_result* out, void* stream);
+/* Number of cached signatures; agg_autotune_clear empties the cache. */
+int64_t agg_autotune_cache_size(void);
+void agg_autotune_clear(void);
+/* Save / load the cache as text (one signature and choice per line). */
+agg_status agg_autotune_save(const char* path);
+agg_status agg_autotune_load(const char* path);
+
+/*
+ * Learned strategy selector (step a11): an MLP 16 -> 64 -> 64 -> 3 (ReLU,
+ * softmax) over the standardised sketch features, classes 0 = SMEM,
+ * 1 = GLOBAL, 2 = SORT, trained on the GPU by these kernels from the
+ * autotuner's timings (the related work of Sec. 7 models aggregation time to
+ * choose a configuration). Parameters are agg_mlp_param_count() = 5443 float32
+ * values: W1[16][64], b1[64], W2[64][64], b2[64], W3[64][3], b3[3] (W[in][out]).
+ * mean/std standardise the 16 inputs as (x - mean) / std (both NULL: raw x).
+ * All pointers are device pointers unless named *_host; calls are async on
+ * `stream` except agg_mlp_train and agg_selector_set.
+ */
+int agg_mlp_param_count(void);
+/* probs_dev[n][3] = softmax(MLP(x_dev[n][16])). */
+agg_status agg_mlp_forward(const float* params_dev, const float* mean_dev, const float* std_dev,
+                           const float* x_dev, int n, float* probs_dev, void* stream);
+/* Gradient of the mean cross-entropy over a batch of 1 <= n <= 256 labelled
+   samples (labels 0..2) into grads_dev[5443]; the loss into *loss_dev. */
+agg_status agg_mlp_grad(const float* params_dev, const float* mean_dev, const float* std_dev,
+                        const float* x_dev, const int32_t* y_dev, int n, float* grads_dev, float* loss_dev,
+                        void* stream);
+/* One Adam step (Kingma and Ba 2015) at step t >= 1 on params with moments m, v. */
+agg_status agg_mlp_adam(float* params_dev, const float* grads_dev, float* m_dev, float* v_dev, int64_t t,
+                        float lr, float beta1, float beta2, float eps, void* stream);
+/* Train for `epochs` passes in mini-batches (1..256) visited in a seeded
+   SplitMix64 Fisher-Yates order; Adam with beta1 0.9, beta2 0.999, eps 1e-8,
+   steps numbered from t0 + 1. epoch_loss_host[epochs] (may be NULL) receives
+   the mean training loss of each epoch. Synchronous. */
+agg_status agg_mlp_train(float* params_dev, float* m_dev, float* v_dev, const float* mean_dev,
+                         const float* std_dev, const float* x_dev, const int32_t* y_dev, int n, int epochs,
+                         int batch, float lr, uint64_t seed, int64_t t0, float* epoch_loss_host, void* stream);
+/* Install (copy) a trained network for AGG_STRAT_LEARNED on the current
+   device; without one, AGG_STRAT_LEARNED falls back to the AUTO rule. */
+agg_status agg_selector_set(const float* params_host, const float* mean_host, const float* std_host);
+void agg_selector_clear(void);
+int agg_selector_installed(void);
+/* The strategy the AUTO rule (no learned model) picks for a sketch (host call, no GPU work). */
+int agg_rule_strategy(const float* features_host, uint32_t ops);
+
+/*
  * agg_reduce_noalloc -- agg_reduce without any device allocation.
  *
  * The paper has no counterpart: this entry point exists for callers that

@@ -82,6 +82,23 @@ class AggOptions(ctypes.Structure):
     ]
 
 
+AGG_TUNE_MAX = 8
+
+
+class AggTuneResult(ctypes.Structure):
+    """Mirror of ``agg_tune_result``."""
+    _fields_ = [
+        ("ncand", ctypes.c_int32),
+        ("best", ctypes.c_int32),
+        ("strategy", ctypes.c_int32 * AGG_TUNE_MAX),
+        ("threads", ctypes.c_int32 * AGG_TUNE_MAX),
+        ("smem_slots", ctypes.c_int32 * AGG_TUNE_MAX),
+        ("ms", ctypes.c_float * AGG_TUNE_MAX),
+        ("best_ms_per_strategy", ctypes.c_float * 3),
+        ("features", ctypes.c_float * 16),
+    ]
+
+
 class AggGroups(ctypes.Structure):
     """Mirror of ``agg_groups``."""
     _fields_ = [
@@ -116,6 +133,22 @@ SIGNATURES = {
     "agg_groups_to_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "agg_groups_free": (None, [_vp]),
     "agg_sketch": (_i32, [_vp, _i64, _i32, _u32, ctypes.c_uint64, _vp, _vp]),
+    "agg_autotune": (_i32, [_vp, _vp, _i64, _i32, _u32, _i32, _vp, _vp]),
+    "agg_autotune_cache_size": (ctypes.c_int64, []),
+    "agg_autotune_clear": (None, []),
+    "agg_autotune_save": (_i32, [ctypes.c_char_p]),
+    "agg_autotune_load": (_i32, [ctypes.c_char_p]),
+    "agg_mlp_param_count": (_i32, []),
+    "agg_mlp_forward": (_i32, [_vp, _vp, _vp, _vp, _i32, _vp, _vp]),
+    "agg_mlp_grad": (_i32, [_vp, _vp, _vp, _vp, _vp, _i32, _vp, _vp, _vp]),
+    "agg_mlp_adam": (_i32, [_vp, _vp, _vp, _vp, _i64, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                            ctypes.c_float, _vp]),
+    "agg_mlp_train": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _i32, _i32, _i32, ctypes.c_float,
+                             ctypes.c_uint64, _i64, _vp, _vp]),
+    "agg_selector_set": (_i32, [_vp, _vp, _vp]),
+    "agg_selector_clear": (None, []),
+    "agg_selector_installed": (_i32, []),
+    "agg_rule_strategy": (_i32, [_vp, _u32]),
     "agg_launch_count": (ctypes.c_int64, []),
     "agg_profile_enable": (None, [_i32]),
     "agg_profile_read": (_i32, [_vp, _vp]),
@@ -324,3 +357,58 @@ def profile_read() -> dict:
     calls = (ctypes.c_int64 * len(PHASES))()
     check(lib().agg_profile_read(ms, calls))
     return {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(PHASES)}
+
+
+def agg_autotune(keys, vals, ops: int = AGG_ALL, reps: int = 1, stream=None) -> AggTuneResult:
+    """Time every GROUP BY candidate on the query; returns the timings (and fills the cache)."""
+    r = AggTuneResult()
+    check(lib().agg_autotune(ctypes.c_void_p(keys.data_ptr()), ctypes.c_void_p(vals.data_ptr()), keys.numel(),
+                             dtype_code(vals), ops, reps, ctypes.byref(r), _stream_ptr(stream)))
+    return r
+
+
+def _p(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def agg_mlp_forward(params, x, mean=None, std=None, out=None, stream=None):
+    import torch
+    n = x.shape[0]
+    out = torch.empty((n, 3), dtype=torch.float32, device=x.device) if out is None else out
+    check(lib().agg_mlp_forward(_p(params), _p(mean), _p(std), _p(x), n, _p(out), _stream_ptr(stream)))
+    return out
+
+
+def agg_mlp_grad(params, x, y, mean=None, std=None, stream=None):
+    import torch
+    g = torch.empty(lib().agg_mlp_param_count(), dtype=torch.float32, device=x.device)
+    loss = torch.empty(1, dtype=torch.float32, device=x.device)
+    check(lib().agg_mlp_grad(_p(params), _p(mean), _p(std), _p(x), _p(y), x.shape[0], _p(g), _p(loss),
+                             _stream_ptr(stream)))
+    return g, loss
+
+
+def agg_mlp_adam(params, grads, m, v, t: int, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    check(lib().agg_mlp_adam(_p(params), _p(grads), _p(m), _p(v), t, lr, beta1, beta2, eps, _stream_ptr(stream)))
+
+
+def agg_mlp_train(params, m, v, x, y, mean=None, std=None, epochs=30, batch=256, lr=1e-3, seed=0, t0=0,
+                  stream=None):
+    """Train in place on the device; returns the per-epoch mean loss."""
+    losses = np.zeros(max(1, epochs), dtype=np.float32)
+    check(lib().agg_mlp_train(_p(params), _p(m), _p(v), _p(mean), _p(std), _p(x), _p(y), x.shape[0], epochs, batch,
+                              lr, seed, t0, losses.ctypes.data_as(ctypes.c_void_p), _stream_ptr(stream)))
+    return losses[:epochs]
+
+
+def agg_selector_set(params: np.ndarray, mean: np.ndarray, std: np.ndarray) -> None:
+    params = np.ascontiguousarray(params, dtype=np.float32)
+    mean = np.ascontiguousarray(mean, dtype=np.float32)
+    std = np.ascontiguousarray(std, dtype=np.float32)
+    check(lib().agg_selector_set(params.ctypes.data_as(ctypes.c_void_p), mean.ctypes.data_as(ctypes.c_void_p),
+                                 std.ctypes.data_as(ctypes.c_void_p)))
+
+
+def agg_rule_strategy(features, ops: int) -> int:
+    f = np.ascontiguousarray(features, dtype=np.float32)
+    return int(lib().agg_rule_strategy(f.ctypes.data_as(ctypes.c_void_p), ops))

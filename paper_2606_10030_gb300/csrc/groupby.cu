@@ -949,11 +949,13 @@ static int smem_slots_for(double est, bool mm) {
 
 // Selector hooks (the learned selector and the autotuner live in their own units).
 int select_learned(const float* feat, bool* ok);
+agg_status sketch_and_select(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
+                             cudaStream_t s, float* feat, int* strategy);
 agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
                          const float* feat, cudaStream_t s, int* strategy, int* smem_slots, int64_t* table_slots);
 
 // Sketch the keys on the device and read the features back (one sync).
-static agg_status sketch_to_host(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
+agg_status sketch_features(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
                                  cudaStream_t s, float* feat) {
   agg_status st = AGG_OK;
   float* fd = (float*)stream_scratch(s, 4096, &st);
@@ -1052,19 +1054,39 @@ static agg_status hash_device(const uint32_t* keys, const void* vals, int64_t n,
 
 using namespace agg;
 
-static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                               const agg_options* opt, cudaStream_t s, agg_groups** out) {
-  agg_options o{};
-  if (opt) o = *opt;
+namespace agg {
+
+// GROUP BY of a device column with explicit options (also used by the autotuner).
+agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                        const agg_options& o, cudaStream_t s, agg_groups** out) {
   float feat[F_COUNT] = {0};
   bool have = false;
+  agg_status st = AGG_OK;
   if (needs_sketch(o) && n > 0) {
-    agg_status st = sketch_to_host(keys, n, vdt, ops, o.sample_offset, s, feat);
+    if (o.strategy == AGG_STRAT_LEARNED) {
+      int learned = -1;
+      st = sketch_and_select(keys, n, vdt, ops, o.sample_offset, s, feat, &learned);
+      if (st != AGG_OK) return st;
+      have = true;
+      agg_options o2 = o;
+      o2.strategy = learned >= 0 ? learned : rule_strategy(feat, ops);
+      Choice c;
+      st = choose(keys, vals, n, vdt, ops, o2, feat, have, s, &c);
+      if (st != AGG_OK) return st;
+      agg_groups* g = nullptr;
+      if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g);
+      else st = hash_device(keys, vals, n, vdt, ops, c.plan, s, &g);
+      if (st != AGG_OK) return st;
+      std::memcpy(g->features, feat, sizeof(feat));
+      *out = g;
+      return AGG_OK;
+    }
+    st = sketch_features(keys, n, vdt, ops, o.sample_offset, s, feat);
     if (st != AGG_OK) return st;
     have = true;
   }
   Choice c;
-  agg_status st = choose(keys, vals, n, vdt, ops, o, feat, have, s, &c);
+  st = choose(keys, vals, n, vdt, ops, o, feat, have, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
   if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g);
@@ -1073,6 +1095,15 @@ static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n
   std::memcpy(g->features, feat, sizeof(feat));
   *out = g;
   return AGG_OK;
+}
+
+}  // namespace agg
+
+static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                               const agg_options* opt, cudaStream_t s, agg_groups** out) {
+  agg_options o{};
+  if (opt) o = *opt;
+  return groupby_with(keys, vals, n, vdt, ops, o, s, out);
 }
 
 // ---------------------------------------------------------------------------
@@ -1170,7 +1201,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     if (needs_sketch(o)) {
       cudaStreamWaitEvent(s, pipe->ready[0], 0);
       const int64_t r0 = std::min<int64_t>(chunk, n);
-      st = sketch_to_host(kbuf(0), r0, vdt, ops, o.sample_offset, s, feat);
+      st = sketch_features(kbuf(0), r0, vdt, ops, o.sample_offset, s, feat);
       if (st != AGG_OK) return st;
       rescale_features(feat, r0, n, ops);
       have = true;
@@ -1302,4 +1333,9 @@ extern "C" agg_status agg_groupby_host(const uint32_t* keys_host, const void* va
   if (st != AGG_OK) return st;
   *out = nullptr;
   return groupby_host_impl(keys_host, vals_host, n, vdtype, ops, opt, (cudaStream_t)stream, out);
+}
+
+extern "C" int agg_rule_strategy(const float* features_host, uint32_t ops) {
+  if (!features_host) return AGG_STRAT_GLOBAL;
+  return rule_strategy(features_host, ops);
 }

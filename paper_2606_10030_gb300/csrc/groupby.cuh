@@ -16,6 +16,10 @@ constexpr int kSketchSample = 4096;
 agg_status sketch_launch(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset, float* feat_dev,
                          cudaStream_t s);
 
+// Sketch the keys and read the features back to the host (one sync).
+agg_status sketch_features(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
+                           cudaStream_t s, float* feat);
+
 // Slot sizes of the global hash table.
 inline int gslot_bytes(bool minmax) { return minmax ? 32 : 16; }
 inline bool ops_minmax(uint32_t ops) { return ops & (AGG_MIN | AGG_MAX); }
