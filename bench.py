@@ -302,6 +302,58 @@ def extra_scan(steps: int, peaks: dict) -> dict:
             "frac_of_nominal_8TBs": round(gbs / 8000.0, 4), "steps": steps}
 
 
+def extra_batched(steps: int, nq: int = 512) -> dict:
+    """512 uneven GROUP BY queries: one batched plan (persistent kernel + CUDA graph,
+    learned selector) against plain per-query agg_groupby calls on one stream."""
+    import torch
+
+    import datagen as dg
+    import paper_2606_10030_gb300 as agg
+    from datagen import cuda as dgc
+    from paper_2606_10030_gb300 import selector
+    learned = selector.install_default()
+    qs = dg.batch_queries(nq, 0)
+    cols = []
+    rows = 0
+    in_bytes = 0
+    for q in qs:
+        k, v = dgc.group_column(q)
+        cols.append((k, v, q.ops))
+        rows += q.n
+        in_bytes += q.n * (4 + v.element_size())
+    torch.cuda.synchronize()
+    strat = agg.AGG_STRAT_LEARNED if learned else agg.AGG_STRAT_AUTO
+    t0 = time.perf_counter()
+    plan = agg.BatchPlan([(k, v, ops, strat) for k, v, ops in cols])
+    plan_s = time.perf_counter() - t0
+    plan.run()  # capture + first replay
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        plan.run()
+    torch.cuda.synchronize()
+    batch_s = (time.perf_counter() - t0) / steps
+    plan.free()
+    o = agg.options(strat)
+    for k, v, ops in cols[:8]:
+        agg.agg_groupby(k, v, ops, o).free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, v, ops in cols:
+        agg.agg_groupby(k, v, ops, o).free()
+    torch.cuda.synchronize()
+    plain_s = time.perf_counter() - t0
+    del cols
+    torch.cuda.empty_cache()
+    return {"workload": f"{nq} GROUP BY queries, rows log-uniform in [2^12, 2^24], distinct keys log-uniform in "
+                        "[1, 2^20] (uniform or Zipf 0.5-1.5), mixed int32/int64/float32/float64 values and ops",
+            "rows": rows, "input_bytes": in_bytes, "selector": "learned" if learned else "rule (no weights file)",
+            "batched_ms": round(batch_s * 1e3, 3), "batched_GB/s": round(in_bytes / batch_s / 1e9, 1),
+            "batched_plan_ms": round(plan_s * 1e3, 1),
+            "plain_ms": round(plain_s * 1e3, 3), "plain_GB/s": round(in_bytes / plain_s / 1e9, 1),
+            "speedup": round(plain_s / batch_s, 2), "steps": steps}
+
+
 def extra_zipf(steps: int) -> dict:
     """GROUP BY SUM/AVG, 2^28 rows, Zipf(1) keys over 2^24 random keys, float32 N(0,1)*1e3."""
     import torch
@@ -422,6 +474,7 @@ def run_ours(args):
     if rank == 0 and world == 1 and not args.no_extra and W.name == "groupby":
         extra["scan"] = extra_scan(200, peaks)
         extra["zipf"] = extra_zipf(5)
+        extra["batched"] = extra_batched(5)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows, t, sample = W.cpu_sample(args.cpu_budget)

@@ -237,6 +237,46 @@ agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uin
                       uint64_t sample_offset, float* features_dev, void* stream);
 
 /*
+ * Batched GROUP BY (step a9): many independent queries in one persistent
+ * kernel captured in a CUDA graph.
+ *
+ * agg_batch_plan_create sketches every query (one batched launch), picks each
+ * query's strategy (query.strategy: AUTO = the rule, LEARNED = the installed
+ * network, or SMEM / GLOBAL) and table sizes, and allocates everything; one
+ * host synchronisation. In a batch every query runs a hash strategy: a query
+ * for which SORT is chosen runs on the global table (identical results).
+ * agg_batch_run performs the device work (tables cleared, one persistent
+ * build kernel over (query, 64 Ki-row tile) work items pulled from a device
+ * counter, batched finalisation into ascending key order) as a CUDA graph
+ * captured on the first run and replayed afterwards, then reads back the group
+ * counts; synchronous. A table that overflows is regrown (new graph) and the
+ * run repeated. Inputs must stay valid and unchanged while the plan is used;
+ * a replay recomputes every query from its inputs.
+ * agg_batch_result returns query i's result; its arrays belong to the plan's
+ * output block, are overwritten by the next run, and stay valid (even after
+ * agg_batch_plan_free) until the result is released with agg_groups_free.
+ * agg_batch is plan + run + results + free in one call.
+ */
+typedef struct agg_query {
+  const uint32_t* keys;  /* device pointer, n keys */
+  const void* vals;      /* device pointer, n values of dtype */
+  int64_t n;             /* 0 <= n < 2^32 */
+  int32_t dtype;         /* agg_dtype */
+  uint32_t ops;          /* AGG_* bitmask */
+  int32_t strategy;      /* agg_strategy */
+  int32_t reserved;
+} agg_query;
+
+typedef struct agg_batch_plan agg_batch_plan;
+
+agg_status agg_batch_plan_create(const agg_query* queries, int nq, agg_batch_plan** plan, void* stream);
+agg_status agg_batch_run(agg_batch_plan* plan, void* stream);
+agg_status agg_batch_result(const agg_batch_plan* plan, int i, agg_groups** out);
+int agg_batch_size(const agg_batch_plan* plan);
+void agg_batch_plan_free(agg_batch_plan* plan);
+agg_status agg_batch(const agg_query* queries, int nq, agg_groups** outs, void* stream);
+
+/*
  * Autotuner (step a8; the paper's related work tunes the configuration
  * parameters of GPU hash group-by, Sec. 7). Candidates: SMEM with the
  * sketch-sized and the largest shared table at 256 and 512 threads, GLOBAL at

@@ -99,6 +99,19 @@ class AggTuneResult(ctypes.Structure):
     ]
 
 
+class AggQuery(ctypes.Structure):
+    """Mirror of ``agg_query``."""
+    _fields_ = [
+        ("keys", ctypes.c_void_p),
+        ("vals", ctypes.c_void_p),
+        ("n", ctypes.c_int64),
+        ("dtype", ctypes.c_int32),
+        ("ops", ctypes.c_uint32),
+        ("strategy", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
+    ]
+
+
 class AggGroups(ctypes.Structure):
     """Mirror of ``agg_groups``."""
     _fields_ = [
@@ -149,6 +162,12 @@ SIGNATURES = {
     "agg_selector_clear": (None, []),
     "agg_selector_installed": (_i32, []),
     "agg_rule_strategy": (_i32, [_vp, _u32]),
+    "agg_batch_plan_create": (_i32, [_vp, _i32, _vp, _vp]),
+    "agg_batch_run": (_i32, [_vp, _vp]),
+    "agg_batch_result": (_i32, [_vp, _i32, _vp]),
+    "agg_batch_size": (_i32, [_vp]),
+    "agg_batch_plan_free": (None, [_vp]),
+    "agg_batch": (_i32, [_vp, _i32, _vp, _vp]),
     "agg_launch_count": (ctypes.c_int64, []),
     "agg_profile_enable": (None, [_i32]),
     "agg_profile_read": (_i32, [_vp, _vp]),
@@ -412,3 +431,43 @@ def agg_selector_set(params: np.ndarray, mean: np.ndarray, std: np.ndarray) -> N
 def agg_rule_strategy(features, ops: int) -> int:
     f = np.ascontiguousarray(features, dtype=np.float32)
     return int(lib().agg_rule_strategy(f.ctypes.data_as(ctypes.c_void_p), ops))
+
+
+class BatchPlan:
+    """A planned batch of GROUP BY queries over device tensors (see agg_batch_plan_create)."""
+
+    def __init__(self, queries, stream=None):
+        """queries: list of (keys, vals, ops, strategy) with device tensors."""
+        self._keep = [(k, v) for k, v, _, _ in queries]
+        arr = (AggQuery * max(1, len(queries)))()
+        for i, (k, v, ops, strat) in enumerate(queries):
+            arr[i].keys = k.data_ptr() if k.numel() else None
+            arr[i].vals = v.data_ptr() if v.numel() else None
+            arr[i].n = k.numel()
+            arr[i].dtype = dtype_code(v)
+            arr[i].ops = ops
+            arr[i].strategy = strat
+        self._arr = arr
+        self.nq = len(queries)
+        h = ctypes.c_void_p()
+        check(lib().agg_batch_plan_create(arr, self.nq, ctypes.byref(h), _stream_ptr(stream)))
+        self._h = h
+
+    def run(self, stream=None):
+        check(lib().agg_batch_run(self._h, _stream_ptr(stream)))
+
+    def result(self, i) -> Groups:
+        out = ctypes.c_void_p()
+        check(lib().agg_batch_result(self._h, i, ctypes.byref(out)))
+        return Groups(out.value)
+
+    def free(self):
+        if self._h:
+            lib().agg_batch_plan_free(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass

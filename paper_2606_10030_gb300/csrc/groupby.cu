@@ -1,625 +1,18 @@
-// GROUP BY with hash tables (steps a5, a5g, a6) and the agg_groupby driver.
-//
-// Build. Every row is folded (the aggregate() of Fig. 4) into the slot of its
-// key in an open-addressing hash table (MurmurHash3 fmix32, linear probing,
-// bounded probe count):
-//   SMEM    each block owns a table in shared memory and updates it with
-//           shared-memory atomics; rows whose key finds no slot within the
-//           probe bound go straight to the global table ("spill"); at the end
-//           the block merges its table into the global one.
-//   GLOBAL  every row updates the global table in HBM with L2 atomics.
-// Keys are stored as key + 1 so that an all-zero table is empty; the key
-// 0xFFFFFFFF has its own side slot after the main slots. All accumulators
-// start at zero: count and sum add, MIN is kept as the complement of an
-// order-preserving image and MAX as the image, both updated with atomicMax.
-// Float32 sums in shared memory are TwoSum-compensated float32 pairs updated
-// with a 64-bit compare-and-swap; the merge into the global table and every
-// global update run in float64 atomics.
-//
-// Finalise. Occupied slots are sorted by key (one-block bitonic sort for small
-// tables; compaction + radix sort otherwise) and written out in ascending key
-// order, with AVG = SUM / COUNT and MIN/MAX decoded.
+// GROUP BY driver (steps a5, a5g, a5s, a6, a7): sketch, strategy choice,
+// table sizing and regrowth, the single-query hash path, the host-fed
+// (end-to-end) path and the C entry points. The device code of the hash
+// strategies is in hashtab.cuh; the sort strategy in sortagg.cu.
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <tuple>
 #include <map>
 #include <mutex>
+#include <tuple>
 
-#include "groupby.cuh"
+#include "hashtab.cuh"
 #include "sort.cuh"
 
 namespace agg {
-
-// ---------------------------------------------------------------------------
-// Value traits: order-preserving 64-bit image of a value.
-// ---------------------------------------------------------------------------
-template <int DT> struct GV;
-template <> struct GV<AGG_I32> {
-  using T = int32_t;
-  __device__ static uint64_t img(T v) { return img_i64((int64_t)v); }
-};
-template <> struct GV<AGG_I64> {
-  using T = int64_t;
-  __device__ static uint64_t img(T v) { return img_i64(v); }
-};
-template <> struct GV<AGG_U32> {
-  using T = uint32_t;
-  __device__ static uint64_t img(T v) { return img_i64((int64_t)v); }
-};
-template <> struct GV<AGG_F32> {
-  using T = float;
-  __device__ static uint64_t img(T v) { return (uint64_t)img_f32(v); }
-};
-template <> struct GV<AGG_F64> {
-  using T = double;
-  __device__ static uint64_t img(T v) { return img_f64(v); }
-};
-
-template <bool MM> struct GSlot;
-template <> struct __align__(16) GSlot<false> {
-  uint32_t key1;
-  uint32_t cnt;
-  unsigned long long sum;
-};
-template <> struct __align__(32) GSlot<true> {
-  uint32_t key1;
-  uint32_t cnt;
-  unsigned long long sum;
-  unsigned long long minc;
-  unsigned long long mx;
-};
-
-constexpr int kGlobalProbe = 128;
-constexpr int kSmemProbe = 8;
-constexpr int kStatusFull = 1;
-
-struct BuildArgs {
-  const uint32_t* keys;
-  const void* vals;
-  int64_t n;
-  int64_t head;        // rows before the 16-byte aligned body (vector path)
-  void* table;         // GSlot[mask + 2]
-  uint32_t mask;       // main slots - 1 (main slots a power of two)
-  int smem_slots;      // S (power of two) for SMEM, else 0
-  int smem_cap;        // max keys inserted into the shared table
-  int* status;
-};
-
-// Global slot of key (insert if absent); -1 if no slot within the probe bound.
-template <bool MM>
-__device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, uint32_t key) {
-  if (key == 0xFFFFFFFFu) return (int64_t)mask + 1;
-  const uint32_t k1 = key + 1;
-  uint32_t h = fmix32(key) & mask;
-#pragma unroll 1
-  for (int p = 0; p < kGlobalProbe; ++p) {
-    uint32_t cur = *(volatile uint32_t*)&tab[h].key1;
-    if (cur == k1) return h;
-    if (cur == 0) {
-      uint32_t old = atomicCAS(&tab[h].key1, 0u, k1);
-      if (old == 0u || old == k1) return h;
-    }
-    h = (h + 1) & mask;
-  }
-  return -1;
-}
-
-// Fold one row (or a merged partial) into a global slot.
-template <int DT, bool MM>
-__device__ __forceinline__ void g_add_row(GSlot<MM>& s, typename GV<DT>::T v) {
-  atomicAdd(&s.cnt, 1u);
-  if (DT == AGG_F32 || DT == AGG_F64) {
-    atomicAdd((double*)&s.sum, (double)v);
-  } else {
-    atomicAdd(&s.sum, (unsigned long long)(int64_t)v);
-  }
-  if (MM) {
-    const uint64_t m = GV<DT>::img(v);
-    atomicMax(&((GSlot<true>&)s).minc, (unsigned long long)~m);
-    atomicMax(&((GSlot<true>&)s).mx, (unsigned long long)m);
-  }
-}
-
-// Shared-memory table over S + 1 slots (S a power of two >= 64; slot S holds
-// the key 0xFFFFFFFF). Keys are probed a bucket of 4 slots at a time with one
-// 16-byte load. Every per-row update uses native 32-bit shared atomics:
-//   count     u32 add
-//   sum       integers: two u32 words; the low word's atomic add returns the
-//             previous value, so the adding thread sees its own carry exactly
-//             and adds it with the high part (the pair is the 64-bit sum mod
-//             2^64). float32: s and c words; the adder recovers the rounding
-//             error of its own atomic add of s with TwoSum from the returned
-//             previous value and adds that error to c. float64: one 64-bit
-//             float atomic add.
-//   MIN/MAX   an adjacent (min, max) pair of order-preserving images (32-bit
-//             for 4-byte values); an atomic is issued only when the value
-//             improves the current extreme.
-// Rows are handled in batches: all lookups first, then all count updates,
-// all sum updates and all min/max updates, so that shared-memory latencies
-// overlap instead of forming one dependent chain per row.
-template <int DT> struct SImg { using U = uint32_t; };
-template <> struct SImg<AGG_I64> { using U = unsigned long long; };
-template <> struct SImg<AGG_F64> { using U = unsigned long long; };
-
-template <int DT>
-__device__ __forceinline__ typename SImg<DT>::U s_img(typename GV<DT>::T v) {
-  if (DT == AGG_I32) return (uint32_t)(int32_t)v ^ 0x80000000u;
-  if (DT == AGG_U32) return (uint32_t)v;
-  if (DT == AGG_F32) return img_f32((float)v);
-  if (DT == AGG_I64) return (unsigned long long)img_i64((int64_t)v);
-  return (unsigned long long)img_f64((double)v);
-}
-// shared image -> the 64-bit image kept in the global table (GV<DT>::img)
-template <int DT>
-__device__ __forceinline__ uint64_t g_img_of(typename SImg<DT>::U m) {
-  if (DT == AGG_I32) return img_i64((int64_t)(int32_t)((uint32_t)m ^ 0x80000000u));
-  if (DT == AGG_U32) return img_i64((int64_t)(uint32_t)m);
-  return (uint64_t)m;
-}
-
-template <int DT, bool MM>
-struct STab {
-  using U = typename SImg<DT>::U;
-  unsigned long long* sum;  // 64-bit word per slot (two u32 halves for integers / float32)
-  U* mm;                    // (min, max) image pairs
-  uint32_t* key1;           // key + 1, 0 = empty (16-byte aligned)
-  uint32_t* cnt;
-  int* used;
-  __device__ void carve(unsigned char* base, int S) {
-    sum = (unsigned long long*)base;
-    unsigned char* p = (unsigned char*)(sum + (S + 1));
-    p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    if (MM) {
-      mm = (U*)p;
-      p = (unsigned char*)(mm + 2 * (S + 1));
-      p = (unsigned char*)(((uintptr_t)p + 15) & ~(uintptr_t)15);
-    }
-    key1 = (uint32_t*)p;
-    cnt = key1 + (S + 4);
-    used = (int*)(cnt + (S + 1));
-  }
-  __device__ void clear(int S) {
-    for (int i = threadIdx.x; i <= S; i += blockDim.x) {
-      sum[i] = 0;
-      if (MM) {
-        mm[2 * i] = (U)~(U)0;
-        mm[2 * i + 1] = 0;
-      }
-      cnt[i] = 0;
-    }
-    for (int i = threadIdx.x; i < S + 4; i += blockDim.x) key1[i] = 0;
-    if (threadIdx.x == 0) *used = 0;
-  }
-};
-
-template <int DT, bool MM>
-__host__ __device__ inline size_t stab_bytes(int S) {
-  const size_t img = (DT == AGG_I64 || DT == AGG_F64) ? 8 : 4;
-  return (size_t)(S + 1) * 8 + 16 + (MM ? 2 * img * (S + 1) + 16 : 0) + (size_t)(S + 4) * 4 + (size_t)(S + 1) * 4 +
-         16;
-}
-
-constexpr int kSmemBuckets = 4;  // buckets of 4 slots probed before a row spills
-
-// Shared-memory vector loads that are re-issued every time (values written by
-// other threads may change). A stale value is harmless for every use below:
-// keys only go from empty to set, minima only fall and maxima only rise.
-__device__ __forceinline__ uint4 lds_v4(const void* p) {
-  uint4 v;
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ld.volatile.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ uint2 lds_v2(const void* p) {
-  uint2 v;
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ld.volatile.shared.v2.u32 {%0,%1}, [%2];" : "=r"(v.x), "=r"(v.y) : "r"(a));
-  return v;
-}
-__device__ __forceinline__ ulonglong2 lds_v2_64(const void* p) {
-  ulonglong2 v;
-  const unsigned a = (unsigned)__cvta_generic_to_shared(p);
-  asm volatile("ld.volatile.shared.v2.u64 {%0,%1}, [%2];" : "=l"(v.x), "=l"(v.y) : "r"(a));
-  return v;
-}
-
-// Fast path: the key's slot if it sits in its home bucket, else -1 (one
-// 16-byte shared load, no branches on the data).
-template <int DT, bool MM>
-__device__ __forceinline__ int s_find_home(const STab<DT, MM>& t, int S, uint32_t key) {
-  const uint32_t k1 = key + 1;
-  const uint32_t b = fmix32(key) & (uint32_t)(S - 1) & ~3u;
-  const uint4 q = lds_v4(&t.key1[b]);
-  int j = -1;
-  j = q.w == k1 ? (int)b + 3 : j;
-  j = q.z == k1 ? (int)b + 2 : j;
-  j = q.y == k1 ? (int)b + 1 : j;
-  j = q.x == k1 ? (int)b : j;
-  return key == 0xFFFFFFFFu ? S : j;
-}
-
-// Slot of key in the shared table (inserting it if there is room), or -1.
-template <int DT, bool MM>
-__device__ __noinline__ int s_lookup(const STab<DT, MM>& t, int S, int cap, uint32_t key) {
-  if (key == 0xFFFFFFFFu) return S;
-  const uint32_t k1 = key + 1;
-  uint32_t b = fmix32(key) & (uint32_t)(S - 1) & ~3u;
-#pragma unroll 1
-  for (int p = 0; p < kSmemBuckets; ++p) {
-    uint4 q = lds_v4(&t.key1[b]);
-    if (q.x == k1) return (int)b;
-    if (q.y == k1) return (int)b + 1;
-    if (q.z == k1) return (int)b + 2;
-    if (q.w == k1) return (int)b + 3;
-    // claim an empty slot of this bucket; each failed claim fills a slot, so
-    // this loop runs at most 4 times
-#pragma unroll 1
-    for (int tries = 0; tries < 4; ++tries) {
-      const int e = q.x == 0 ? 0 : q.y == 0 ? 1 : q.z == 0 ? 2 : q.w == 0 ? 3 : -1;
-      if (e < 0) break;
-      if (*(volatile int*)t.used >= cap) return -1;  // full enough: no new keys
-      const uint32_t old = atomicCAS(&t.key1[b + e], 0u, k1);
-      if (old == 0u) {
-        atomicAdd(t.used, 1);
-        return (int)b + e;
-      }
-      if (old == k1) return (int)b + e;
-      q = lds_v4(&t.key1[b]);
-      if (q.x == k1) return (int)b;
-      if (q.y == k1) return (int)b + 1;
-      if (q.z == k1) return (int)b + 2;
-      if (q.w == k1) return (int)b + 3;
-    }
-    b = (b + 4) & (uint32_t)(S - 1);
-  }
-  return -1;
-}
-
-// Fold a row into the global table. MIN/MAX atomics are skipped when the
-// value does not improve the slot's current extreme.
-template <int DT, bool MM>
-__device__ __forceinline__ void g_add_row_cached(GSlot<MM>& s, typename GV<DT>::T v) {
-  atomicAdd(&s.cnt, 1u);
-  if (DT == AGG_F32 || DT == AGG_F64) {
-    atomicAdd((double*)&s.sum, (double)v);
-  } else {
-    atomicAdd(&s.sum, (unsigned long long)(int64_t)v);
-  }
-  if (MM) {
-    GSlot<true>& w = (GSlot<true>&)s;
-    const uint64_t m = GV<DT>::img(v);
-    if (~m > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~m);
-    if (m > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)m);
-  }
-}
-
-template <int DT, bool MM>
-__device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
-  GSlot<MM>* tab = (GSlot<MM>*)a.table;
-  const int64_t g = g_slot<MM>(tab, a.mask, key);
-  if (g < 0) {
-    *(volatile int*)a.status = kStatusFull;
-    return;
-  }
-  g_add_row_cached<DT, MM>(tab[g], v);
-}
-
-// Fold a batch of N rows (valid[r] false = skip).
-template <int DT, bool MM, bool SMEM, int N>
-__device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
-                                           const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
-  using T = typename GV<DT>::T;
-  using U = typename SImg<DT>::U;
-  if (!SMEM) {
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-      if (valid[r]) g_row<DT, MM>(a, key[r], val[r]);
-    return;
-  }
-  int j[N];
-#pragma unroll
-  for (int r = 0; r < N; ++r) j[r] = valid[r] ? s_find_home<DT, MM>(st, a.smem_slots, key[r]) : -2;
-#pragma unroll
-  for (int r = 0; r < N; ++r)
-    if (j[r] == -1) j[r] = s_lookup<DT, MM>(st, a.smem_slots, a.smem_cap, key[r]);
-#pragma unroll
-  for (int r = 0; r < N; ++r)
-    if (j[r] >= 0) atomicAdd(&st.cnt[j[r]], 1u);
-  if (DT == AGG_F32) {
-    float old[N];
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-      if (j[r] >= 0) old[r] = atomicAdd((float*)&st.sum[j[r]], (float)val[r]);
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      if (j[r] >= 0) {
-        float t, e;
-        two_sum(old[r], (float)val[r], t, e);  // t is what the atomic stored; e its rounding error
-        if (e != 0.f) atomicAdd((float*)&st.sum[j[r]] + 1, e);
-      }
-    }
-  } else if (DT == AGG_F64) {
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-      if (j[r] >= 0) atomicAdd((double*)&st.sum[j[r]], (double)val[r]);
-  } else {
-    uint32_t old[N];
-#pragma unroll
-    for (int r = 0; r < N; ++r)
-      if (j[r] >= 0) old[r] = atomicAdd((uint32_t*)&st.sum[j[r]], (uint32_t)(uint64_t)(int64_t)val[r]);
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      if (j[r] >= 0) {
-        const uint64_t u = (uint64_t)(int64_t)val[r];
-        const uint32_t lo = (uint32_t)u;
-        const uint32_t hi = (uint32_t)(u >> 32) + ((uint32_t)(old[r] + lo) < old[r] ? 1u : 0u);
-        if (hi) atomicAdd((uint32_t*)&st.sum[j[r]] + 1, hi);
-      }
-    }
-  }
-  if (MM) {
-    U cur_mn[N], cur_mx[N];
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      if (j[r] >= 0) {
-        if (sizeof(U) == 4) {
-          const uint2 q = lds_v2(&st.mm[2 * j[r]]);
-          cur_mn[r] = (U)q.x;
-          cur_mx[r] = (U)q.y;
-        } else {
-          const ulonglong2 q = lds_v2_64(&st.mm[2 * j[r]]);
-          cur_mn[r] = (U)q.x;
-          cur_mx[r] = (U)q.y;
-        }
-      }
-    }
-#pragma unroll
-    for (int r = 0; r < N; ++r) {
-      if (j[r] >= 0) {
-        const U m = s_img<DT>(val[r]);
-        if (m < cur_mn[r]) atomicMin(&st.mm[2 * j[r]], m);
-        if (m > cur_mx[r]) atomicMax(&st.mm[2 * j[r] + 1], m);
-      }
-    }
-  }
-#pragma unroll
-  for (int r = 0; r < N; ++r)
-    if (j[r] == -1) g_row<DT, MM>(a, key[r], val[r]);
-}
-
-template <class T>
-__device__ __forceinline__ void unpack4(const uint4& lo, const uint4& hi, T* v) {
-  if (sizeof(T) == 4) {
-    uint32_t w[4] = {lo.x, lo.y, lo.z, lo.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      uint32_t x = w[i];
-      memcpy(&v[i], &x, 4);
-    }
-  } else {
-    uint64_t w[4] = {((uint64_t)lo.y << 32) | lo.x, ((uint64_t)lo.w << 32) | lo.z, ((uint64_t)hi.y << 32) | hi.x,
-                     ((uint64_t)hi.w << 32) | hi.z};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) memcpy(&v[i], &w[i], 8);
-  }
-}
-
-// The build kernel. VEC: 16-byte vector loads of 4 keys and 4 values per quad,
-// two quads (8 rows) per thread per iteration, folded in batches of kBatch.
-constexpr int kBatch = 1;
-template <int DT, bool MM, bool SMEM, bool VEC>
-__global__ void gb_build(BuildArgs a) {
-  using T = typename GV<DT>::T;
-  extern __shared__ __align__(16) unsigned char smem[];
-  STab<DT, MM> st;
-  if (SMEM) {
-    st.carve(smem, a.smem_slots);
-    st.clear(a.smem_slots);
-    __syncthreads();
-  }
-  const uint32_t* keys = a.keys;
-  const T* vals = (const T*)a.vals;
-  const int64_t gtid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
-  if (VEC) {
-    const int64_t nq = (a.n - a.head) / 4;  // full quads of rows
-    const int64_t tail0 = a.head + nq * 4;
-    {
-      uint32_t k1[1];
-      T v1[1];
-      bool ok1[1];
-      ok1[0] = gtid < a.head;
-      k1[0] = ok1[0] ? keys[gtid] : 0u;
-      v1[0] = ok1[0] ? vals[gtid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
-      ok1[0] = gtid < a.n - tail0;
-      k1[0] = ok1[0] ? keys[tail0 + gtid] : 0u;
-      v1[0] = ok1[0] ? vals[tail0 + gtid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
-    }
-    const uint4* kq = (const uint4*)(keys + a.head);
-    const uint4* vq = (const uint4*)(vals + a.head);
-    constexpr int VPQ = sizeof(T) == 4 ? 1 : 2;  // 16-byte value vectors per quad
-    int it = 0;
-    for (int64_t q = gtid; q < nq; q += 2 * nthreads) {
-      const int64_t q2 = q + nthreads;
-      const bool has2 = q2 < nq;
-      const uint4 k0 = ld_stream_v4(kq + q);
-      const uint4 v0a = ld_stream_v4(vq + q * VPQ);
-      const uint4 v0b = VPQ == 2 ? ld_stream_v4(vq + q * VPQ + 1) : v0a;
-      uint4 k1 = make_uint4(0, 0, 0, 0), v1a = k1, v1b = k1;
-      if (has2) {
-        k1 = ld_stream_v4(kq + q2);
-        v1a = ld_stream_v4(vq + q2 * VPQ);
-        v1b = VPQ == 2 ? ld_stream_v4(vq + q2 * VPQ + 1) : v1a;
-      }
-      uint32_t key[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-      T val[8];
-      unpack4<T>(v0a, v0b, val);
-      unpack4<T>(v1a, v1b, val + 4);
-#pragma unroll
-      for (int r0 = 0; r0 < 8; r0 += kBatch) {
-        uint32_t kb[kBatch];
-        T vb[kBatch];
-        bool ok[kBatch];
-#pragma unroll
-        for (int r = 0; r < kBatch; ++r) {
-          kb[r] = key[r0 + r];
-          vb[r] = val[r0 + r];
-          ok[r] = r0 + r < 4 || has2;
-        }
-        fold_batch<DT, MM, SMEM, kBatch>(a, st, kb, vb, ok);
-      }
-      if ((++it & 15) == 0 && *(volatile int*)a.status) break;  // table full: the build is redone
-    }
-  } else {
-    int it = 0;
-    for (int64_t i = gtid; i < a.n; i += nthreads) {
-      uint32_t k1[1] = {keys[i]};
-      T v1[1] = {vals[i]};
-      bool ok1[1] = {true};
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
-      if ((++it & 63) == 0 && *(volatile int*)a.status) break;
-    }
-  }
-  if (!SMEM) return;
-  __syncthreads();
-  // merge the block's shared table into the global table
-  GSlot<MM>* tab = (GSlot<MM>*)a.table;
-  const int S = a.smem_slots;
-  for (int j = threadIdx.x; j <= S; j += blockDim.x) {
-    const uint32_t c = st.cnt[j];
-    if (c == 0) continue;
-    const uint32_t key = j == S ? 0xFFFFFFFFu : st.key1[j] - 1;
-    const int64_t g = g_slot<MM>(tab, a.mask, key);
-    if (g < 0) {
-      *(volatile int*)a.status = kStatusFull;
-      continue;
-    }
-    GSlot<MM>& gs = tab[g];
-    atomicAdd(&gs.cnt, c);
-    const unsigned long long sv = st.sum[j];
-    if (DT == AGG_F32) {
-      const double d = (double)__uint_as_float((uint32_t)sv) + (double)__uint_as_float((uint32_t)(sv >> 32));
-      atomicAdd((double*)&gs.sum, d);
-    } else if (DT == AGG_F64) {
-      atomicAdd((double*)&gs.sum, __longlong_as_double((long long)sv));
-    } else {
-      atomicAdd(&gs.sum, sv);
-    }
-    if (MM) {
-      GSlot<true>& w = (GSlot<true>&)gs;
-      const uint64_t mn = g_img_of<DT>(st.mm[2 * j]), mx = g_img_of<DT>(st.mm[2 * j + 1]);
-      if (~mn > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~mn);
-      if (mx > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)mx);
-    }
-  }
-}
-
-// ---------------------------------------------------------------------------
-// Finalise.
-// ---------------------------------------------------------------------------
-struct OutArrays {
-  uint32_t* keys;
-  int64_t* count;
-  unsigned long long* sum;
-  unsigned long long* min;
-  unsigned long long* max;
-  double* avg;
-  int64_t* d;  // number of groups (device)
-};
-
-template <int DT, bool MM>
-__device__ __forceinline__ void write_group(const OutArrays& o, int64_t i, uint32_t key, const GSlot<MM>& s) {
-  const uint32_t c = s.cnt;
-  o.keys[i] = key;
-  o.count[i] = c;
-  const unsigned long long sv = s.sum;
-  o.sum[i] = sv;
-  double fsum;
-  if (DT == AGG_F32 || DT == AGG_F64) fsum = __longlong_as_double((long long)sv);
-  else fsum = (double)(long long)sv;
-  o.avg[i] = fsum / (double)c;
-  if (MM) {
-    const GSlot<true>& w = (const GSlot<true>&)s;
-    const uint64_t mn = ~w.minc, mx = w.mx;
-    if (DT == AGG_F32) {
-      o.min[i] = (unsigned long long)__double_as_longlong((double)f32_of_img((uint32_t)mn));
-      o.max[i] = (unsigned long long)__double_as_longlong((double)f32_of_img((uint32_t)mx));
-    } else if (DT == AGG_F64) {
-      o.min[i] = (unsigned long long)__double_as_longlong(f64_of_img(mn));
-      o.max[i] = (unsigned long long)__double_as_longlong(f64_of_img(mx));
-    } else {
-      o.min[i] = (unsigned long long)i64_of_img(mn);
-      o.max[i] = (unsigned long long)i64_of_img(mx);
-    }
-  }
-}
-
-template <bool MM>
-__device__ __forceinline__ bool occupied(const GSlot<MM>* tab, uint32_t mask, int64_t j) {
-  return j <= (int64_t)mask ? tab[j].key1 != 0 : tab[j].cnt != 0;
-}
-
-template <bool MM>
-__device__ __forceinline__ uint32_t key_of(const GSlot<MM>* tab, uint32_t mask, int64_t j) {
-  return j <= (int64_t)mask ? tab[j].key1 - 1 : 0xFFFFFFFFu;
-}
-
-// Small tables (at most kSmallRank occupied slots): after compaction, every
-// block loads all d distinct keys into shared memory and writes each of its
-// keys at its rank (the number of smaller keys); keys are distinct, so the
-// ranks are a permutation and the output is in ascending key order.
-constexpr int kSmallRank = 4097;
-constexpr int kRankThreads = 256;
-
-template <int DT, bool MM>
-__global__ void __launch_bounds__(kRankThreads) gb_rank_gather(const GSlot<MM>* tab, const uint32_t* ckeys,
-                                                               const uint32_t* cslot, OutArrays o) {
-  __shared__ uint32_t sk[kSmallRank];
-  const int d = (int)*(const unsigned long long*)o.d;
-  for (int t = threadIdx.x; t < d; t += kRankThreads) sk[t] = ckeys[t];
-  __syncthreads();
-  const int i = blockIdx.x * kRankThreads + threadIdx.x;
-  if (i >= d) return;
-  const uint32_t key = sk[i];
-  int rank = 0;
-#pragma unroll 8
-  for (int t = 0; t < d; ++t) rank += sk[t] < key ? 1 : 0;
-  write_group<DT, MM>(o, rank, key, tab[cslot[i]]);
-}
-
-// Large tables: compact occupied slots into (key, slot) pairs.
-template <bool MM>
-__global__ void gb_compact(const GSlot<MM>* tab, uint32_t mask, uint32_t* okeys, uint32_t* oslot,
-                           unsigned long long* counter) {
-  const int64_t nslots = (int64_t)mask + 2;
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nslots; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = base + threadIdx.x;
-    const bool occ = j < nslots && occupied<MM>(tab, mask, j);
-    const uint32_t b = __ballot_sync(0xffffffffu, occ);
-    unsigned long long w0 = 0;
-    if (lane == 0 && b) w0 = atomicAdd(counter, (unsigned long long)__popc(b));
-    w0 = __shfl_sync(0xffffffffu, w0, 0);
-    if (occ) {
-      const unsigned long long pos = w0 + __popc(b & ((1u << lane) - 1u));
-      okeys[pos] = key_of<MM>(tab, mask, j);
-      oslot[pos] = (uint32_t)j;
-    }
-  }
-}
-
-template <int DT, bool MM>
-__global__ void gb_gather(const GSlot<MM>* tab, const uint32_t* skeys, const uint32_t* sslot, OutArrays o,
-                          int64_t cap) {
-  const int64_t d = *(const unsigned long long*)o.d;
-  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d && i < cap;
-       i += (int64_t)gridDim.x * blockDim.x) {
-    write_group<DT, MM>(o, i, skeys[i], tab[sslot[i]]);
-  }
-}
 
 // ---------------------------------------------------------------------------
 // Host side.
@@ -1314,6 +707,11 @@ extern "C" agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, in
 extern "C" void agg_groups_free(agg_groups* g) {
   if (!g) return;
   GroupsPriv* p = (GroupsPriv*)g->priv;
+  if (p && p->shared) {
+    shared_block_release(p->shared);
+    delete p;
+    p = nullptr;
+  }
   if (p) {
     int cur = 0;
     cudaGetDevice(&cur);

@@ -16,6 +16,15 @@ constexpr int kSketchSample = 4096;
 agg_status sketch_launch(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset, float* feat_dev,
                          cudaStream_t s);
 
+// One query of a batched sketch launch.
+struct SketchJob {
+  const uint32_t* keys;
+  int64_t n;
+  uint64_t offset;
+  int vbytes, nops, fp, slot_bytes;
+};
+agg_status sketch_batch_launch(const SketchJob* jobs_dev, int nq, float* feat_dev, cudaStream_t s);
+
 // Sketch the keys and read the features back to the host (one sync).
 agg_status sketch_features(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
                            cudaStream_t s, float* feat);
@@ -29,9 +38,14 @@ int rule_strategy(const float* feat, uint32_t ops);
 // Distinct-key estimate from the sketch (*covered: the sample covers >= 90% of the mass).
 double distinct_estimate(const float* feat, bool* covered);
 
+// Output block shared by the results of one batch (reference counted).
+struct SharedBlock;
+void shared_block_release(SharedBlock* b);
+
 // Library-private part of an agg_groups.
 struct GroupsPriv {
-  void* block = nullptr;  // one device allocation holding every output array
+  void* block = nullptr;          // one device allocation holding every output array
+  SharedBlock* shared = nullptr;  // or a reference to a batch's output block
   int device = 0;
 };
 

@@ -264,6 +264,25 @@ agg_status sketch_and_select(const uint32_t* keys, int64_t n, int vdt, uint32_t 
   return AGG_OK;
 }
 
+// Batched sketch, then (with a selector installed) the network on all the
+// sketches in one launch.
+agg_status batch_select(const SketchJob* jobs_dev, int nq, float* feat_dev, float* probs_dev, cudaStream_t s,
+                        bool* have_probs) {
+  *have_probs = false;
+  agg_status st = sketch_batch_launch(jobs_dev, nq, feat_dev, s);
+  if (st != AGG_OK) return st;
+  float* sel = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_sel_mu);
+    Selector* S = selector_for_device();
+    if (S && S->ok) sel = S->dev;
+  }
+  if (!sel) return AGG_OK;
+  st = mlp_launch(sel, sel + kParamsPad, sel + kParamsPad + kIn, feat_dev, nullptr, nq, probs_dev, nullptr, nullptr, s);
+  if (st == AGG_OK) *have_probs = true;
+  return st;
+}
+
 // Strategy from host features (used by the host-fed path): one tiny launch.
 int select_learned(const float* feat, bool* ok) {
   *ok = false;

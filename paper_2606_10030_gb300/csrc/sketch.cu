@@ -31,10 +31,9 @@ __device__ double block_sum_d(double v, double* red) {
 // (64-bit slots holding key << 1 | 1, so every key value is representable),
 // their counts histogrammed, and the 32 largest counts read off the histogram
 // from the top by one warp.
-__global__ void __launch_bounds__(kSketchThreads) sketch_kernel(const uint32_t* __restrict__ keys, int64_t n,
-                                                                int vbytes, int nops, int fp, int slot_bytes,
-                                                                uint64_t offset, double smem_bytes, double l2_bytes,
-                                                                float* __restrict__ feat) {
+__device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int vbytes, int nops, int fp,
+                             int slot_bytes, uint64_t offset, double smem_bytes, double l2_bytes,
+                             float* __restrict__ feat) {
   extern __shared__ __align__(16) unsigned char sm[];
   unsigned long long* slot = (unsigned long long*)sm;            // kSketchSlots
   uint32_t* cnt = (uint32_t*)(slot + kSketchSlots);              // kSketchSlots
@@ -166,6 +165,39 @@ __global__ void __launch_bounds__(kSketchThreads) sketch_kernel(const uint32_t* 
   f[F_SMEM_RATIO] = (float)log2(1.0 + tbytes / smem_bytes);
   f[F_L2_RATIO] = (float)log2(1.0 + tbytes / l2_bytes);
   f[F_LOG2_RANGE] = (float)log2((double)(s_kmax - s_kmin) + 1.0);
+}
+
+__global__ void __launch_bounds__(kSketchThreads) sketch_kernel(const uint32_t* __restrict__ keys, int64_t n,
+                                                                int vbytes, int nops, int fp, int slot_bytes,
+                                                                uint64_t offset, double smem_bytes, double l2_bytes,
+                                                                float* __restrict__ feat) {
+  sketch_block(keys, n, vbytes, nops, fp, slot_bytes, offset, smem_bytes, l2_bytes, feat);
+}
+
+// One block per query of a batch.
+__global__ void __launch_bounds__(kSketchThreads) sketch_batch_kernel(const SketchJob* __restrict__ jobs,
+                                                                      double smem_bytes, double l2_bytes,
+                                                                      float* __restrict__ feat) {
+  const SketchJob j = jobs[blockIdx.x];
+  sketch_block(j.keys, j.n, j.vbytes, j.nops, j.fp, j.slot_bytes, j.offset, smem_bytes, l2_bytes,
+               feat + (size_t)blockIdx.x * F_COUNT);
+}
+
+agg_status sketch_batch_launch(const SketchJob* jobs_dev, int nq, float* feat_dev, cudaStream_t s) {
+  const DeviceInfo& di = device_info();
+  static bool attr_set[64] = {};
+  if (di.device >= 0 && di.device < 64 && !attr_set[di.device]) {
+    AGG_CUDA_TRY(
+        cudaFuncSetAttribute(sketch_batch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem));
+    attr_set[di.device] = true;
+  }
+  if (nq <= 0) return AGG_OK;
+  PhaseTimer pt(AGG_PHASE_SKETCH, s);
+  sketch_batch_kernel<<<nq, kSketchThreads, kSketchSmem, s>>>(jobs_dev, (double)di.smem_per_block_optin,
+                                                              (double)di.l2_bytes, feat_dev);
+  note_launch();
+  AGG_CUDA_TRY(cudaGetLastError());
+  return AGG_OK;
 }
 
 agg_status sketch_launch(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset, float* feat_dev,

@@ -244,13 +244,8 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
   size_t cbytes = ((size_t)256 * ntiles * sizeof(uint32_t) + 255) & ~size_t(255);
   void* stmp = (char*)tmp + cbytes;
   const size_t sm = scatter_smem<P>();
-  static bool attr_set[64] = {};  // per device; the attribute belongs to the function on a device
-  int dev = 0;
-  cudaGetDevice(&dev);
-  if (dev >= 64 || !attr_set[dev]) {
-    AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<P>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    if (dev < 64) attr_set[dev] = true;
-  }
+  agg_status pst = radix_prepare();  // a no-op once done on this device
+  if (pst != AGG_OK) return pst;
   const uint32_t* ki = kin;
   const P* vi = vin;
   int pass = 0;
@@ -269,6 +264,19 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
     *kout = ko;
     *vout = vo;
   }
+  return AGG_OK;
+}
+
+agg_status radix_prepare() {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static bool done[64] = {};
+  if (dev < 64 && done[dev]) return AGG_OK;
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem<uint32_t>()));
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem<uint64_t>()));
+  if (dev < 64) done[dev] = true;
   return AGG_OK;
 }
 

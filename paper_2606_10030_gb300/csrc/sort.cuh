@@ -29,6 +29,9 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
                             int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
                             uint32_t** kout, P** vout);
 
+// Set the kernel attributes the sort needs (call before a stream capture).
+agg_status radix_prepare();
+
 // Small-sort capacity of the single-block bitonic sorter used for small tables.
 constexpr int kSmallSort = 8192;
 
