@@ -145,8 +145,10 @@ typedef struct agg_options {
   int32_t smem_slots;      /* shared-memory table slots (power of two, <= 8192); 0 = from the sketch */
   int64_t table_slots;     /* global table slots (power of two); 0 = from the sketch */
   uint64_t sample_offset;  /* offset of the strided key sample (pass a seeded draw) */
-  int32_t items_per_thread;/* rows per thread per loop iteration (4 or 8); 0 = default */
-  int32_t reserved[3];
+  int32_t items_per_thread;/* reserved for a rows-per-thread knob; must be 0 */
+  int32_t partition;       /* hash-partition the rows before a hash build: 0 = when the global table
+                              is larger than half of L2, 1 = always, -1 = never */
+  int32_t reserved[2];
 } agg_options;
 
 /*

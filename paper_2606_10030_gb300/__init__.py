@@ -78,7 +78,8 @@ class AggOptions(ctypes.Structure):
         ("table_slots", ctypes.c_int64),
         ("sample_offset", ctypes.c_uint64),
         ("items_per_thread", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 3),
+        ("partition", ctypes.c_int32),
+        ("reserved", ctypes.c_int32 * 2),
     ]
 
 

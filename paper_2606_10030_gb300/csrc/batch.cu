@@ -48,7 +48,7 @@ struct BQ {  // one query of a batch, on the device
   uint32_t mask;
   int dt, mm, smem, vec;
   int smem_slots, smem_cap;
-  int pad;
+  int gshift;
 };
 
 template <int DT, bool MM, bool SMEM>
@@ -61,6 +61,7 @@ __device__ void batch_tile(const BQ& q, int64_t r0, int64_t r1, unsigned char* s
   a.head = 0;
   a.table = q.table;
   a.mask = q.mask;
+  a.gshift = q.gshift;
   a.smem_slots = SMEM ? q.smem_slots : 0;
   a.smem_cap = SMEM ? q.smem_cap : 0;
   a.status = q.status;
@@ -439,6 +440,7 @@ static agg_status plan_alloc(agg_batch_plan* P, cudaStream_t s) {
     b.status = P->status + i;
     b.slot0 = qp.large ? slot_prefix[li++] : -1;
     b.mask = (uint32_t)(qp.slots - 1);
+    b.gshift = 32 - (63 - __builtin_clzll((unsigned long long)qp.slots));
     b.dt = q.dtype;
     b.mm = qp.mm ? 1 : 0;
     b.smem = qp.strategy == AGG_STRAT_SMEM ? 1 : 0;

@@ -33,6 +33,14 @@ static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec) {
   return nullptr;
 }
 
+static KernelPtr pick_tiles(int dt, bool mm) {
+#define AGG_T(D) \
+  case D: return mm ? (KernelPtr)gb_build_tiles<D, true, true> : (KernelPtr)gb_build_tiles<D, false, true>;
+  switch (dt) { AGG_T(AGG_I32) AGG_T(AGG_I64) AGG_T(AGG_U32) AGG_T(AGG_F32) AGG_T(AGG_F64) }
+#undef AGG_T
+  return nullptr;
+}
+
 template <int DT>
 static KernelPtr fin_small(bool mm) {
   return mm ? (KernelPtr)gb_rank_gather<DT, true> : (KernelPtr)gb_rank_gather<DT, false>;
@@ -146,6 +154,7 @@ agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_
 
 struct HashPlan {
   int strategy;     // AGG_STRAT_SMEM or AGG_STRAT_GLOBAL
+  bool partition = false;  // hash-partition the rows first (table larger than L2)
   int64_t slots;    // global main slots (power of two)
   int smem_slots;   // shared slots (power of two) for SMEM
   int threads;
@@ -195,9 +204,11 @@ class HashRun {
     a.head = head;
     a.table = mem_;
     a.mask = (uint32_t)(plan_.slots - 1);
+    a.gshift = 32 - (63 - __builtin_clzll((unsigned long long)plan_.slots));
     a.smem_slots = use_smem ? plan_.smem_slots : 0;
     a.smem_cap = use_smem ? (plan_.smem_slots * 3) / 4 : 0;
     a.status = status_;
+    if (plan_.partition && n >= kPartTileRows) return build_partitioned(a, use_smem);
     KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec);
     const size_t smem = use_smem ? stab_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;
     const int threads = plan_.threads;
@@ -214,6 +225,69 @@ class HashRun {
     note_launch();
     if (e != cudaSuccess) {
       set_error("group-by build launch failed: %s", cudaGetErrorString(e));
+      return AGG_ERR_CUDA;
+    }
+    return AGG_OK;
+  }
+
+  // Hash-partition the rows (one radix pass on the top 8 hash bits) into
+  // scratch, then build over the partitioned rows: a tile queue with a
+  // per-tile shared table (SMEM) or grid-stride global updates (GLOBAL).
+  agg_status build_partitioned(BuildArgs a, bool use_smem) {
+    const int64_t n = a.n;
+    const size_t es = dtype_size(vdt_);
+    const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255), vb = ((size_t)n * es + 255) & ~size_t(255);
+    void* tmp = nullptr;
+    AGG_CUDA_TRY(cudaMallocAsync(&tmp, kb + vb + radix_tmp_bytes(n), s_));
+    uint32_t* kp = (uint32_t*)tmp;
+    char* vp = (char*)tmp + kb;
+    void* rt = (char*)tmp + kb + vb;
+    agg_status st;
+    {
+      PhaseTimer pt(AGG_PHASE_SORT, s_);
+      st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_)
+                   : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_);
+    }
+    if (st != AGG_OK) {
+      cudaFreeAsync(tmp, s_);
+      return st;
+    }
+    a.keys = kp;
+    a.vals = vp;
+    a.head = 0;
+    const DeviceInfo& di = device_info();
+    cudaError_t e;
+    {
+      PhaseTimer pt(AGG_PHASE_BUILD, s_);
+      if (use_smem) {
+        unsigned long long* next_tile = (unsigned long long*)((char*)mem_ + status_off_ + 128);
+        AGG_CUDA_TRY(cudaMemsetAsync(next_tile, 0, 8, s_));
+        KernelPtr bk = pick_tiles(vdt_, mm_);
+        const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
+        const int threads = plan_.threads;
+        int bps = occupancy(bk, threads, smem);
+        if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
+        int64_t grid = (int64_t)di.sm_count * bps;
+        const int64_t tiles = (n + kPartTileRows - 1) / kPartTileRows;
+        if (tiles < grid) grid = tiles;
+        void* args[] = {&a, &next_tile};
+        e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, smem, s_);
+      } else {
+        KernelPtr bk = pick_build(vdt_, mm_, false, true);
+        const int threads = plan_.threads;
+        int bps = occupancy(bk, threads, 0);
+        if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
+        int64_t grid = (int64_t)di.sm_count * bps;
+        const int64_t need = ((n + 3) / 4 + threads - 1) / threads;
+        if (need < grid) grid = need;
+        void* args[] = {&a};
+        e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, 0, s_);
+      }
+      note_launch();
+    }
+    cudaFreeAsync(tmp, s_);
+    if (e != cudaSuccess) {
+      set_error("partitioned build launch failed: %s", cudaGetErrorString(e));
       return AGG_ERR_CUDA;
     }
     return AGG_OK;
@@ -412,6 +486,8 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   c->plan.smem_slots = sslots ? sslots : smem_slots_for(est, ops_minmax(ops));
   c->plan.threads = o.block_threads ? o.block_threads : (strategy == AGG_STRAT_SMEM ? 512 : 256);
   c->plan.blocks_per_sm = o.blocks_per_sm;
+  const double table_bytes = (double)(c->plan.slots + 2) * gslot_bytes(ops_minmax(ops));
+  c->plan.partition = o.partition > 0 || (o.partition == 0 && table_bytes > 0.5 * device_info().l2_bytes);
   return AGG_OK;
 }
 

@@ -74,17 +74,21 @@ struct BuildArgs {
   int64_t head;        // rows before the 16-byte aligned body (vector path)
   void* table;         // GSlot[mask + 2]
   uint32_t mask;       // main slots - 1 (main slots a power of two)
+  int gshift;          // home slot = fmix32(key) >> gshift (top bits: 32 - log2(main slots))
   int smem_slots;      // S (power of two) for SMEM, else 0
   int smem_cap;        // max keys inserted into the shared table
   int* status;
 };
 
 // Global slot of key (insert if absent); -1 if no slot within the probe bound.
+// The home slot is taken from the top bits of the hash, so keys whose hash
+// shares its top bits (one partition of a hash-partitioned input) live in one
+// contiguous region of the table.
 template <bool MM>
-__device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, uint32_t key) {
+__device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, int shift, uint32_t key) {
   if (key == 0xFFFFFFFFu) return (int64_t)mask + 1;
   const uint32_t k1 = key + 1;
-  uint32_t h = fmix32(key) & mask;
+  uint32_t h = fmix32(key) >> shift;
 #pragma unroll 1
   for (int p = 0; p < kGlobalProbe; ++p) {
     uint32_t cur = *(volatile uint32_t*)&tab[h].key1;
@@ -290,7 +294,7 @@ __device__ __forceinline__ void g_add_row_cached(GSlot<MM>& s, typename GV<DT>::
 template <int DT, bool MM>
 __device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
-  const int64_t g = g_slot<MM>(tab, a.mask, key);
+  const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
   if (g < 0) {
     *(volatile int*)a.status = kStatusFull;
     return;
@@ -481,7 +485,7 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     const uint32_t c = st.cnt[j];
     if (c == 0) continue;
     const uint32_t key = j == S ? 0xFFFFFFFFu : st.key1[j] - 1;
-    const int64_t g = g_slot<MM>(tab, a.mask, key);
+    const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
     if (g < 0) {
       *(volatile int*)a.status = kStatusFull;
       continue;
@@ -521,6 +525,39 @@ __global__ void gb_build(BuildArgs a) {
   if (!SMEM) return;
   __syncthreads();
   flush_smem<DT, MM>(a, st);
+}
+
+// Tile-queue build for hash-partitioned input: blocks pull 64 Ki-row tiles in
+// order from a counter, so all blocks work on neighbouring partitions and the
+// table region they update stays in L2; each tile clears its shared table
+// first and merges it into the global table at the end.
+constexpr int64_t kPartTileRows = int64_t(1) << 16;
+
+template <int DT, bool MM, bool VEC>
+__global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile) {
+  using T = typename GV<DT>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int64_t s_t;
+  STab<DT, MM> st;
+  st.carve(smem, a.smem_slots);
+  for (;;) {
+    if (threadIdx.x == 0) s_t = (int64_t)atomicAdd(next_tile, 1ull);
+    __syncthreads();
+    const int64_t r0 = s_t * kPartTileRows;
+    __syncthreads();
+    if (r0 >= a.n) return;
+    BuildArgs b = a;
+    b.keys = a.keys + r0;
+    b.vals = (const T*)a.vals + r0;
+    b.n = min(kPartTileRows, a.n - r0);
+    b.head = 0;
+    st.clear(a.smem_slots);
+    __syncthreads();
+    build_rows<DT, MM, true, VEC>(b, st, threadIdx.x, blockDim.x);
+    __syncthreads();
+    flush_smem<DT, MM>(b, st);
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------------------

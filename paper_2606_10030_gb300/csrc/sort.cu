@@ -127,6 +127,14 @@ __device__ __forceinline__ int64_t rows_of(int64_t n_cap, const int64_t* n_dev) 
   return n < n_cap ? n : n_cap;
 }
 
+// Digit of a key: 8 bits of the key itself, or (HASHED) of its MurmurHash3
+// fmix32 image, which spreads any key distribution evenly over the digits.
+template <bool HASHED>
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, int shift) {
+  return ((HASHED ? fmix32(key) : key) >> shift) & 0xFFu;
+}
+
+template <bool HASHED>
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __restrict__ keys, int64_t n_cap,
                                                            const int64_t* n_dev, int shift, int64_t ntiles,
                                                            uint32_t* __restrict__ counts) {
@@ -138,13 +146,13 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
 #pragma unroll 4
   for (int i = 0; i < kSortItems; ++i) {
     int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
-    if (j < n) atomicAdd(&h[(keys[j] >> shift) & 0xFF], 1u);
+    if (j < n) atomicAdd(&h[digit_of<HASHED>(keys[j], shift)], 1u);
   }
   __syncthreads();
   counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-template <class P>
+template <class P, bool HASHED>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __restrict__ keys,
                                                               const P* __restrict__ vals, uint32_t* __restrict__ okeys,
                                                               P* __restrict__ ovals, int64_t n_cap,
@@ -176,7 +184,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
     const bool ok = j < n;
     k[r] = ok ? keys[j] : 0u;
     v[r] = ok ? vals[j] : P(0);
-    const uint32_t d = (k[r] >> shift) & 0xFFu;
+    const uint32_t d = digit_of<HASHED>(k[r], shift);
     const uint32_t tag = ok ? d : (0x100u | (uint32_t)lane);
     const uint32_t peers = __match_any_sync(0xffffffffu, tag);
     const uint32_t before = ok ? whist[w * 256 + d] : 0u;
@@ -203,7 +211,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
     if (j < n) {
-      const uint32_t d = (k[r] >> shift) & 0xFFu;
+      const uint32_t d = digit_of<HASHED>(k[r], shift);
       const uint32_t lp = tstart[d] + whist[w * 256 + d] + lr[r];
       stage_k[lp] = k[r];
       stage_v[lp] = v[r];
@@ -213,7 +221,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
   const int cnt = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
   for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
     const uint32_t key = stage_k[i];
-    const uint32_t d = (key >> shift) & 0xFFu;
+    const uint32_t d = digit_of<HASHED>(key, shift);
     const int64_t pos = (int64_t)gbase[d] + (i - (int64_t)tstart[d]);
     okeys[pos] = key;
     ovals[pos] = stage_v[i];
@@ -252,11 +260,11 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
   for (int shift = 0; shift < bits; shift += 8, ++pass) {
     uint32_t* ko = (pass & 1) ? kb : ka;
     P* vo = (pass & 1) ? vb : va;
-    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ntiles, counts);
+    radix_hist<false><<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ntiles, counts);
     agg_status st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
     if (st != AGG_OK) return st;
-    radix_scatter<P><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ntiles,
-                                                                 counts);
+    radix_scatter<P, false><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ntiles,
+                                                                        counts);
     note_launch(2);
     AGG_CUDA_TRY(cudaGetLastError());
     ki = ko;
@@ -272,13 +280,42 @@ agg_status radix_prepare() {
   cudaGetDevice(&dev);
   static bool done[64] = {};
   if (dev < 64 && done[dev]) return AGG_OK;
-  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)scatter_smem<uint32_t>()));
-  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem<uint64_t>()));
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)scatter_smem<uint32_t>()));
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)scatter_smem<uint64_t>()));
   if (dev < 64) done[dev] = true;
   return AGG_OK;
 }
+
+template <class P>
+agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
+                                  cudaStream_t s) {
+  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+  if (ntiles == 0) return AGG_OK;
+  agg_status st = radix_prepare();
+  if (st != AGG_OK) return st;
+  uint32_t* counts = (uint32_t*)tmp;
+  const size_t cbytes = ((size_t)256 * ntiles * sizeof(uint32_t) + 255) & ~size_t(255);
+  void* stmp = (char*)tmp + cbytes;
+  radix_hist<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, nullptr, 24, ntiles, counts);
+  st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
+  if (st != AGG_OK) return st;
+  radix_scatter<P, true><<<(unsigned)ntiles, kSortThreads, scatter_smem<P>(), s>>>(kin, vin, kout, vout, n, nullptr,
+                                                                                    24, ntiles, counts);
+  note_launch(2);
+  AGG_CUDA_TRY(cudaGetLastError());
+  return AGG_OK;
+}
+
+template agg_status radix_partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t,
+                                                     void*, cudaStream_t);
+template agg_status radix_partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t,
+                                                     void*, cudaStream_t);
 
 template agg_status radix_sort_pairs<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                                uint32_t*, int64_t, const int64_t*, int, void*, cudaStream_t,

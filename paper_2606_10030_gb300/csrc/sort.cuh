@@ -29,6 +29,13 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
                             int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
                             uint32_t** kout, P** vout);
 
+// One stable radix pass on the top 8 bits of fmix32(key): rows come out
+// grouped by hash partition (each partition's keys in their input order).
+// tmp must hold radix_tmp_bytes(n).
+template <class P>
+agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
+                                  cudaStream_t s);
+
 // Set the kernel attributes the sort needs (call before a stream capture).
 agg_status radix_prepare();
 

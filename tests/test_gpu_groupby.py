@@ -237,3 +237,15 @@ def test_sketch_parity(case, offset):
     got = agg.agg_sketch(torch.from_numpy(keys).cuda(), agg.AGG_F64, ops, offset).cpu().numpy()
     ref = oracle_sketch(keys, 8, 2, 1, 32, offset, smem, l2)
     assert np.allclose(got, ref, rtol=1e-5, atol=1e-6), (got, ref)
+
+
+@pytest.mark.parametrize("strategy", [agg.AGG_STRAT_SMEM, agg.AGG_STRAT_GLOBAL])
+@pytest.mark.parametrize("dt", DTS)
+@pytest.mark.parametrize("case", ["uniform50k", "zipf", "sentinel", "distinct"])
+def test_hash_partitioned_build_parity(strategy, dt, case):
+    """Rows hash-partitioned before the build (forced on for these small inputs)."""
+    keys, vals = make_case(case, dt, seed=21)
+    res, meta = run(keys, vals, strategy, partition=1)
+    check_groups(res, keys, vals)
+    res2, _ = run(keys, vals, strategy, partition=-1)
+    assert np.array_equal(res["keys"], res2["keys"]) and np.array_equal(res["count"], res2["count"])
