@@ -506,7 +506,9 @@ def run_reference(args):
     if rank != 0:
         return
     W = WORKLOADS[args.workload]()
-    per_step = max(1.0, args.cpu_budget / max(1, args.steps + args.warmup))
+    if args.rows:
+        W.n = args.rows
+    per_step = max(0.1, args.cpu_budget / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
         W.cpu_sample(per_step)
     rows_t, t_t = 0, 0.0

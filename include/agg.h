@@ -65,7 +65,7 @@ typedef enum {
   AGG_ERR_OOM = -2,        /* device or pinned allocation failed */
   AGG_ERR_CUDA = -3,       /* a CUDA call failed (message in agg_last_error) */
   AGG_ERR_TABLE_FULL = -4, /* a hash table ran out of slots (retried internally) */
-  AGG_ERR_TIMEOUT = -5     /* a bounded device-side wait gave up */
+  AGG_ERR_TIMEOUT = -5     /* reserved: no kernel of this library waits on another block or device */
 } agg_status;
 
 /*
@@ -396,6 +396,9 @@ enum {
   AGG_PHASES = 8
 };
 int64_t agg_launch_count(void);
+/* Test hook: the countdown-th device allocation the library makes from now on
+   fails as if the device were out of memory (1 = the next one; 0 disables). */
+void agg_debug_fail_alloc(int64_t countdown);
 void agg_profile_enable(int on);
 agg_status agg_profile_read(double* ms, int64_t* calls);
 

@@ -170,6 +170,7 @@ SIGNATURES = {
     "agg_batch_plan_free": (None, [_vp]),
     "agg_batch": (_i32, [_vp, _i32, _vp, _vp]),
     "agg_launch_count": (ctypes.c_int64, []),
+    "agg_debug_fail_alloc": (None, [_i64]),
     "agg_profile_enable": (None, [_i32]),
     "agg_profile_read": (_i32, [_vp, _vp]),
     "agg_last_error": (ctypes.c_char_p, []),

@@ -353,7 +353,7 @@ static agg_status plan_alloc(agg_batch_plan* P, cudaStream_t s) {
   P->outs = new SharedBlock();
   P->outs->refs = 1;
   cudaGetDevice(&P->outs->device);
-  AGG_CUDA_TRY(cudaMalloc(&P->outs->p, std::max<size_t>(out_bytes, 256)));
+  AGG_CUDA_TRY(dev_malloc(&P->outs->p, std::max<size_t>(out_bytes, 256)));
   // tables and the small / large split
   size_t tb = 0;
   std::vector<int> small_ids, large_ids, is_large(nq, 0);
@@ -402,7 +402,7 @@ static agg_status plan_alloc(agg_batch_plan* P, cudaStream_t s) {
   off += 2 * align256((size_t)L * 4) + 2 * align256((size_t)L * 8);
   const size_t rt_off = off;
   off += align256(radix_tmp_bytes(L));
-  AGG_CUDA_TRY(cudaMalloc(&P->work, off));
+  AGG_CUDA_TRY(dev_malloc(&P->work, off));
   char* w = (char*)P->work;
   P->zero_bytes = zero_end;
   P->status = (int*)(w + status_off);
@@ -627,7 +627,7 @@ extern "C" agg_status agg_batch_plan_create(const agg_query* queries, int nq, ag
     }
     void* tmp = nullptr;
     const size_t jb = align256(sizeof(SketchJob) * nq), fb = align256(sizeof(float) * F_COUNT * nq);
-    if (cudaMalloc(&tmp, jb + fb + align256(sizeof(float) * 3 * nq)) != cudaSuccess) {
+    if (dev_malloc(&tmp, jb + fb + align256(sizeof(float) * 3 * nq)) != cudaSuccess) {
       delete P;
       set_error("batch plan: allocation failed");
       return AGG_ERR_OOM;

@@ -56,6 +56,10 @@ const DeviceInfo& device_info();  // of the current device
 void* stream_scratch(cudaStream_t s, size_t bytes, agg_status* st);
 void* stream_pinned(cudaStream_t s, size_t bytes, agg_status* st);
 
+// Device allocation (stream-ordered / plain); both honour agg_debug_fail_alloc.
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s);
+cudaError_t dev_malloc(void** p, size_t bytes);
+
 // Kernel-launch counter and optional per-phase event timing.
 void note_launch(int k = 1);
 struct PhaseTimer {

@@ -126,7 +126,7 @@ agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_
   const size_t kbytes = ((size_t)cap * 4 + 255) & ~size_t(255);
   const size_t bytes = kbytes + 5 * ((a8 + 255) & ~size_t(255)) + 256;
   void* blk = nullptr;
-  cudaError_t e = cudaMallocAsync(&blk, bytes, s);
+  cudaError_t e = dev_malloc_async(&blk, bytes, s);
   if (e != cudaSuccess) {
     set_error("result allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
     return AGG_ERR_OOM;
@@ -180,7 +180,7 @@ class HashRun {
     status_off_ = (tbytes + 255) & ~size_t(255);
     aux_off_ = status_off_ + 256;
     size_t aux_bytes = small_ ? 2 * (size_t)nslots_ * 4 + 1024 : 4 * (size_t)nslots_ * 4 + 1024 + radix_tmp_bytes(nslots_);
-    AGG_CUDA_TRY(cudaMallocAsync(&mem_, aux_off_ + aux_bytes, s_));
+    AGG_CUDA_TRY(dev_malloc_async(&mem_, aux_off_ + aux_bytes, s_));
     AGG_CUDA_TRY(cudaMemsetAsync(mem_, 0, aux_off_, s_));
     status_ = (int*)((char*)mem_ + status_off_);
     counter_ = (unsigned long long*)((char*)mem_ + status_off_ + 64);
@@ -238,7 +238,7 @@ class HashRun {
     const size_t es = dtype_size(vdt_);
     const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255), vb = ((size_t)n * es + 255) & ~size_t(255);
     void* tmp = nullptr;
-    AGG_CUDA_TRY(cudaMallocAsync(&tmp, kb + vb + radix_tmp_bytes(n), s_));
+    AGG_CUDA_TRY(dev_malloc_async(&tmp, kb + vb + radix_tmp_bytes(n), s_));
     uint32_t* kp = (uint32_t*)tmp;
     char* vp = (char*)tmp + kb;
     void* rt = (char*)tmp + kb + vb;
@@ -631,7 +631,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
   const size_t kbytes = (size_t)chunk * 4, vbytes = (size_t)chunk * es;
   const size_t slot_bytes = ((kbytes + 255) & ~size_t(255)) + ((vbytes + 255) & ~size_t(255));
   void* ring = nullptr;
-  AGG_CUDA_TRY(cudaMallocAsync(&ring, (size_t)GbPipe::kRing * slot_bytes, s));
+  AGG_CUDA_TRY(dev_malloc_async(&ring, (size_t)GbPipe::kRing * slot_bytes, s));
   struct Free {
     void* p;
     cudaStream_t s;
@@ -685,7 +685,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     // the sort needs the whole column on the device
     void* full = nullptr;
     const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255);
-    AGG_CUDA_TRY(cudaMallocAsync(&full, kb + (size_t)n * es + 256, s));
+    AGG_CUDA_TRY(dev_malloc_async(&full, kb + (size_t)n * es + 256, s));
     Free full_free{full, s};
     AGG_CUDA_TRY(cudaMemcpyAsync(full, keys, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     AGG_CUDA_TRY(cudaMemcpyAsync((char*)full + kb, vals, (size_t)n * es, cudaMemcpyHostToDevice, s));

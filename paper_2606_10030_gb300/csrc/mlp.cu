@@ -364,11 +364,17 @@ extern "C" agg_status agg_mlp_train(float* params_dev, float* m_dev, float* v_de
   const int nb = (n + batch - 1) / batch;
   float *grads = nullptr, *xb = nullptr, *losses = nullptr;
   int32_t *yb = nullptr, *idx = nullptr;
-  AGG_CUDA_TRY(cudaMallocAsync(&grads, sizeof(float) * kParamsPad, s));
-  AGG_CUDA_TRY(cudaMallocAsync(&xb, sizeof(float) * kMlpBatch * kIn, s));
-  AGG_CUDA_TRY(cudaMallocAsync(&yb, sizeof(int32_t) * kMlpBatch, s));
-  AGG_CUDA_TRY(cudaMallocAsync(&idx, sizeof(int32_t) * (size_t)n, s));
-  AGG_CUDA_TRY(cudaMallocAsync(&losses, sizeof(float) * (size_t)nb, s));
+  {
+    void* blk = nullptr;
+    const size_t b0 = 256 * ((sizeof(float) * kParamsPad + 255) / 256), b1 = 256 * ((sizeof(float) * kMlpBatch * kIn + 255) / 256),
+                 b2 = 256 * ((sizeof(int32_t) * kMlpBatch + 255) / 256), b3 = 256 * ((sizeof(int32_t) * (size_t)n + 255) / 256);
+    AGG_CUDA_TRY(dev_malloc_async(&blk, b0 + b1 + b2 + b3 + sizeof(float) * (size_t)nb, s));
+    grads = (float*)blk;
+    xb = (float*)((char*)blk + b0);
+    yb = (int32_t*)((char*)blk + b0 + b1);
+    idx = (int32_t*)((char*)blk + b0 + b1 + b2);
+    losses = (float*)((char*)blk + b0 + b1 + b2 + b3);
+  }
   uint64_t st64 = seed;
   auto next = [&]() {  // SplitMix64
     uint64_t z = (st64 += 0x9E3779B97F4A7C15ull);
@@ -411,11 +417,7 @@ extern "C" agg_status agg_mlp_train(float* params_dev, float* m_dev, float* v_de
       epoch_loss_host[ep] = (float)(sum / n);
     }
   }
-  cudaFreeAsync(grads, s);
-  cudaFreeAsync(xb, s);
-  cudaFreeAsync(yb, s);
-  cudaFreeAsync(idx, s);
-  cudaFreeAsync(losses, s);
+  cudaFreeAsync(grads, s);  // the one block holding all of the scratch
   if (st == AGG_OK) AGG_CUDA_TRY(cudaStreamSynchronize(s));
   return st;
 }
@@ -427,7 +429,7 @@ extern "C" agg_status agg_selector_set(const float* params_host, const float* me
   std::lock_guard<std::mutex> lk(g_sel_mu);
   Selector* S = selector_for_device();
   AGG_CHECK_ARG(S != nullptr, "device index out of range");
-  if (!S->dev) AGG_CUDA_TRY(cudaMalloc(&S->dev, sizeof(float) * (kParamsPad + 2 * kIn)));
+  if (!S->dev) AGG_CUDA_TRY(dev_malloc((void**)&S->dev, sizeof(float) * (kParamsPad + 2 * kIn)));
   S->host.assign(kParamsPad + 2 * kIn, 0.f);
   std::memcpy(S->host.data(), params_host, sizeof(float) * kParams);
   std::memcpy(S->host.data() + kParamsPad, mean_host, sizeof(float) * kIn);

@@ -64,7 +64,7 @@ void* stream_scratch(cudaStream_t s, size_t bytes, agg_status* st) {
   }
   size_t want = bytes < (1u << 20) ? (1u << 20) : bytes;
   void* p = nullptr;
-  cudaError_t e = cudaMallocAsync(&p, want, s);
+  cudaError_t e = dev_malloc_async(&p, want, s);
   if (e != cudaSuccess) {
     set_error("scratch allocation of %zu bytes failed: %s", want, cudaGetErrorString(e));
     *st = e == cudaErrorMemoryAllocation ? AGG_ERR_OOM : AGG_ERR_CUDA;
@@ -82,6 +82,37 @@ void* stream_scratch(cudaStream_t s, size_t bytes, agg_status* st) {
   sc.bytes = want;
   *st = AGG_OK;
   return p;
+}
+
+// ---------------------------------------------------------------------------
+// Device allocations go through these two helpers so that a test can make the
+// n-th one fail (agg_debug_fail_alloc) and check the error path.
+// ---------------------------------------------------------------------------
+namespace {
+std::atomic<int64_t> g_fail_countdown{0};
+bool injected_failure() {
+  int64_t c = g_fail_countdown.load();
+  while (c > 0) {
+    if (g_fail_countdown.compare_exchange_weak(c, c - 1)) return c == 1;
+  }
+  return false;
+}
+}  // namespace
+
+cudaError_t dev_malloc_async(void** p, size_t bytes, cudaStream_t s) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMallocAsync(p, bytes, s);
+}
+
+cudaError_t dev_malloc(void** p, size_t bytes) {
+  if (injected_failure()) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, bytes);
 }
 
 // A small pinned host buffer per (device, stream) for reading a few result
@@ -163,6 +194,8 @@ PhaseTimer::~PhaseTimer() {
 }
 
 }  // namespace agg
+
+extern "C" void agg_debug_fail_alloc(int64_t countdown) { agg::g_fail_countdown.store(countdown > 0 ? countdown : 0); }
 
 extern "C" int64_t agg_launch_count(void) { return agg::g_launches.load(); }
 

@@ -299,7 +299,7 @@ static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t
   const size_t tc = ((size_t)(ntiles + 1) * 4 + 255) & ~size_t(255);
   const size_t st_b = (scan_tmp_bytes(ntiles) + 255) & ~size_t(255);
   void* tmp = nullptr;
-  AGG_CUDA_TRY(cudaMallocAsync(&tmp, 2 * kb + 2 * vb + rt + tc + st_b + 256, s));
+  AGG_CUDA_TRY(dev_malloc_async(&tmp, 2 * kb + 2 * vb + rt + tc + st_b + 256, s));
   char* c = (char*)tmp;
   uint32_t* kA = (uint32_t*)c; c += kb;
   uint32_t* kB = (uint32_t*)c; c += kb;

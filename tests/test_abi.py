@@ -58,3 +58,64 @@ def test_reduce_rejects_bad_arguments_without_launching(L):
 
 def test_scalar_struct_layout():
     assert agg.SCALAR_BYTES == 80
+
+
+def test_groupby_batch_and_network_reject_bad_arguments_without_launching(L):
+    out = ctypes.c_void_p()
+    k = ctypes.c_void_p(0x1000)
+    v = ctypes.c_void_p(0x2000)
+    assert L.agg_groupby(k, v, 10, 7, agg.AGG_SUM, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
+    assert L.agg_groupby(k, v, 10, agg.AGG_I32, 0, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
+    assert L.agg_groupby(k, v, 1 << 32, agg.AGG_I32, agg.AGG_SUM, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
+    assert "2^32" in agg.last_error()
+    assert L.agg_groupby(None, v, 10, agg.AGG_I32, agg.AGG_SUM, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
+    assert L.agg_groupby(k, v, 10, agg.AGG_I32, agg.AGG_SUM, None, None, None) == agg.AGG_ERR_INVALID
+    assert L.agg_groupby(ctypes.c_void_p(0x1002), v, 10, agg.AGG_I32, agg.AGG_SUM, None, ctypes.byref(out),
+                         None) == agg.AGG_ERR_INVALID
+    assert L.agg_groupby(k, ctypes.c_void_p(0x2004), 10, agg.AGG_I64, agg.AGG_SUM, None, ctypes.byref(out),
+                         None) == agg.AGG_ERR_INVALID
+    for bad in [dict(strategy=9), dict(table_slots=1000), dict(smem_slots=100), dict(smem_slots=16384),
+                dict(block_threads=100), dict(blocks_per_sm=-1)]:
+        o = agg.options(**bad) if "strategy" not in bad else agg.options(bad["strategy"])
+        assert L.agg_groupby(k, v, 10, agg.AGG_I32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
+                             None) == agg.AGG_ERR_INVALID, bad
+    assert L.agg_groupby_host(k, v, 10, 9, agg.AGG_SUM, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
+    assert L.agg_sketch(k, 10, 9, agg.AGG_SUM, 0, v, None) == agg.AGG_ERR_INVALID
+    assert L.agg_sketch(k, 10, agg.AGG_I32, agg.AGG_SUM, 0, None, None) == agg.AGG_ERR_INVALID
+    r = agg.AggTuneResult()
+    assert L.agg_autotune(k, v, 0, agg.AGG_I32, agg.AGG_SUM, 1, ctypes.byref(r), None) == agg.AGG_ERR_INVALID
+    assert L.agg_groups_to_host(None, None, None, None, None, None, None) == agg.AGG_ERR_INVALID
+    # batches
+    q = (agg.AggQuery * 2)()
+    q[0].keys, q[0].vals, q[0].n, q[0].dtype, q[0].ops = 0x1000, 0x2000, 10, agg.AGG_I32, agg.AGG_SUM
+    q[1].keys, q[1].vals, q[1].n, q[1].dtype, q[1].ops = 0x1000, 0x2000, 10, 11, agg.AGG_SUM
+    plan = ctypes.c_void_p()
+    assert L.agg_batch_plan_create(q, 2, ctypes.byref(plan), None) == agg.AGG_ERR_INVALID
+    assert "query 1" in agg.last_error()
+    assert L.agg_batch_plan_create(q, 70000, ctypes.byref(plan), None) == agg.AGG_ERR_INVALID
+    assert L.agg_batch_run(None, None) == agg.AGG_ERR_INVALID
+    # network
+    f = ctypes.c_void_p(0x3000)
+    assert L.agg_mlp_grad(f, None, None, f, f, 0, f, f, None) == agg.AGG_ERR_INVALID
+    assert L.agg_mlp_grad(f, None, None, f, f, 257, f, f, None) == agg.AGG_ERR_INVALID
+    assert L.agg_mlp_grad(f, f, None, f, f, 10, f, f, None) == agg.AGG_ERR_INVALID
+    assert L.agg_mlp_adam(f, f, f, f, 0, 1e-3, 0.9, 0.999, 1e-8, None) == agg.AGG_ERR_INVALID
+    import numpy as np
+    p = np.zeros(5443, np.float32)
+    z = np.zeros(16, np.float32)
+    assert L.agg_selector_set(p.ctypes.data_as(ctypes.c_void_p), z.ctypes.data_as(ctypes.c_void_p),
+                              z.ctypes.data_as(ctypes.c_void_p)) == agg.AGG_ERR_INVALID
+    assert "std" in agg.last_error()
+
+
+def test_rule_strategy_is_a_host_call(L):
+    import numpy as np
+    f = np.zeros(16, np.float32)
+    f[0] = 20
+    f[4] = 1024 / 4096
+    f[5] = 0.0
+    f[6] = 0.1
+    f[12] = 10
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
+    f[4], f[5], f[6], f[8], f[12] = 1.0, 1.0, 0.0, 8 / 4096, 24
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_GLOBAL
