@@ -486,8 +486,13 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   c->plan.smem_slots = sslots ? sslots : smem_slots_for(est, ops_minmax(ops));
   c->plan.threads = o.block_threads ? o.block_threads : (strategy == AGG_STRAT_SMEM ? 512 : 256);
   c->plan.blocks_per_sm = o.blocks_per_sm;
+  // Partition the rows by hash first when the shared tables would spill (more
+  // distinct keys than a shared table admits) or the global table exceeds
+  // half of L2; each partition then has about 1/256 of the keys.
   const double table_bytes = (double)(c->plan.slots + 2) * gslot_bytes(ops_minmax(ops));
-  c->plan.partition = o.partition > 0 || (o.partition == 0 && table_bytes > 0.5 * device_info().l2_bytes);
+  const bool spills = strategy == AGG_STRAT_SMEM && est > 0.75 * c->plan.smem_slots;
+  const bool big_table = table_bytes > 0.5 * device_info().l2_bytes;
+  c->plan.partition = o.partition > 0 || (o.partition == 0 && n >= (int64_t(1) << 20) && (spills || big_table));
   return AGG_OK;
 }
 
@@ -662,10 +667,21 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
 
   cudaEventRecord(start_ev, s);
   cudaStreamWaitEvent(pipe->copy, start_ev, 0);  // the ring is ours once prior work on s is done
+  // The copy engine runs up to kRing chunks ahead of the builds; the first
+  // kRing copies are queued before the sketch's host synchronisation.
+  int64_t next_copy = 0;
+  bool fresh_ring = true;
+  auto ensure_copied = [&](int64_t upto) -> agg_status {
+    for (; next_copy <= upto && next_copy < nchunks; ++next_copy) {
+      agg_status e = copy_chunk(next_copy, fresh_ring);
+      if (e != AGG_OK) return e;
+    }
+    return AGG_OK;
+  };
   float feat[F_COUNT] = {0};
   bool have = false;
   if (n > 0) {
-    st = copy_chunk(0, true);
+    st = ensure_copied(GbPipe::kRing - 1);
     if (st != AGG_OK) return st;
     if (needs_sketch(o)) {
       cudaStreamWaitEvent(s, pipe->ready[0], 0);
@@ -678,6 +694,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
   }
   Choice c;
   // the autotuner times candidates on a device column: give it the first chunk
+  cudaStreamWaitEvent(s, pipe->ready[0], 0);
   st = choose(kbuf(0), vbuf(0), std::min<int64_t>(chunk, n), vdt, ops, o, feat, have, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
@@ -689,24 +706,21 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     Free full_free{full, s};
     AGG_CUDA_TRY(cudaMemcpyAsync(full, keys, (size_t)n * 4, cudaMemcpyHostToDevice, s));
     AGG_CUDA_TRY(cudaMemcpyAsync((char*)full + kb, vals, (size_t)n * es, cudaMemcpyHostToDevice, s));
-    cudaEventRecord(pipe->freed[0], s);
+    // the prefetched chunks are no longer needed; let s own the ring again
+    for (int b = 0; b < GbPipe::kRing; ++b) cudaStreamWaitEvent(s, pipe->ready[b], 0);
     st = sort_groupby((const uint32_t*)full, (char*)full + kb, n, vdt, ops, s, &g);
     if (st != AGG_OK) return st;
   } else {
     HashPlan plan = c.plan;
     int retries = 0;
-    bool chunk0_copied = n > 0;
     for (;;) {
       {
         HashRun run(vdt, ops, plan, s);
         st = run.init();
-        // The copy of chunk k + 1 is enqueued before the build of chunk k, so
-        // the copy engine works one chunk ahead of the build.
         for (int64_t k = 0; st == AGG_OK && k < nchunks; ++k) {
-          const int b = (int)(k % GbPipe::kRing);
-          if (k == 0 && !chunk0_copied) st = copy_chunk(0, retries == 0);
-          if (st == AGG_OK && k + 1 < nchunks) st = copy_chunk(k + 1, retries == 0);
+          st = ensure_copied(k + GbPipe::kRing - 1);
           if (st != AGG_OK) break;
+          const int b = (int)(k % GbPipe::kRing);
           cudaStreamWaitEvent(s, pipe->ready[b], 0);
           const int64_t rows = std::min<int64_t>(chunk, n - k * chunk);
           st = run.build(kbuf(b), vbuf(b), rows);
@@ -722,7 +736,8 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
         return st;
       ++retries;
       plan.slots = std::min<int64_t>(plan.slots * 4, int64_t(1) << 31);
-      chunk0_copied = false;
+      next_copy = 0;  // copy the column again
+      fresh_ring = false;
     }
   }
   std::memcpy(g->features, feat, sizeof(feat));

@@ -403,9 +403,12 @@ __device__ __forceinline__ void unpack4(const uint4& lo, const uint4& hi, T* v) 
 }
 
 // Rows [0, a.n) of a column folded by threads tid, tid + nthreads, ...
-// VEC: 16-byte vector loads of 4 keys and 4 values per quad, two quads
-// (8 rows) per thread per iteration, folded in batches of kBatch.
-constexpr int kBatch = 1;
+// VEC: 16-byte vector loads of 4 keys and 4 values per quad, kQuadsPerIter
+// quads per thread per iteration (all loads issued before any row is folded).
+#ifndef AGG_QUADS_PER_ITER
+#define AGG_QUADS_PER_ITER 1
+#endif
+constexpr int kQuadsPerIter = AGG_QUADS_PER_ITER;
 
 template <int DT, bool MM, bool SMEM, bool VEC>
 __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
@@ -433,34 +436,29 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
     const uint4* vq = (const uint4*)(vals + a.head);
     constexpr int VPQ = sizeof(T) == 4 ? 1 : 2;  // 16-byte value vectors per quad
     int it = 0;
-    for (int64_t q = tid; q < nq; q += 2 * nthreads) {
-      const int64_t q2 = q + nthreads;
-      const bool has2 = q2 < nq;
-      const uint4 k0 = ld_stream_v4(kq + q);
-      const uint4 v0a = ld_stream_v4(vq + q * VPQ);
-      const uint4 v0b = VPQ == 2 ? ld_stream_v4(vq + q * VPQ + 1) : v0a;
-      uint4 k1 = make_uint4(0, 0, 0, 0), v1a = k1, v1b = k1;
-      if (has2) {
-        k1 = ld_stream_v4(kq + q2);
-        v1a = ld_stream_v4(vq + q2 * VPQ);
-        v1b = VPQ == 2 ? ld_stream_v4(vq + q2 * VPQ + 1) : v1a;
+    for (int64_t q = tid; q < nq; q += kQuadsPerIter * nthreads) {
+      uint4 kk[kQuadsPerIter], va[kQuadsPerIter], vb[kQuadsPerIter];
+      bool has[kQuadsPerIter];
+#pragma unroll
+      for (int u = 0; u < kQuadsPerIter; ++u) {  // issue every load of the iteration first
+        const int64_t qu = q + u * nthreads;
+        has[u] = qu < nq;
+        kk[u] = has[u] ? ld_stream_v4(kq + qu) : make_uint4(0, 0, 0, 0);
+        va[u] = has[u] ? ld_stream_v4(vq + qu * VPQ) : make_uint4(0, 0, 0, 0);
+        vb[u] = (has[u] && VPQ == 2) ? ld_stream_v4(vq + qu * VPQ + 1) : va[u];
       }
-      uint32_t key[8] = {k0.x, k0.y, k0.z, k0.w, k1.x, k1.y, k1.z, k1.w};
-      T val[8];
-      unpack4<T>(v0a, v0b, val);
-      unpack4<T>(v1a, v1b, val + 4);
 #pragma unroll
-      for (int r0 = 0; r0 < 8; r0 += kBatch) {
-        uint32_t kb[kBatch];
-        T vb[kBatch];
-        bool ok[kBatch];
+      for (int u = 0; u < kQuadsPerIter; ++u) {
+        const uint32_t key[4] = {kk[u].x, kk[u].y, kk[u].z, kk[u].w};
+        T val[4];
+        unpack4<T>(va[u], vb[u], val);
 #pragma unroll
-        for (int r = 0; r < kBatch; ++r) {
-          kb[r] = key[r0 + r];
-          vb[r] = val[r0 + r];
-          ok[r] = r0 + r < 4 || has2;
+        for (int r = 0; r < 4; ++r) {
+          uint32_t kb[1] = {key[r]};
+          T vv[1] = {val[r]};
+          bool ok[1] = {has[u]};
+          fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok);
         }
-        fold_batch<DT, MM, SMEM, kBatch>(a, st, kb, vb, ok);
       }
       if ((++it & 15) == 0 && *(volatile int*)a.status) break;  // table full: the build is redone
     }

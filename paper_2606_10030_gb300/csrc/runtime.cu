@@ -47,6 +47,14 @@ const DeviceInfo& device_info() {
   cudaDeviceGetAttribute(&d.l2_bytes, cudaDevAttrL2CacheSize, dev);
   cudaDeviceGetAttribute(&d.max_threads_per_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
   if (d.sm_count <= 0) d.sm_count = 1;
+  // Keep freed stream-ordered allocations in this process's default pool
+  // instead of unmapping them at every synchronisation: the GROUP BY paths
+  // free and re-allocate large scratch on every call.
+  cudaMemPool_t pool;
+  if (cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  }
   return g_devices.emplace(dev, d).first->second;
 }
 

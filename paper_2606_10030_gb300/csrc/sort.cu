@@ -21,8 +21,10 @@ constexpr int kScanThreads = 256;
 constexpr int kScanItems = 16;
 constexpr int kScanTile = kScanThreads * kScanItems;
 
+// Block-wide exclusive scan for blocks of up to 1024 threads (a multiple of 32).
 __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* total) {
-  __shared__ uint32_t warp_sums[kScanThreads / 32];
+  __shared__ uint32_t warp_sums[32];
+  const int nw = blockDim.x >> 5;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   uint32_t x = v;
 #pragma unroll
@@ -33,17 +35,17 @@ __device__ __forceinline__ uint32_t block_exclusive_scan(uint32_t v, uint32_t* t
   if (lane == 31) warp_sums[w] = x;
   __syncthreads();
   if (w == 0) {
-    uint32_t s = lane < kScanThreads / 32 ? warp_sums[lane] : 0;
+    uint32_t s = lane < nw ? warp_sums[lane] : 0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
       if (lane >= o) s += y;
     }
-    if (lane < kScanThreads / 32) warp_sums[lane] = s;
+    if (lane < nw) warp_sums[lane] = s;
   }
   __syncthreads();
   uint32_t base = w ? warp_sums[w - 1] : 0;
-  if (total) *total = warp_sums[kScanThreads / 32 - 1];
+  if (total) *total = warp_sums[nw - 1];
   uint32_t r = base + x - v;
   __syncthreads();
   return r;
@@ -139,7 +141,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
                                                            const int64_t* n_dev, int shift, int64_t ntiles,
                                                            uint32_t* __restrict__ counts) {
   __shared__ uint32_t h[256];
-  h[threadIdx.x] = 0;
+  if (threadIdx.x < 256) h[threadIdx.x] = 0;
   __syncthreads();
   const int64_t n = rows_of(n_cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -149,32 +151,39 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
     if (j < n) atomicAdd(&h[digit_of<HASHED>(keys[j], shift)], 1u);
   }
   __syncthreads();
-  counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
+  if (threadIdx.x < 256) counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
+// Per tile (512 threads x 8 rows, each warp owning 256 consecutive rows):
+// 1. each warp ranks its rows among equal digits, round by round, with a
+//    warp match and a per-warp running digit count (only the ranks are kept
+//    in registers);
+// 2. digit totals are scanned across warps and digits;
+// 3. rows are re-loaded (they are in L2) and staged in shared memory in digit
+//    order;
+// 4. each digit's run is written to its global offset with coalesced stores.
 template <class P, bool HASHED>
 __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __restrict__ keys,
                                                               const P* __restrict__ vals, uint32_t* __restrict__ okeys,
                                                               P* __restrict__ ovals, int64_t n_cap,
                                                               const int64_t* n_dev, int shift, int64_t ntiles,
                                                               const uint32_t* __restrict__ offsets) {
+  constexpr int kWarps = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  P* stage_v = (P*)sm_raw;                                           // kSortTile
-  uint32_t* stage_k = (uint32_t*)(stage_v + kSortTile);              // kSortTile
-  uint32_t* whist = stage_k + kSortTile;                             // 8 x 256
-  uint32_t* tstart = whist + (kSortThreads / 32) * 256;              // 256
-  uint32_t* gbase = tstart + 256;                                    // 256
+  P* stage_v = (P*)sm_raw;                                // kSortTile
+  uint32_t* stage_k = (uint32_t*)(stage_v + kSortTile);  // kSortTile
+  uint32_t* whist = stage_k + kSortTile;                 // kWarps x 256
+  uint32_t* tstart = whist + kWarps * 256;               // 256
+  uint32_t* gbase = tstart + 256;                        // 256
 
   const int64_t n = rows_of(n_cap, n_dev);
   const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
   if (tile0 >= n) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < (kSortThreads / 32) * 256; i += kSortThreads) whist[i] = 0;
-  gbase[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) whist[i] = 0;
+  if (threadIdx.x < 256) gbase[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
   __syncthreads();
 
-  uint32_t k[kSortItems];
-  P v[kSortItems];
   uint32_t lr[kSortItems];
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
@@ -182,9 +191,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
     const bool ok = j < n;
-    k[r] = ok ? keys[j] : 0u;
-    v[r] = ok ? vals[j] : P(0);
-    const uint32_t d = digit_of<HASHED>(k[r], shift);
+    const uint32_t d = ok ? digit_of<HASHED>(keys[j], shift) : 0u;
     const uint32_t tag = ok ? d : (0x100u | (uint32_t)lane);
     const uint32_t peers = __match_any_sync(0xffffffffu, tag);
     const uint32_t before = ok ? whist[w * 256 + d] : 0u;
@@ -194,27 +201,30 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
     __syncwarp();
   }
   __syncthreads();
-  {  // per digit: prefix over warps, then exclusive scan over digits
-    const int d = threadIdx.x;
+  {  // per digit: exclusive prefix over warps, then over digits
     uint32_t run = 0;
+    if (threadIdx.x < 256) {
+      const int d = threadIdx.x;
 #pragma unroll
-    for (int ww = 0; ww < kSortThreads / 32; ++ww) {
-      uint32_t c = whist[ww * 256 + d];
-      whist[ww * 256 + d] = run;
-      run += c;
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t c = whist[ww * 256 + d];
+        whist[ww * 256 + d] = run;
+        run += c;
+      }
     }
-    uint32_t e = block_exclusive_scan(run, nullptr);
-    tstart[d] = e;
+    const uint32_t e = block_exclusive_scan(threadIdx.x < 256 ? run : 0u, nullptr);
+    if (threadIdx.x < 256) tstart[threadIdx.x] = e;
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
     if (j < n) {
-      const uint32_t d = digit_of<HASHED>(k[r], shift);
+      const uint32_t key = keys[j];
+      const uint32_t d = digit_of<HASHED>(key, shift);
       const uint32_t lp = tstart[d] + whist[w * 256 + d] + lr[r];
-      stage_k[lp] = k[r];
-      stage_v[lp] = v[r];
+      stage_k[lp] = key;
+      stage_v[lp] = vals[j];
     }
   }
   __syncthreads();

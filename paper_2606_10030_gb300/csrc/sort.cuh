@@ -6,8 +6,8 @@
 
 namespace agg {
 
-constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;
+constexpr int kSortThreads = 512;
+constexpr int kSortItems = 8;
 constexpr int kSortTile = kSortThreads * kSortItems;  // 4096 rows per tile
 
 // Exclusive scan of n uint32 values (in may equal out). If total_dev is not

@@ -217,7 +217,9 @@ __global__ void __launch_bounds__(kSegThreads) seg_reduce(const uint32_t* __rest
       last = cur; last_key = pk; last_run = run; have_last = true;
     }
   };
-  for (int i = 0; i < nv; ++i) {
+#pragma unroll
+  for (int i = 0; i < kSegItems; ++i) {
+    if (i >= nv) break;
     const bool h = (heads >> i) & 1u;
     if (h && open) {
       close_piece(true);

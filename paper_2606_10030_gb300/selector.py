@@ -153,6 +153,63 @@ def install_default() -> bool:
     return True
 
 
+def evaluate_large(log2_rows: int = 30, log2_keys=range(4, 27, 2), skews=(0.0, 0.5, 1.0, 1.5),
+                   e2e_tables: int = 4, seed: int = 7, log=print) -> dict:
+    """Regret of the installed selector against the exhaustive autotuner on large
+    uint32-key / int64-value tables, on the device; and end-to-end GB/s from pinned
+    host memory (AGG_STRAT_LEARNED through agg_groupby_host) on a few of them."""
+    import torch
+
+    import datagen as dg
+    from datagen import cuda as dgc
+
+    from . import AGG_ALL, AGG_STRAT_LEARNED, agg_groupby_host, options
+    n = 1 << log2_rows
+    ops = AGG_ALL
+    rows = []
+    k = torch.empty(n, dtype=torch.uint32, device="cuda")
+    v = torch.empty(n, dtype=torch.int64, device="cuda")
+    e2e_done = 0
+    for lk in log2_keys:
+        for sk in skews:
+            D = 1 << lk
+            q = dg.GroupQuery(n, D, sk, "i64", ops, dg.mix64_int(seed * 1000 + lk * 10 + int(sk * 2)))
+            dgc.group_column(q, out_keys=k, out_vals=v)
+            r = agg_autotune(k, v, ops, 1)
+            f = np.array(list(r.features), np.float32)
+            T = np.array(list(r.best_ms_per_strategy), np.float64)
+            probs = agg_mlp_forward(*[torch.from_numpy(a).cuda() for a in load()[:1]],
+                                    torch.from_numpy(f[None]).cuda(),
+                                    *[torch.from_numpy(a).cuda() for a in load()[1:]]).cpu().numpy()[0]
+            learned = int(probs.argmax())
+            rule = CLASS_OF_STRATEGY[agg_rule_strategy(f, ops)]
+            row = {"log2_keys": lk, "zipf_s": sk, "ms": T.round(3).tolist(), "best": int(T.argmin()),
+                   "learned": learned, "rule": rule, "learned_regret": float(T[learned] / T.min() - 1),
+                   "rule_regret": float(T[rule] / T.min() - 1),
+                   "best_GBps": float(n * 12 / (T.min() * 1e-3) / 1e9)}
+            if e2e_done < e2e_tables and lk in (4, 12, 20, 26) and sk == 1.0:
+                hk, hv = k.cpu().pin_memory(), v.cpu().pin_memory()
+                g = agg_groupby_host(hk, hv, ops, options(AGG_STRAT_LEARNED))
+                g.free()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                g = agg_groupby_host(hk, hv, ops, options(AGG_STRAT_LEARNED))
+                res = g.to_host()
+                g.free()
+                dt = time.perf_counter() - t0
+                row["e2e_GBps"] = float(n * 12 / dt / 1e9)
+                row["e2e_groups"] = int(len(res["keys"]))
+                del hk, hv
+                e2e_done += 1
+            rows.append(row)
+            log(row)
+    lr = np.array([r["learned_regret"] for r in rows])
+    rr = np.array([r["rule_regret"] for r in rows])
+    return {"tables": rows, "rows_per_table": n, "learned_mean_regret": float(lr.mean()),
+            "learned_p95_regret": float(np.percentile(lr, 95)), "rule_mean_regret": float(rr.mean()),
+            "rule_p95_regret": float(np.percentile(rr, 95))}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--samples", type=int, default=2000)
@@ -161,7 +218,17 @@ def main():
     ap.add_argument("--max-log2-rows", type=int, default=24)
     ap.add_argument("--epochs", type=int, default=80)
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
+    ap.add_argument("--evaluate-large", default="", help="write the large-table evaluation (JSON) to this path")
+    ap.add_argument("--large-log2-rows", type=int, default=30)
     args = ap.parse_args()
+    if args.evaluate_large:
+        import json
+        install_default()
+        ev = evaluate_large(args.large_log2_rows)
+        with open(args.evaluate_large, "w") as f:
+            json.dump(ev, f, indent=1)
+        print({k: v for k, v in ev.items() if k != "tables"})
+        return
     qs = sample_queries(args.samples + args.holdout, args.seed, log2_rows=(16, args.max_log2_rows))
     X, y, T, ops = label(qs, log_every=200)
     ntr = args.samples
