@@ -146,8 +146,10 @@ typedef struct agg_options {
   int64_t table_slots;     /* global table slots (power of two); 0 = from the sketch */
   uint64_t sample_offset;  /* offset of the strided key sample (pass a seeded draw) */
   int32_t items_per_thread;/* reserved for a rows-per-thread knob; must be 0 */
-  int32_t partition;       /* hash-partition the rows before a hash build: 0 = when the global table
-                              is larger than half of L2, 1 = always, -1 = never */
+  int32_t partition;       /* hash-partition the rows before a hash build: 0 = automatic (when the
+                              shared tables would spill or the global table exceeds half of L2; two
+                              levels above ~600k distinct keys), 1 = one level (256 partitions),
+                              2 = two levels (65536 partitions), -1 = never */
   int32_t reserved[2];
 } agg_options;
 

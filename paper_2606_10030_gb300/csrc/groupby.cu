@@ -155,6 +155,7 @@ agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_
 struct HashPlan {
   int strategy;     // AGG_STRAT_SMEM or AGG_STRAT_GLOBAL
   bool partition = false;  // hash-partition the rows first (table larger than L2)
+  int partition_passes = 1;  // 1: 256 partitions; 2: 65536 partitions
   int64_t slots;    // global main slots (power of two)
   int smem_slots;   // shared slots (power of two) for SMEM
   int threads;
@@ -237,16 +238,27 @@ class HashRun {
     const int64_t n = a.n;
     const size_t es = dtype_size(vdt_);
     const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255), vb = ((size_t)n * es + 255) & ~size_t(255);
+    const int passes = plan_.partition_passes;
     void* tmp = nullptr;
-    AGG_CUDA_TRY(dev_malloc_async(&tmp, kb + vb + radix_tmp_bytes(n), s_));
+    AGG_CUDA_TRY(dev_malloc_async(&tmp, passes * (kb + vb) + radix_tmp_bytes(n), s_));
     uint32_t* kp = (uint32_t*)tmp;
     char* vp = (char*)tmp + kb;
-    void* rt = (char*)tmp + kb + vb;
+    uint32_t* kq = (uint32_t*)((char*)tmp + kb + vb);
+    char* vq = (char*)tmp + 2 * kb + vb;
+    void* rt = (char*)tmp + passes * (kb + vb);
     agg_status st;
     {
       PhaseTimer pt(AGG_PHASE_SORT, s_);
-      st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_)
-                   : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_);
+      if (passes == 1) {
+        st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_, 24)
+                     : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_, 24);
+      } else {  // by bits 16..23, then stably by bits 24..31: ordered by the top 16 bits
+        st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kq, (uint32_t*)vq, n, rt, s_, 16)
+                     : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kq, (uint64_t*)vq, n, rt, s_, 16);
+        if (st == AGG_OK)
+          st = es == 4 ? radix_partition_hashed<uint32_t>(kq, (const uint32_t*)vq, kp, (uint32_t*)vp, n, rt, s_, 24)
+                       : radix_partition_hashed<uint64_t>(kq, (const uint64_t*)vq, kp, (uint64_t*)vp, n, rt, s_, 24);
+      }
     }
     if (st != AGG_OK) {
       cudaFreeAsync(tmp, s_);
@@ -268,9 +280,10 @@ class HashRun {
         int bps = occupancy(bk, threads, smem);
         if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
         int64_t grid = (int64_t)di.sm_count * bps;
-        const int64_t tiles = (n + kPartTileRows - 1) / kPartTileRows;
+        int64_t tile_rows = plan_.partition_passes == 2 ? kPartTileRows / 2 : kPartTileRows;
+        const int64_t tiles = (n + tile_rows - 1) / tile_rows;
         if (tiles < grid) grid = tiles;
-        void* args[] = {&a, &next_tile};
+        void* args[] = {&a, &next_tile, &tile_rows};
         e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, smem, s_);
       } else {
         KernelPtr bk = pick_build(vdt_, mm_, false, true);
@@ -493,6 +506,8 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   const bool spills = strategy == AGG_STRAT_SMEM && est > 0.75 * c->plan.smem_slots;
   const bool big_table = table_bytes > 0.5 * device_info().l2_bytes;
   c->plan.partition = o.partition > 0 || (o.partition == 0 && n >= (int64_t(1) << 20) && (spills || big_table));
+  // two levels (65536 partitions) when 256 partitions would still spill
+  c->plan.partition_passes = (o.partition == 2 || (o.partition == 0 && est > 256.0 * 0.75 * c->plan.smem_slots)) ? 2 : 1;
   return AGG_OK;
 }
 

@@ -385,6 +385,139 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
     if (j[r] == -1) g_row<DT, MM>(a, key[r], val[r]);
 }
 
+// ---------------------------------------------------------------------------
+// Warp-uniform runs: when all 32 lanes' four rows carry one key (hot keys of
+// a partitioned or clustered input), the warp reduces its 128 rows with
+// shuffles and applies a single partial aggregate.
+// ---------------------------------------------------------------------------
+template <int DT>
+struct Partial4 {  // partial aggregate of rows with one key
+  uint32_t cnt;
+  unsigned long long isum;  // integer sum mod 2^64
+  float fs, fc;             // float32: compensated pair
+  double ds;                // float64 sum
+  typename SImg<DT>::U mn, mx;
+};
+
+template <int DT, bool MM>
+__device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)[4]) {
+  Partial4<DT> p;
+  p.cnt = 4;
+  p.isum = 0;
+  p.fs = 0.f;
+  p.fc = 0.f;
+  p.ds = 0.0;
+  p.mn = (typename SImg<DT>::U) ~(typename SImg<DT>::U)0;
+  p.mx = 0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    if (DT == AGG_F32) {
+      float t, e;
+      two_sum(p.fs, (float)v[r], t, e);
+      p.fs = t;
+      p.fc += e;
+    } else if (DT == AGG_F64) {
+      p.ds += (double)v[r];
+    } else {
+      p.isum += (unsigned long long)(int64_t)v[r];
+    }
+    if (MM) {
+      const typename SImg<DT>::U m = s_img<DT>(v[r]);
+      p.mn = min(p.mn, m);
+      p.mx = max(p.mx, m);
+    }
+  }
+  return p;
+}
+
+template <int DT, bool MM>
+__device__ __forceinline__ void warp_reduce_partial(Partial4<DT>& p) {
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    p.cnt += __shfl_xor_sync(0xffffffffu, p.cnt, o);
+    if (DT == AGG_F32) {
+      const float s2 = __shfl_xor_sync(0xffffffffu, p.fs, o), c2 = __shfl_xor_sync(0xffffffffu, p.fc, o);
+      float t, e;
+      two_sum(p.fs, s2, t, e);
+      p.fs = t;
+      p.fc += c2 + e;
+    } else if (DT == AGG_F64) {
+      p.ds += __shfl_xor_sync(0xffffffffu, p.ds, o);
+    } else {
+      p.isum += __shfl_xor_sync(0xffffffffu, p.isum, o);
+    }
+    if (MM) {
+      p.mn = min(p.mn, __shfl_xor_sync(0xffffffffu, p.mn, o));
+      p.mx = max(p.mx, __shfl_xor_sync(0xffffffffu, p.mx, o));
+    }
+  }
+}
+
+// Apply a partial aggregate to a shared slot (same encodings as s_add via fold_batch).
+template <int DT, bool MM>
+__device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, const Partial4<DT>& p) {
+  using U = typename SImg<DT>::U;
+  atomicAdd(&st.cnt[j], p.cnt);
+  uint32_t* w = (uint32_t*)&st.sum[j];
+  if (DT == AGG_F32) {
+    const float old = atomicAdd((float*)&w[0], p.fs);
+    float t, e;
+    two_sum(old, p.fs, t, e);
+    const float c = e + p.fc;
+    if (c != 0.f) atomicAdd((float*)&w[1], c);
+  } else if (DT == AGG_F64) {
+    atomicAdd((double*)&st.sum[j], p.ds);
+  } else {
+    const uint32_t lo = (uint32_t)p.isum;
+    const uint32_t old = atomicAdd(&w[0], lo);
+    const uint32_t hi = (uint32_t)(p.isum >> 32) + ((uint32_t)(old + lo) < old ? 1u : 0u);
+    if (hi) atomicAdd(&w[1], hi);
+  }
+  if (MM) {
+    if (p.mn < *(volatile U*)&st.mm[2 * j]) atomicMin(&st.mm[2 * j], p.mn);
+    if (p.mx > *(volatile U*)&st.mm[2 * j + 1]) atomicMax(&st.mm[2 * j + 1], p.mx);
+  }
+}
+
+template <int DT, bool MM>
+__device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, const Partial4<DT>& p) {
+  GSlot<MM>* tab = (GSlot<MM>*)a.table;
+  const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
+  if (g < 0) {
+    *(volatile int*)a.status = kStatusFull;
+    return;
+  }
+  GSlot<MM>& gs = tab[g];
+  atomicAdd(&gs.cnt, p.cnt);
+  if (DT == AGG_F32) atomicAdd((double*)&gs.sum, (double)p.fs + (double)p.fc);
+  else if (DT == AGG_F64) atomicAdd((double*)&gs.sum, p.ds);
+  else atomicAdd(&gs.sum, p.isum);
+  if (MM) {
+    GSlot<true>& w = (GSlot<true>&)gs;
+    const uint64_t mn = g_img_of<DT>(p.mn), mx = g_img_of<DT>(p.mx);
+    if (~mn > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~mn);
+    if (mx > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)mx);
+  }
+}
+
+// Lane 0 folds the warp's reduced partial for key into the tables.
+template <int DT, bool MM, bool SMEM>
+__device__ __forceinline__ void fold_warp_uniform(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
+                                                  const typename GV<DT>::T (&v)[4]) {
+  Partial4<DT> p = partial_of<DT, MM>(v);
+  warp_reduce_partial<DT, MM>(p);
+  if ((threadIdx.x & 31) != 0) return;
+  if (SMEM) {
+    int j = s_find_home<DT, MM>(st, a.smem_slots, key);
+    if (j < 0) j = s_lookup<DT, MM>(st, a.smem_slots, a.smem_cap, key);
+    if (j >= 0) {
+      s_add_partial<DT, MM>(st, j, p);
+      return;
+    }
+  }
+  g_add_partial<DT, MM>(a, key, p);
+}
+
 template <class T>
 __device__ __forceinline__ void unpack4(const uint4& lo, const uint4& hi, T* v) {
   if (sizeof(T) == 4) {
@@ -452,6 +585,15 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
         const uint32_t key[4] = {kk[u].x, kk[u].y, kk[u].z, kk[u].w};
         T val[4];
         unpack4<T>(va[u], vb[u], val);
+        // a full warp whose 128 rows share one key: one reduced update
+        if (__activemask() == 0xffffffffu) {
+          const uint32_t k0 = __shfl_sync(0xffffffffu, key[0], 0);
+          const bool same = has[u] && key[0] == k0 && key[1] == k0 && key[2] == k0 && key[3] == k0;
+          if (__all_sync(0xffffffffu, same)) {
+            fold_warp_uniform<DT, MM, SMEM>(a, st, k0, val);
+            continue;
+          }
+        }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           uint32_t kb[1] = {key[r]};
@@ -532,7 +674,7 @@ __global__ void gb_build(BuildArgs a) {
 constexpr int64_t kPartTileRows = int64_t(1) << 16;
 
 template <int DT, bool MM, bool VEC>
-__global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile) {
+__global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile, int64_t tile_rows) {
   using T = typename GV<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_t;
@@ -541,13 +683,13 @@ __global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile) {
   for (;;) {
     if (threadIdx.x == 0) s_t = (int64_t)atomicAdd(next_tile, 1ull);
     __syncthreads();
-    const int64_t r0 = s_t * kPartTileRows;
+    const int64_t r0 = s_t * tile_rows;
     __syncthreads();
     if (r0 >= a.n) return;
     BuildArgs b = a;
     b.keys = a.keys + r0;
     b.vals = (const T*)a.vals + r0;
-    b.n = min(kPartTileRows, a.n - r0);
+    b.n = min(tile_rows, a.n - r0);
     b.head = 0;
     st.clear(a.smem_slots);
     __syncthreads();

@@ -304,7 +304,7 @@ agg_status radix_prepare() {
 
 template <class P>
 agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                                  cudaStream_t s) {
+                                  cudaStream_t s, int shift) {
   const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
   if (ntiles == 0) return AGG_OK;
   agg_status st = radix_prepare();
@@ -312,20 +312,20 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
   uint32_t* counts = (uint32_t*)tmp;
   const size_t cbytes = ((size_t)256 * ntiles * sizeof(uint32_t) + 255) & ~size_t(255);
   void* stmp = (char*)tmp + cbytes;
-  radix_hist<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, nullptr, 24, ntiles, counts);
+  radix_hist<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, nullptr, shift, ntiles, counts);
   st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
   if (st != AGG_OK) return st;
   radix_scatter<P, true><<<(unsigned)ntiles, kSortThreads, scatter_smem<P>(), s>>>(kin, vin, kout, vout, n, nullptr,
-                                                                                    24, ntiles, counts);
+                                                                                    shift, ntiles, counts);
   note_launch(2);
   AGG_CUDA_TRY(cudaGetLastError());
   return AGG_OK;
 }
 
 template agg_status radix_partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t,
-                                                     void*, cudaStream_t);
+                                                     void*, cudaStream_t, int);
 template agg_status radix_partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t,
-                                                     void*, cudaStream_t);
+                                                     void*, cudaStream_t, int);
 
 template agg_status radix_sort_pairs<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                                uint32_t*, int64_t, const int64_t*, int, void*, cudaStream_t,

@@ -29,12 +29,13 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
                             int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
                             uint32_t** kout, P** vout);
 
-// One stable radix pass on the top 8 bits of fmix32(key): rows come out
-// grouped by hash partition (each partition's keys in their input order).
-// tmp must hold radix_tmp_bytes(n).
+// One stable radix pass on bits [shift, shift + 8) of fmix32(key) (shift 24:
+// the top 8 bits; a pass at 16 followed by a pass at 24 orders rows by the top
+// 16 bits). Rows come out grouped by hash partition, in input order within a
+// partition. tmp must hold radix_tmp_bytes(n).
 template <class P>
 agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                                  cudaStream_t s);
+                                  cudaStream_t s, int shift);
 
 // Set the kernel attributes the sort needs (call before a stream capture).
 agg_status radix_prepare();

@@ -42,6 +42,11 @@ def make_case(case: str, dt: str, seed: int = 0):
         keys = dg.keys_zipf(200_003, 100_000, 1.0, seed)
     elif case == "distinct":
         keys = dg.domain_keys(seed, rng.permutation(70_001))
+    elif case == "runs":  # sorted keys: long runs, whole warps on one key
+        keys = np.sort(dg.keys_uniform(400_009, 300, seed))
+    elif case == "onekey":  # every row on one key, the sentinel key in a tail run
+        keys = np.full(262_147, 77, dtype=np.uint32)
+        keys[-70_000:] = 0xFFFFFFFF
     elif case == "sentinel":
         keys = dg.keys_uniform(50_001, 5, seed)
         keys[::3] = 0xFFFFFFFF
@@ -93,7 +98,7 @@ def run(keys, vals, strategy, ops=agg.AGG_ALL, **kw):
     return res, meta
 
 
-CASES = ["empty", "one", "few", "uniform1k", "uniform50k", "zipf", "distinct", "sentinel"]
+CASES = ["empty", "one", "few", "uniform1k", "uniform50k", "zipf", "distinct", "sentinel", "runs", "onekey"]
 
 
 @pytest.mark.parametrize("strategy", STRATS)
@@ -239,13 +244,14 @@ def test_sketch_parity(case, offset):
     assert np.allclose(got, ref, rtol=1e-5, atol=1e-6), (got, ref)
 
 
+@pytest.mark.parametrize("levels", [1, 2])
 @pytest.mark.parametrize("strategy", [agg.AGG_STRAT_SMEM, agg.AGG_STRAT_GLOBAL])
 @pytest.mark.parametrize("dt", DTS)
-@pytest.mark.parametrize("case", ["uniform50k", "zipf", "sentinel", "distinct"])
-def test_hash_partitioned_build_parity(strategy, dt, case):
-    """Rows hash-partitioned before the build (forced on for these small inputs)."""
+@pytest.mark.parametrize("case", ["uniform50k", "zipf", "sentinel", "distinct", "runs"])
+def test_hash_partitioned_build_parity(levels, strategy, dt, case):
+    """Rows hash-partitioned (one or two levels) before the build, forced on for these small inputs."""
     keys, vals = make_case(case, dt, seed=21)
-    res, meta = run(keys, vals, strategy, partition=1)
+    res, meta = run(keys, vals, strategy, partition=levels)
     check_groups(res, keys, vals)
     res2, _ = run(keys, vals, strategy, partition=-1)
     assert np.array_equal(res["keys"], res2["keys"]) and np.array_equal(res["count"], res2["count"])
