@@ -66,12 +66,7 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
   agg_status st = AGG_OK;
   // every candidate gets the global table size the sketch implies, so that
   // none of them pays for a second sketch of its own
-  bool covered = false;
-  const double est = distinct_estimate(feat, &covered);
-  double want = 2.0 * (covered ? 1.25 : 16.0) * est;
-  if (want > 2.0 * (double)n) want = 2.0 * (double)n;
-  int64_t tslots = next_pow2((int64_t)std::ceil(want));
-  tslots = std::max<int64_t>(1024, std::min<int64_t>(tslots, int64_t(1) << 31));
+  const int64_t tslots = table_slots_from_sketch(feat, n);
   for (int i = 0; i < nc && st == AGG_OK; ++i) {
     agg_options o{};
     o.strategy = c[i].strategy;

@@ -202,9 +202,13 @@ __global__ void batch_compact(const BQ* __restrict__ qs, const int* __restrict__
         occ = occupied<false>((const GSlot<false>*)q.table, q.mask, local);
         if (occ) key = key_of<false>((const GSlot<false>*)q.table, q.mask, local);
       }
-      if (occ) atomicAdd((unsigned long long*)qs[qi].out.d, 1ull);
     }
     const uint32_t b = __ballot_sync(0xffffffffu, occ);
+    if (occ) {  // one count update per query present in the warp
+      const uint32_t peers = __match_any_sync(b, qi);
+      if ((peers & ((1u << lane) - 1u)) == 0)
+        atomicAdd((unsigned long long*)qs[qi].out.d, (unsigned long long)__popc(peers));
+    }
     unsigned long long w0 = 0;
     if (lane == 0 && b) w0 = atomicAdd(counter, (unsigned long long)__popc(b));
     w0 = __shfl_sync(0xffffffffu, w0, 0);
@@ -267,6 +271,7 @@ __global__ void batch_first(const BQ* __restrict__ qs, int nq, const int* __rest
 // ---------------------------------------------------------------------------
 int select_learned(const float* feat, bool* ok);
 double distinct_estimate(const float* feat, bool* covered);
+int64_t table_slots_from_sketch(const float* feat, int64_t n);
 
 struct SharedBlock {
   void* p = nullptr;
@@ -576,10 +581,7 @@ static void plan_sizes(agg_batch_plan* P, const std::vector<int>& learned) {
     qp.strategy = strat == AGG_STRAT_SMEM ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
     bool covered = false;
     const double est = q.n > 0 ? distinct_estimate(f, &covered) : 1.0;
-    double want = 2.0 * (covered ? 1.25 : 16.0) * est;
-    if (want > 2.0 * (double)q.n) want = 2.0 * (double)q.n;
-    int64_t slots = next_pow2((int64_t)std::ceil(want));
-    slots = std::max<int64_t>(1024, std::min<int64_t>(slots, int64_t(1) << 31));
+    const int64_t slots = q.n > 0 ? table_slots_from_sketch(f, q.n) : 1024;
     qp.slots = slots;
     const int maxs = qp.mm ? 2048 : 4096;
     const int64_t ss = next_pow2((int64_t)std::ceil(2.0 * est));

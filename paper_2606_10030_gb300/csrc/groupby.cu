@@ -95,28 +95,74 @@ static int occupancy(KernelPtr fn, int threads, size_t smem) {
   return b;
 }
 
-// Distinct-key estimate used for the rule and for table sizing.
-//  coverage = 1 - f1/m (Good's estimate of the probability mass of keys seen
-//  in the sample). When the sample covers >= 90% of the mass the population
-//  has few unseen keys and Chao1 (d + f1^2 / (2 f2), bias-corrected; Chao,
-//  Scand. J. Stat. 1984) estimates it well; otherwise use GEE, which errs high
-//  on low-cardinality columns but is the safer bound for sizing.
-double distinct_estimate(const float* f, bool* covered) {
+// Distinct-key estimates from the sketch of m sampled keys (d distinct, f1
+// seen once, f2 seen twice).
+//  coverage = 1 - f1/m, Good's estimate of the probability mass of the keys
+//  seen in the sample;
+//  Chao1 = d + f1 (f1 - 1) / (2 (f2 + 1)), the bias-corrected lower-bound
+//  estimator (Chao, Scand. J. Stat. 1984), close for near-uniform keys;
+//  GEE = sqrt(n/m) f1 + (d - f1) (Charikar et al., PODS 2000), which errs high
+//  on flat columns and is the safer bound for skewed ones.
+// A sample is flat when its top-8 keys hold at most twice what the largest
+// counts of a uniform column of Chao1 keys would hold (Poisson, mean m/Chao1,
+// largest counts about mean + 3 sd + 3); Chao1 of a flat sample is reliable
+// once f2 >= 2 (below, the column has about m^2/4 or more keys, and Chao1 can
+// be off by several times).
+KeyEstimate key_estimate(const float* f) {
+  KeyEstimate e;
   const double m = std::min(std::exp2((double)f[F_LOG2N]), (double)kSketchSample);
   const double d = (double)f[F_DISTINCT] * m, f1 = (double)f[F_F1] * m, f2 = (double)f[F_F2] * m;
-  const double coverage = m > 0 ? 1.0 - f1 / m : 1.0;
-  const double chao1 = d + f1 * (f1 - 1.0) / (2.0 * (f2 + 1.0));
-  *covered = coverage >= 0.9;
-  return *covered ? chao1 : std::max(chao1, std::exp2((double)f[F_LOG2_GEE]));
+  e.chao1 = std::max(1.0, d + f1 * (f1 - 1.0) / (2.0 * (f2 + 1.0)));
+  e.gee = std::exp2((double)f[F_LOG2_GEE]);
+  e.covered = m <= 0 || 1.0 - f1 / m >= 0.9;
+  const double lam = m / e.chao1;
+  const double top8_flat = m > 0 ? 8.0 * (lam + 3.0 * std::sqrt(lam) + 3.0) / m : 1.0;
+  e.flat = (double)f[F_TOP8] <= 2.0 * top8_flat;
+  e.reliable = e.covered || (e.flat && f2 >= 1.5);
+  if (e.covered) e.plan = e.chao1;
+  else if (e.flat) e.plan = (e.reliable ? 1.0 : 2.0) * e.chao1;
+  else e.plan = std::max(e.chao1, 8.0 * e.gee);
+  return e;
 }
 
+double distinct_estimate(const float* f, bool* covered) {
+  const KeyEstimate e = key_estimate(f);
+  *covered = e.covered;
+  return e.plan;
+}
+
+// Global-table slots for a column of n rows from its sketch: a power of two
+// at least twice a sizing estimate, within [1024, 2^31] and at most 2n.
+//  - covered: 1.25 x Chao1;
+//  - flat: 2 x Chao1 (4 x while Chao1 is unreliable);
+//  - skewed and not covered: max(2 x Chao1, 16 x GEE), as the long tail of
+//    rare keys is barely seen in the sample.
+// A table that still overflows is regrown (4x) and the build redone.
+int64_t table_slots_from_sketch(const float* f, int64_t n) {
+  const KeyEstimate e = key_estimate(f);
+  double est;
+  if (e.covered) est = 1.25 * e.chao1;
+  else if (e.flat) est = (e.reliable ? 2.0 : 4.0) * e.chao1;
+  else est = std::max(2.0 * e.chao1, 16.0 * e.gee);
+  double want = 2.0 * est;
+  if (want > 2.0 * (double)n) want = 2.0 * (double)n;
+  int64_t p = next_pow2((int64_t)std::ceil(std::max(want, 1.0)));
+  if (p < 1024) p = 1024;
+  if (p > (int64_t(1) << 31)) p = int64_t(1) << 31;
+  return p;
+}
+
+// The AUTO rule:
+//  - few distinct keys (a shared table holds them) or strong skew: SMEM;
+//  - columns of 2^20 rows or more: SORT when the sample is flat and leaves the
+//    number of keys open (about m^2/4 or more), else SMEM on hash-partitioned
+//    rows (the partitioning is chosen with the plan);
+//  - smaller columns: one global table.
 int rule_strategy(const float* f, uint32_t ops) {
-  // distinct keys few enough for a shared-memory table, or strong skew (the
-  // hot keys stay in shared memory): SMEM; otherwise one global table.
-  bool covered = false;
-  const double est = distinct_estimate(f, &covered);
+  const KeyEstimate e = key_estimate(f);
   const int cap = ops_minmax(ops) ? 1536 : 3072;  // 3/4 of the largest shared tables
-  if (est <= cap || f[F_TOP8] >= 0.05f) return AGG_STRAT_SMEM;
+  if (e.plan <= cap || f[F_TOP8] >= 0.05f) return AGG_STRAT_SMEM;
+  if (f[F_LOG2N] >= 20.0f) return (!e.reliable && e.flat) ? AGG_STRAT_SORT : AGG_STRAT_SMEM;
   return AGG_STRAT_GLOBAL;
 }
 
@@ -410,15 +456,6 @@ class HashRun {
 agg_status sort_groupby(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops, cudaStream_t s,
                         agg_groups** gout);
 
-static int64_t table_slots_for(double est, int64_t n) {
-  double want = 2.0 * est;
-  if (want > 2.0 * (double)n) want = 2.0 * (double)n;
-  int64_t p = next_pow2((int64_t)std::ceil(want));
-  if (p < 1024) p = 1024;
-  if (p > (int64_t(1) << 31)) p = int64_t(1) << 31;
-  return p;
-}
-
 static int smem_slots_for(double est, bool mm) {
   const int maxs = mm ? 2048 : 4096;
   int64_t s = next_pow2((int64_t)std::ceil(2.0 * est));
@@ -492,10 +529,7 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   }
   c->strategy = strategy;
   c->plan.strategy = strategy;
-  // Global table: twice the estimate with a 25% margin when the sample covers
-  // the column, 16x otherwise (the sample of 4096 keys errs low on skewed,
-  // high-cardinality columns); an overflow regrows the table 4x.
-  c->plan.slots = tslots ? tslots : table_slots_for((covered ? 1.25 : 16.0) * est, n);
+  c->plan.slots = tslots ? tslots : (have_feat ? table_slots_from_sketch(feat, n) : 2048);
   c->plan.smem_slots = sslots ? sslots : smem_slots_for(est, ops_minmax(ops));
   c->plan.threads = o.block_threads ? o.block_threads : (strategy == AGG_STRAT_SMEM ? 512 : 256);
   c->plan.blocks_per_sm = o.blocks_per_sm;
@@ -507,7 +541,11 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   const bool big_table = table_bytes > 0.5 * device_info().l2_bytes;
   c->plan.partition = o.partition > 0 || (o.partition == 0 && n >= (int64_t(1) << 20) && (spills || big_table));
   // two levels (65536 partitions) when 256 partitions would still spill
-  c->plan.partition_passes = (o.partition == 2 || (o.partition == 0 && est > 256.0 * 0.75 * c->plan.smem_slots)) ? 2 : 1;
+  c->plan.partition_passes =
+      (o.partition == 2 ||
+       (o.partition == 0 && strategy == AGG_STRAT_SMEM && est > 256.0 * 0.75 * c->plan.smem_slots))
+          ? 2
+          : 1;
   return AGG_OK;
 }
 

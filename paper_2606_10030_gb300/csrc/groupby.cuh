@@ -35,8 +35,19 @@ inline bool ops_minmax(uint32_t ops) { return ops & (AGG_MIN | AGG_MAX); }
 
 // Strategy choice without a learned model: a rule on the sketch.
 int rule_strategy(const float* feat, uint32_t ops);
-// Distinct-key estimate from the sketch (*covered: the sample covers >= 90% of the mass).
+// Distinct-key estimates from a sketch.
+struct KeyEstimate {
+  double chao1, gee;
+  double plan;    // the estimate plans use (table and partition sizes)
+  bool covered;   // the sample covers >= 90% of the probability mass
+  bool flat;      // no more skew than a uniform column would show
+  bool reliable;  // plan is within a small factor of the truth
+};
+KeyEstimate key_estimate(const float* feat);
+// Planning estimate of the distinct keys (*covered as in KeyEstimate).
 double distinct_estimate(const float* feat, bool* covered);
+// Global hash-table slots for a column of n rows from its sketch (power of two).
+int64_t table_slots_from_sketch(const float* feat, int64_t n);
 
 // Output block shared by the results of one batch (reference counted).
 struct SharedBlock;

@@ -386,10 +386,13 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
 }
 
 // ---------------------------------------------------------------------------
-// Warp-uniform runs: when all 32 lanes' four rows carry one key (hot keys of
-// a partitioned or clustered input), the warp reduces its 128 rows with
-// shuffles and applies a single partial aggregate.
+// Dominant keys: when at least a quarter of the 128 rows a warp holds carry
+// the key of lane 0's first row (hot keys of a partitioned or clustered
+// input), the warp reduces those rows with shuffles and applies one partial
+// aggregate; the remaining rows take the per-row path. This removes the
+// same-slot atomic conflicts that hot keys cause.
 // ---------------------------------------------------------------------------
+constexpr int kDominantRows = 32;
 template <int DT>
 struct Partial4 {  // partial aggregate of rows with one key
   uint32_t cnt;
@@ -400,9 +403,9 @@ struct Partial4 {  // partial aggregate of rows with one key
 };
 
 template <int DT, bool MM>
-__device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)[4]) {
+__device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)[4], const bool (&take)[4]) {
   Partial4<DT> p;
-  p.cnt = 4;
+  p.cnt = 0;
   p.isum = 0;
   p.fs = 0.f;
   p.fc = 0.f;
@@ -411,6 +414,8 @@ __device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)
   p.mx = 0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
+    if (!take[r]) continue;
+    p.cnt += 1;
     if (DT == AGG_F32) {
       float t, e;
       two_sum(p.fs, (float)v[r], t, e);
@@ -500,11 +505,12 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
   }
 }
 
-// Lane 0 folds the warp's reduced partial for key into the tables.
+// The warp reduces the rows marked in take (all of one key) and lane 0 folds
+// the partial into the tables.
 template <int DT, bool MM, bool SMEM>
-__device__ __forceinline__ void fold_warp_uniform(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
-                                                  const typename GV<DT>::T (&v)[4]) {
-  Partial4<DT> p = partial_of<DT, MM>(v);
+__device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
+                                              const typename GV<DT>::T (&v)[4], const bool (&take)[4]) {
+  Partial4<DT> p = partial_of<DT, MM>(v, take);
   warp_reduce_partial<DT, MM>(p);
   if ((threadIdx.x & 31) != 0) return;
   if (SMEM) {
@@ -585,20 +591,31 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
         const uint32_t key[4] = {kk[u].x, kk[u].y, kk[u].z, kk[u].w};
         T val[4];
         unpack4<T>(va[u], vb[u], val);
-        // a full warp whose 128 rows share one key: one reduced update
+        // rows on the key of lane 0's first row, if it dominates the warp's
+        // 128 rows, go through one reduced update
+        bool taken[4] = {false, false, false, false};
         if (__activemask() == 0xffffffffu) {
           const uint32_t k0 = __shfl_sync(0xffffffffu, key[0], 0);
-          const bool same = has[u] && key[0] == k0 && key[1] == k0 && key[2] == k0 && key[3] == k0;
-          if (__all_sync(0xffffffffu, same)) {
-            fold_warp_uniform<DT, MM, SMEM>(a, st, k0, val);
-            continue;
+          unsigned nm = 0;
+#pragma unroll
+          for (int r = 0; r < 4; ++r) {
+            taken[r] = has[u] && key[r] == k0;
+            nm += taken[r] ? 1u : 0u;
+          }
+          const unsigned tot = __reduce_add_sync(0xffffffffu, nm);
+          if (tot >= (unsigned)kDominantRows) {
+            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, taken);
+            if (tot == 128u) continue;
+          } else {
+#pragma unroll
+            for (int r = 0; r < 4; ++r) taken[r] = false;
           }
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
-          bool ok[1] = {has[u]};
+          bool ok[1] = {has[u] && !taken[r]};
           fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok);
         }
       }
@@ -774,23 +791,54 @@ __global__ void __launch_bounds__(kRankThreads) gb_rank_gather(const GSlot<MM>* 
 }
 
 // Large tables: compact occupied slots into (key, slot) pairs.
+constexpr int kCompactPer = 8;  // slots per thread per run of the compaction
+
 template <bool MM>
 __global__ void gb_compact(const GSlot<MM>* tab, uint32_t mask, uint32_t* okeys, uint32_t* oslot,
                            unsigned long long* counter) {
+  // each block takes runs of kCompactPer * blockDim.x slots and reserves its
+  // output range with one atomic per run (order within a run: warp, then lane)
+  __shared__ uint32_t s_warp[32];
+  __shared__ unsigned long long s_base;
   const int64_t nslots = (int64_t)mask + 2;
-  const int lane = threadIdx.x & 31;
-  for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < nslots; base += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t j = base + threadIdx.x;
-    const bool occ = j < nslots && occupied<MM>(tab, mask, j);
-    const uint32_t b = __ballot_sync(0xffffffffu, occ);
-    unsigned long long w0 = 0;
-    if (lane == 0 && b) w0 = atomicAdd(counter, (unsigned long long)__popc(b));
-    w0 = __shfl_sync(0xffffffffu, w0, 0);
-    if (occ) {
-      const unsigned long long pos = w0 + __popc(b & ((1u << lane) - 1u));
-      okeys[pos] = key_of<MM>(tab, mask, j);
-      oslot[pos] = (uint32_t)j;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t span = (int64_t)kCompactPer * blockDim.x;
+  for (int64_t base = (int64_t)blockIdx.x * span; base < nslots; base += (int64_t)gridDim.x * span) {
+    bool occ[kCompactPer];
+    uint32_t b[kCompactPer];
+    uint32_t wtot = 0;
+#pragma unroll
+    for (int i = 0; i < kCompactPer; ++i) {
+      const int64_t j = base + (int64_t)i * blockDim.x + threadIdx.x;
+      occ[i] = j < nslots && occupied<MM>(tab, mask, j);
+      b[i] = __ballot_sync(0xffffffffu, occ[i]);
+      wtot += __popc(b[i]);
     }
+    if (lane == 0) s_warp[warp] = wtot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t t = 0;
+      for (int w = 0; w < nw; ++w) {
+        const uint32_t c = s_warp[w];
+        s_warp[w] = t;
+        t += c;
+      }
+      s_base = t ? atomicAdd(counter, (unsigned long long)t) : 0ull;
+    }
+    __syncthreads();
+    unsigned long long pos = s_base + s_warp[warp];
+#pragma unroll
+    for (int i = 0; i < kCompactPer; ++i) {
+      if (occ[i]) {
+        const int64_t j = base + (int64_t)i * blockDim.x + threadIdx.x;
+        const unsigned long long p = pos + __popc(b[i] & lt);
+        okeys[p] = key_of<MM>(tab, mask, j);
+        oslot[p] = (uint32_t)j;
+      }
+      pos += __popc(b[i]);
+    }
+    __syncthreads();  // s_warp and s_base are rewritten by the next run
   }
 }
 

@@ -117,5 +117,14 @@ def test_rule_strategy_is_a_host_call(L):
     f[6] = 0.1
     f[12] = 10
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
-    f[4], f[5], f[6], f[8], f[12] = 1.0, 1.0, 0.0, 8 / 4096, 24
+    # all-distinct sample: a flat column whose key count the sample leaves open
+    f[4], f[5], f[6], f[8], f[12] = 1.0, 1.0, 0.0, 8 / 4096, 21
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SORT
+    f[0] = 16  # ... on a small column: one global table
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_GLOBAL
+    # flat with repeats (about 65536 keys, f2 well above 2): partitioned shared-memory build
+    f[0], f[4], f[5], f[6], f[8], f[12] = 28, 3970 / 4096, 3846 / 4096, 124 / 4096, 17 / 4096, 20
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
+    # strongly skewed: shared-memory tables keep the hot keys
+    f[8] = 0.2
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
