@@ -33,7 +33,7 @@ Sig signature(int vdt, uint32_t ops, const float* f) {
 }  // namespace
 
 agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                        const agg_options& o, cudaStream_t s, agg_groups** out);
+                        const agg_options& o, cudaStream_t s, agg_groups** out, const float* known_feat);
 
 static int smem_slots_sized(const float* f, bool mm) {
   bool covered = false;
@@ -77,7 +77,7 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
     for (int rep = 0; rep < std::max(1, reps) && st == AGG_OK; ++rep) {
       agg_groups* g = nullptr;
       cudaEventRecord(a, s);
-      st = groupby_with(keys, vals, n, vdt, ops, o, s, &g);
+      st = groupby_with(keys, vals, n, vdt, ops, o, s, &g, feat);
       cudaEventRecord(b, s);
       if (st != AGG_OK) break;
       cudaEventSynchronize(b);

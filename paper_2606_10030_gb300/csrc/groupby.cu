@@ -583,13 +583,18 @@ using namespace agg;
 
 namespace agg {
 
-// GROUP BY of a device column with explicit options (also used by the autotuner).
+// GROUP BY of a device column with explicit options. known_feat, when not
+// null, is the column's sketch (the autotuner passes it, so that its timed
+// candidates plan partitioning exactly as the untuned call would).
 agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                        const agg_options& o, cudaStream_t s, agg_groups** out) {
+                        const agg_options& o, cudaStream_t s, agg_groups** out, const float* known_feat) {
   float feat[F_COUNT] = {0};
   bool have = false;
   agg_status st = AGG_OK;
-  if (needs_sketch(o) && n > 0) {
+  if (known_feat && n > 0) {
+    std::memcpy(feat, known_feat, sizeof(feat));
+    have = true;
+  } else if (needs_sketch(o) && n > 0) {
     if (o.strategy == AGG_STRAT_LEARNED) {
       int learned = -1;
       st = sketch_and_select(keys, n, vdt, ops, o.sample_offset, s, feat, &learned);
@@ -630,7 +635,7 @@ static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n
                                const agg_options* opt, cudaStream_t s, agg_groups** out) {
   agg_options o{};
   if (opt) o = *opt;
-  return groupby_with(keys, vals, n, vdt, ops, o, s, out);
+  return groupby_with(keys, vals, n, vdt, ops, o, s, out, nullptr);
 }
 
 // ---------------------------------------------------------------------------
@@ -751,17 +756,45 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
   st = choose(kbuf(0), vbuf(0), std::min<int64_t>(chunk, n), vdt, ops, o, feat, have, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
-  if (c.strategy == AGG_STRAT_SORT) {
-    // the sort needs the whole column on the device
+  // The sort, and hash plans that partition the rows, work on the whole
+  // column: it is copied once (the prefetched chunks device to device, the
+  // rest from the host at link speed) and the device path runs on it. Plans
+  // that partition fall back to per-chunk builds when the device lacks room.
+  const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255);
+  const size_t col_bytes = kb + (size_t)n * es + 256;
+  bool whole = c.strategy == AGG_STRAT_SORT;
+  if (!whole && c.plan.partition && n > chunk) {
+    size_t free_b = 0, total_b = 0;
+    const double table_b = (double)(c.plan.slots + 2) * gslot_bytes(ops_minmax(ops));
+    whole = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)free_b > 4.0 * col_bytes + 2.0 * table_b;
+  }
+  if (whole) {
     void* full = nullptr;
-    const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255);
-    AGG_CUDA_TRY(dev_malloc_async(&full, kb + (size_t)n * es + 256, s));
+    AGG_CUDA_TRY(dev_malloc_async(&full, col_bytes, s));
     Free full_free{full, s};
-    AGG_CUDA_TRY(cudaMemcpyAsync(full, keys, (size_t)n * 4, cudaMemcpyHostToDevice, s));
-    AGG_CUDA_TRY(cudaMemcpyAsync((char*)full + kb, vals, (size_t)n * es, cudaMemcpyHostToDevice, s));
-    // the prefetched chunks are no longer needed; let s own the ring again
-    for (int b = 0; b < GbPipe::kRing; ++b) cudaStreamWaitEvent(s, pipe->ready[b], 0);
-    st = sort_groupby((const uint32_t*)full, (char*)full + kb, n, vdt, ops, s, &g);
+    uint32_t* fk = (uint32_t*)full;
+    char* fv = (char*)full + kb;
+    const int64_t pre = std::min<int64_t>(next_copy, nchunks);  // chunks already queued into the ring
+    if (n > pre * chunk) {
+      const int64_t r0 = pre * chunk;
+      AGG_CUDA_TRY(cudaMemcpyAsync(fk + r0, keys + r0, (size_t)(n - r0) * 4, cudaMemcpyHostToDevice, pipe->copy));
+      AGG_CUDA_TRY(cudaMemcpyAsync(fv + (size_t)r0 * es, (const char*)vals + (size_t)r0 * es, (size_t)(n - r0) * es,
+                                   cudaMemcpyHostToDevice, pipe->copy));
+    }
+    cudaEvent_t done_ev;
+    AGG_CUDA_TRY(cudaEventCreateWithFlags(&done_ev, cudaEventDisableTiming));
+    EvFree done_free{done_ev};
+    cudaEventRecord(done_ev, pipe->copy);
+    for (int64_t k = 0; k < pre; ++k) {
+      const int b = (int)(k % GbPipe::kRing);
+      const int64_t r0 = k * chunk, rows = std::min<int64_t>(chunk, n - r0);
+      cudaStreamWaitEvent(s, pipe->ready[b], 0);
+      AGG_CUDA_TRY(cudaMemcpyAsync(fk + r0, kbuf(b), (size_t)rows * 4, cudaMemcpyDeviceToDevice, s));
+      AGG_CUDA_TRY(cudaMemcpyAsync(fv + (size_t)r0 * es, vbuf(b), (size_t)rows * es, cudaMemcpyDeviceToDevice, s));
+    }
+    cudaStreamWaitEvent(s, done_ev, 0);
+    if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(fk, fv, n, vdt, ops, s, &g);
+    else st = hash_device(fk, fv, n, vdt, ops, c.plan, s, &g);
     if (st != AGG_OK) return st;
   } else {
     HashPlan plan = c.plan;

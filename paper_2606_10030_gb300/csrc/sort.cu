@@ -141,14 +141,20 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
                                                            const int64_t* n_dev, int shift, int64_t ntiles,
                                                            uint32_t* __restrict__ counts) {
   __shared__ uint32_t h[256];
-  if (threadIdx.x < 256) h[threadIdx.x] = 0;
-  __syncthreads();
   const int64_t n = rows_of(n_cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
-#pragma unroll 4
+  uint32_t k[kSortItems];  // every load of the tile is issued before the first count
+#pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
-    int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
-    if (j < n) atomicAdd(&h[digit_of<HASHED>(keys[j], shift)], 1u);
+    const int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
+    k[i] = j < n ? keys[j] : 0u;
+  }
+  if (threadIdx.x < 256) h[threadIdx.x] = 0;
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < kSortItems; ++i) {
+    const int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
+    if (j < n) atomicAdd(&h[digit_of<HASHED>(k[i], shift)], 1u);
   }
   __syncthreads();
   if (threadIdx.x < 256) counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];

@@ -223,6 +223,19 @@ def test_host_fed_groupby(dt, strategy):
     check_groups(res, keys, vals)
 
 
+@pytest.mark.parametrize("partition", [-1, 1, 2])
+def test_host_fed_groupby_high_cardinality(partition):
+    """Partitioned plans copy the whole column and run the device path; -1 keeps per-chunk builds."""
+    n = 20_000_017
+    keys = dg.keys_zipf(n, 1 << 20, 1.0, 4)
+    vals = dg.values("f32", n, 4)
+    g = agg.agg_groupby_host(torch.from_numpy(keys).pin_memory(), torch.from_numpy(vals).pin_memory(),
+                             agg.AGG_ALL, agg.options(agg.AGG_STRAT_SMEM, partition=partition))
+    res = g.to_host()
+    g.free()
+    check_groups(res, keys, vals)
+
+
 def _dev_consts():
     p = torch.cuda.get_device_properties(0)
     return float(p.shared_memory_per_block_optin), float(p.L2_cache_size)
