@@ -7,7 +7,7 @@
 //                  global output offset;
 //   scan           device-wide exclusive scan of those counts;
 //   radix_scatter  per tile: stable rank of every row among rows with the
-//                  same digit (warp match + per-warp running counts), staging
+//                  same digit (ballots + per-warp running counts), staging
 //                  of the tile in shared memory in digit order, then coalesced
 //                  writes of each digit's run to its global offset.
 #include "sort.cuh"
@@ -160,16 +160,19 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
   if (threadIdx.x < 256) counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
 }
 
-// Per tile (512 threads x 8 rows, each warp owning 256 consecutive rows):
-// 1. each warp ranks its rows among equal digits, round by round, with a
-//    warp match and a per-warp running digit count (only the ranks are kept
-//    in registers);
-// 2. digit totals are scanned across warps and digits;
-// 3. rows are re-loaded (they are in L2) and staged in shared memory in digit
-//    order;
+// Per tile (512 threads x 8 rows, each warp owning 256 consecutive rows;
+// three blocks per SM, so at most 40 registers a thread):
+// 0. the warp's keys are loaded into registers up front;
+// 1. each warp ranks its rows among equal digits, round by round, with
+//    digit-bit ballots and a per-warp running digit count (ranks stay in
+//    registers);
+// 2. digit totals are scanned across warps and digits, and the tile's digit
+//    starts folded into the per-warp offsets and the global offsets;
+// 3. values are loaded (keys are in registers) and rows staged in shared
+//    memory in digit order;
 // 4. each digit's run is written to its global offset with coalesced stores.
 template <class P, bool HASHED>
-__global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t* __restrict__ keys,
                                                               const P* __restrict__ vals, uint32_t* __restrict__ okeys,
                                                               P* __restrict__ ovals, int64_t n_cap,
                                                               const int64_t* n_dev, int shift, int64_t ntiles,
@@ -179,27 +182,40 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
   P* stage_v = (P*)sm_raw;                                // kSortTile
   uint32_t* stage_k = (uint32_t*)(stage_v + kSortTile);  // kSortTile
   uint32_t* whist = stage_k + kSortTile;                 // kWarps x 256
-  uint32_t* tstart = whist + kWarps * 256;               // 256
-  uint32_t* gbase = tstart + 256;                        // 256
+  uint32_t* gbase = whist + kWarps * 256;                // 256
 
   const int64_t n = rows_of(n_cap, n_dev);
   const int64_t tile0 = (int64_t)blockIdx.x * kSortTile;
   if (tile0 >= n) return;
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   for (int i = threadIdx.x; i < kWarps * 256; i += kSortThreads) whist[i] = 0;
-  if (threadIdx.x < 256) gbase[threadIdx.x] = offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x];
+  // the tile's global digit offsets are needed only from step 2 on: their
+  // load is issued now and waited for there
+  const uint32_t goff = threadIdx.x < 256 ? offsets[(int64_t)threadIdx.x * ntiles + blockIdx.x] : 0u;
   __syncthreads();
 
   uint32_t lr[kSortItems];
+  uint32_t kr[kSortItems];
   const uint32_t lt = (1u << lane) - 1u;
   const int64_t wbase = tile0 + (int64_t)w * (kSortItems * 32);
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
+    kr[r] = j < n ? keys[j] : 0u;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; ++r) {
+    const int64_t j = wbase + r * 32 + lane;
     const bool ok = j < n;
-    const uint32_t d = ok ? digit_of<HASHED>(keys[j], shift) : 0u;
-    const uint32_t tag = ok ? d : (0x100u | (uint32_t)lane);
-    const uint32_t peers = __match_any_sync(0xffffffffu, tag);
+    const uint32_t d = ok ? digit_of<HASHED>(kr[r], shift) : 0u;
+    // lanes holding the same digit: one ballot per digit bit
+    uint32_t peers = __ballot_sync(0xffffffffu, ok);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const uint32_t bit = (d >> b) & 1u;
+      const uint32_t m = __ballot_sync(0xffffffffu, bit != 0u);
+      peers &= bit ? m : ~m;
+    }
     const uint32_t before = ok ? whist[w * 256 + d] : 0u;
     lr[r] = before + __popc(peers & lt);
     __syncwarp();
@@ -219,16 +235,23 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
       }
     }
     const uint32_t e = block_exclusive_scan(threadIdx.x < 256 ? run : 0u, nullptr);
-    if (threadIdx.x < 256) tstart[threadIdx.x] = e;
+    if (threadIdx.x < 256) {
+      // fold the digit's tile start into its per-warp offsets, and its global
+      // offset minus the tile start into gbase (mod 2^32: positions are < 2^32)
+      const int d = threadIdx.x;
+#pragma unroll
+      for (int ww = 0; ww < kWarps; ++ww) whist[ww * 256 + d] += e;
+      gbase[d] = goff - e;
+    }
   }
   __syncthreads();
 #pragma unroll
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
     if (j < n) {
-      const uint32_t key = keys[j];
+      const uint32_t key = kr[r];
       const uint32_t d = digit_of<HASHED>(key, shift);
-      const uint32_t lp = tstart[d] + whist[w * 256 + d] + lr[r];
+      const uint32_t lp = whist[w * 256 + d] + lr[r];
       stage_k[lp] = key;
       stage_v[lp] = vals[j];
     }
@@ -238,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
   for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
     const uint32_t key = stage_k[i];
     const uint32_t d = digit_of<HASHED>(key, shift);
-    const int64_t pos = (int64_t)gbase[d] + (i - (int64_t)tstart[d]);
+    const int64_t pos = (int64_t)(uint32_t)(gbase[d] + (uint32_t)i);
     okeys[pos] = key;
     ovals[pos] = stage_v[i];
   }
@@ -246,7 +269,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_scatter(const uint32_t* __
 
 template <class P>
 static size_t scatter_smem() {
-  return (size_t)kSortTile * (sizeof(P) + 4) + ((kSortThreads / 32) * 256 + 512) * 4;
+  return (size_t)kSortTile * (sizeof(P) + 4) + ((kSortThreads / 32) * 256 + 256) * 4;
 }
 
 size_t radix_tmp_bytes(int64_t n_cap) {

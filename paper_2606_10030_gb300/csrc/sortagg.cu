@@ -1,15 +1,22 @@
 // GROUP BY by sorting (step a5s; the sort-based group-by of Sec. 7).
 //
 // 1. Stable LSD radix sort of the (key, value) pairs by key.
-// 2. seg_heads: per 4096-row tile, the number of run heads (rows whose key
-//    differs from the previous row's); an exclusive scan gives each tile the
-//    index of its first run, and the total is the number of groups d.
-// 3. seg_reduce: each thread folds 16 consecutive sorted rows. A run that
-//    starts and ends inside one thread is complete and stored directly; a run
-//    piece that crosses a thread boundary is combined with the other pieces of
-//    the same run in the warp (match on the run index) and added to the output
-//    with one set of atomics per warp.
-// 4. seg_finalize: decode MIN/MAX images and compute AVG.
+// 2. seg_count: each warp owns a chunk of 512 consecutive sorted rows and
+//    counts its run heads (rows whose key differs from the previous row's);
+//    an exclusive scan gives every chunk the index of the first run starting
+//    in it, and the total is the number of groups d.
+// 3. seg_reduce: each lane folds 16 consecutive rows of its warp's chunk in
+//    order (16-byte vector loads); a run begun and ended in the lane is
+//    written in its final form. The parts of runs that cross lanes are joined
+//    with one segmented scan over the warp, and the run a lane's first head
+//    ends is written by that lane. The part of a run that crosses the chunk's
+//    start or end is written as a piece (at most two per chunk).
+// 4. The pieces of one run are consecutive in chunk order: their targets are
+//    cleared, the pieces added with atomics (one set per run per warp), and
+//    the targets brought to the raw form of the finished runs.
+// 5. seg_finalize converts every group to the output encodings and computes
+//    AVG in float64 with converged warps (GB300's float64 pipe is narrow; in
+//    the divergent per-run code it was the bottleneck).
 // Runs come out in ascending key order by construction.
 #include <type_traits>
 
@@ -19,8 +26,11 @@
 namespace agg {
 
 constexpr int kSegThreads = 256;
-constexpr int kSegItems = 16;
-constexpr int kSegTile = kSegThreads * kSegItems;
+constexpr int kSegItems = 16;                // consecutive sorted rows per lane
+constexpr int kSegRounds = kSegItems;        // rounds of 32 rows when counting heads
+constexpr int kSegChunk = 32 * kSegItems;    // sorted rows per warp
+constexpr int kSegChunksPerBlock = kSegThreads / 32;
+constexpr uint32_t kNoRun = 0xFFFFFFFFu;
 
 template <int DT> struct SV;
 template <> struct SV<AGG_I32> { using T = int32_t; using P = uint32_t; };
@@ -43,240 +53,409 @@ __device__ __forceinline__ uint64_t sv_img(typename SV<DT>::T v) {
   return img_i64((int64_t)v);
 }
 
-__device__ __forceinline__ uint32_t block_excl_scan256(uint32_t v) {
-  __shared__ uint32_t ws[kSegThreads / 32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
-    if (lane >= o) x += y;
+constexpr bool is_fp(int dt) { return dt == AGG_F32 || dt == AGG_F64; }
+
+// Partial aggregate of rows of one run: count, sum (compensated pair in the
+// input precision for floats, wrapping 64-bit integer otherwise) and the
+// order-preserving images of MIN and MAX.
+template <int DT>
+struct SAcc {
+  using F = typename std::conditional<DT == AGG_F32, float, double>::type;
+  uint32_t cnt;
+  F s, c;
+  unsigned long long is;
+  unsigned long long mn, mx;
+};
+
+template <int DT, bool MM>
+__device__ __forceinline__ SAcc<DT> acc_of(bool valid, typename SV<DT>::T v) {
+  using F = typename SAcc<DT>::F;
+  SAcc<DT> a;
+  a.cnt = valid ? 1u : 0u;
+  a.s = valid && is_fp(DT) ? (F)v : F(0);
+  a.c = F(0);
+  a.is = valid && !is_fp(DT) ? (unsigned long long)(int64_t)v : 0ull;
+  if (MM) {
+    const unsigned long long m = sv_img<DT>(v);
+    a.mn = valid ? m : ~0ull;
+    a.mx = valid ? m : 0ull;
   }
-  if (lane == 31) ws[w] = x;
-  __syncthreads();
-  if (w == 0) {
-    uint32_t s = lane < kSegThreads / 32 ? ws[lane] : 0;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
-      if (lane >= o) s += y;
-    }
-    if (lane < kSegThreads / 32) ws[lane] = s;
+  return a;
+}
+
+// a holds earlier rows of the run than b.
+template <int DT, bool MM>
+__device__ __forceinline__ SAcc<DT> acc_combine(const SAcc<DT>& a, const SAcc<DT>& b) {
+  using F = typename SAcc<DT>::F;
+  SAcc<DT> r;
+  r.cnt = a.cnt + b.cnt;
+  if (DT == AGG_F32) {
+    F t, e;
+    two_sum(a.s, b.s, t, e);
+    r.s = t;
+    r.c = a.c + b.c + e;
+  } else if (DT == AGG_F64) {  // plain float64 additions: GB300's FP64 pipe is narrow
+    r.s = a.s + b.s;
+    r.c = F(0);
+  } else {
+    r.s = F(0);
+    r.c = F(0);
   }
-  __syncthreads();
-  uint32_t r = (w ? ws[w - 1] : 0) + x - v;
-  __syncthreads();
+  r.is = is_fp(DT) ? 0ull : a.is + b.is;
+  if (MM) {
+    r.mn = min(a.mn, b.mn);
+    r.mx = max(a.mx, b.mx);
+  }
   return r;
 }
 
-__global__ void __launch_bounds__(kSegThreads) seg_heads(const uint32_t* __restrict__ sk, int64_t n,
-                                                         uint32_t* __restrict__ tile_counts) {
-  const int64_t r0 = (int64_t)blockIdx.x * kSegTile + (int64_t)threadIdx.x * kSegItems;
-  uint32_t prev = r0 > 0 && r0 - 1 < n ? sk[r0 - 1] : 0;
-  uint32_t c = 0;
-#pragma unroll
-  for (int i = 0; i < kSegItems; ++i) {
-    const int64_t r = r0 + i;
-    if (r < n) {
-      const uint32_t k = sk[r];
-      c += (r == 0 || k != prev) ? 1u : 0u;
-      prev = k;
-    }
+template <int DT, bool MM, bool UP>
+__device__ __forceinline__ SAcc<DT> acc_shfl(const SAcc<DT>& a, int arg) {
+  SAcc<DT> r;
+  r.cnt = UP ? __shfl_up_sync(0xffffffffu, a.cnt, arg) : __shfl_sync(0xffffffffu, a.cnt, arg);
+  if (is_fp(DT)) {
+    r.s = UP ? __shfl_up_sync(0xffffffffu, a.s, arg) : __shfl_sync(0xffffffffu, a.s, arg);
+    r.c = UP ? __shfl_up_sync(0xffffffffu, a.c, arg) : __shfl_sync(0xffffffffu, a.c, arg);
+    r.is = 0ull;
+  } else {
+    r.s = 0;
+    r.c = 0;
+    r.is = UP ? __shfl_up_sync(0xffffffffu, a.is, arg) : __shfl_sync(0xffffffffu, a.is, arg);
   }
-#pragma unroll
-  for (int o = 16; o >= 1; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-  __shared__ uint32_t ws[kSegThreads / 32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = c;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    uint32_t t = 0;
-    for (int i = 0; i < kSegThreads / 32; ++i) t += ws[i];
-    tile_counts[blockIdx.x] = t;
+  if (MM) {
+    r.mn = UP ? __shfl_up_sync(0xffffffffu, a.mn, arg) : __shfl_sync(0xffffffffu, a.mn, arg);
+    r.mx = UP ? __shfl_up_sync(0xffffffffu, a.mx, arg) : __shfl_sync(0xffffffffu, a.mx, arg);
   }
+  return r;
+}
+
+// Sum of a piece (added with atomics): int64 bits or float64 bits.
+template <int DT>
+__device__ __forceinline__ unsigned long long sum_bits(const SAcc<DT>& a) {
+  if (DT == AGG_F32) return (unsigned long long)__double_as_longlong((double)a.s + (double)a.c);
+  if (DT == AGG_F64) return (unsigned long long)__double_as_longlong(a.s);
+  return a.is;
+}
+
+// Sum as first stored, before seg_finalize: int64 bits, float64 bits, or for
+// float32 the compensated pair (s in the low word, c in the high word), so
+// that no float64 instruction runs in the divergent per-run code.
+template <int DT>
+__device__ __forceinline__ unsigned long long raw_sum(const SAcc<DT>& a) {
+  if (DT == AGG_F32)
+    return ((unsigned long long)__float_as_uint((float)a.c) << 32) | (unsigned long long)__float_as_uint((float)a.s);
+  if (DT == AGG_F64) return (unsigned long long)__double_as_longlong((double)a.s);
+  return a.is;
+}
+
+template <int DT>
+__device__ __forceinline__ double fsum_of_raw(unsigned long long r) {
+  if (DT == AGG_F32)
+    return (double)__uint_as_float((uint32_t)r) + (double)__uint_as_float((uint32_t)(r >> 32));
+  if (DT == AGG_F64) return __longlong_as_double((long long)r);
+  return (double)(long long)r;
 }
 
 struct SegOut {
   uint32_t* keys;
   unsigned long long* count;
   unsigned long long* sum;
-  unsigned long long* minc;  // complement of the min image (atomicMax)
-  unsigned long long* mx;    // max image
+  unsigned long long* min;
+  unsigned long long* max;
   double* avg;
 };
 
-struct Piece {
-  uint32_t cnt;
-  unsigned long long sum;  // int64 bits or double bits
+// Part of a run cut by a chunk boundary.
+struct SegPiece {
+  uint32_t run, key;
+  uint32_t cnt, pad;
+  unsigned long long sum;  // int64 bits or float64 bits
   unsigned long long mn, mx;
 };
 
+// MIN/MAX image -> the output encoding (float64 bits for floats, int64 otherwise).
 template <int DT>
-__device__ __forceinline__ unsigned long long sum_add(unsigned long long a, unsigned long long b) {
-  if (DT == AGG_F32 || DT == AGG_F64)
-    return (unsigned long long)__double_as_longlong(__longlong_as_double((long long)a) +
-                                                    __longlong_as_double((long long)b));
-  return a + b;
+__device__ __forceinline__ unsigned long long out_of_img(unsigned long long m) {
+  if (DT == AGG_F32) return (unsigned long long)__double_as_longlong((double)f32_of_img((uint32_t)m));
+  if (DT == AGG_F64) return (unsigned long long)__double_as_longlong(f64_of_img(m));
+  return (unsigned long long)i64_of_img(m);
 }
 
+// A finished run in raw form (count, raw sum, MIN/MAX images); seg_finalize
+// converts every group afterwards with converged warps.
 template <int DT, bool MM>
-__device__ __forceinline__ void store_run(const SegOut& o, uint32_t run, uint32_t key, const Piece& p) {
+__device__ __forceinline__ void store_final(const SegOut& o, uint32_t run, uint32_t key, const SAcc<DT>& a) {
   o.keys[run] = key;
-  o.count[run] = p.cnt;
-  o.sum[run] = p.sum;
+  o.count[run] = a.cnt;
+  o.sum[run] = raw_sum<DT>(a);
   if (MM) {
-    o.minc[run] = ~p.mn;
-    o.mx[run] = p.mx;
+    o.min[run] = a.mn;
+    o.max[run] = a.mx;
   }
 }
 
 template <int DT, bool MM>
-__device__ __forceinline__ void add_run(const SegOut& o, uint32_t run, uint32_t key, const Piece& p) {
-  o.keys[run] = key;
-  atomicAdd(&o.count[run], (unsigned long long)p.cnt);
-  if (DT == AGG_F32 || DT == AGG_F64) atomicAdd((double*)&o.sum[run], __longlong_as_double((long long)p.sum));
-  else atomicAdd(&o.sum[run], p.sum);
-  if (MM) {
-    atomicMax(&o.minc[run], ~p.mn);
-    atomicMax(&o.mx[run], p.mx);
-  }
+__device__ __forceinline__ void store_piece(SegPiece* p, uint32_t run, uint32_t key, const SAcc<DT>& a) {
+  SegPiece q;
+  q.run = run;
+  q.key = key;
+  q.cnt = a.cnt;
+  q.pad = 0;
+  q.sum = sum_bits<DT>(a);
+  q.mn = MM ? a.mn : 0ull;
+  q.mx = MM ? a.mx : 0ull;
+  *p = q;
 }
 
-// Warp-combine boundary pieces with equal run index, then one atomic set per run.
-template <int DT, bool MM>
-__device__ __forceinline__ void warp_emit(const SegOut& o, bool has, uint32_t run, uint32_t key, Piece p) {
+// Run heads per chunk of kSegChunk sorted rows (one warp per chunk).
+__global__ void __launch_bounds__(kSegThreads) seg_count(const uint32_t* __restrict__ sk, int64_t n,
+                                                         uint32_t* __restrict__ chunk_heads) {
   const int lane = threadIdx.x & 31;
-  // lanes without a piece get a tag no run index can take
-  const unsigned long long tag = has ? (unsigned long long)run : ((1ull << 32) | (unsigned long long)lane);
-  const uint32_t peers = __match_any_sync(0xffffffffu, tag);
-  const bool leader = has && (peers & ((1u << lane) - 1u)) == 0;
-  for (int src = 0; src < 32; ++src) {
-    const uint32_t c2 = __shfl_sync(0xffffffffu, p.cnt, src);
-    const unsigned long long s2 = __shfl_sync(0xffffffffu, p.sum, src);
-    unsigned long long n2 = 0, x2 = 0;
-    if (MM) {
-      n2 = __shfl_sync(0xffffffffu, p.mn, src);
-      x2 = __shfl_sync(0xffffffffu, p.mx, src);
-    }
-    if (leader && src != lane && ((peers >> src) & 1u)) {
-      p.cnt += c2;
-      p.sum = sum_add<DT>(p.sum, s2);
-      if (MM) {
-        p.mn = min(p.mn, n2);
-        p.mx = max(p.mx, x2);
-      }
-    }
+  const int64_t chunk = (int64_t)blockIdx.x * kSegChunksPerBlock + (threadIdx.x >> 5);
+  const int64_t r0 = chunk * kSegChunk;
+  if (r0 >= n) return;
+  uint32_t k[kSegRounds];
+#pragma unroll
+  for (int r = 0; r < kSegRounds; ++r) {
+    const int64_t row = r0 + r * 32 + lane;
+    k[r] = row < n ? sk[row] : 0u;
   }
-  if (leader) add_run<DT, MM>(o, run, key, p);
+  uint32_t prev = r0 > 0 ? sk[r0 - 1] : 0u;
+  uint32_t heads = 0;
+#pragma unroll
+  for (int r = 0; r < kSegRounds; ++r) {
+    const int64_t row = r0 + r * 32 + lane;
+    uint32_t pk = __shfl_up_sync(0xffffffffu, k[r], 1);
+    if (lane == 0) pk = prev;
+    prev = __shfl_sync(0xffffffffu, k[r], 31);
+    heads += __popc(__ballot_sync(0xffffffffu, row < n && (row == 0 || k[r] != pk)));
+  }
+  if (lane == 0) chunk_heads[chunk] = heads;
 }
 
 template <int DT, bool MM>
 __global__ void __launch_bounds__(kSegThreads) seg_reduce(const uint32_t* __restrict__ sk,
                                                           const typename SV<DT>::P* __restrict__ sv, int64_t n,
-                                                          const uint32_t* __restrict__ tile_first_run, SegOut o) {
-  using T = typename SV<DT>::T;
-  using F = typename std::conditional<DT == AGG_F32, float, double>::type;
-  const int64_t r0 = (int64_t)blockIdx.x * kSegTile + (int64_t)threadIdx.x * kSegItems;
+                                                          const uint32_t* __restrict__ chunk_first, SegOut o,
+                                                          SegPiece* __restrict__ pieces) {
+  using P = typename SV<DT>::P;
+  const int lane = threadIdx.x & 31;
+  const int64_t chunk = (int64_t)blockIdx.x * kSegChunksPerBlock + (threadIdx.x >> 5);
+  const int64_t r0 = chunk * kSegChunk;
+  if (r0 >= n) return;
+  // this lane's kSegItems consecutive rows, loaded with 16-byte vectors when whole
+  const int64_t l0 = r0 + (int64_t)lane * kSegItems;
+  const int nv = l0 >= n ? 0 : (int)(n - l0 < kSegItems ? n - l0 : kSegItems);
   uint32_t k[kSegItems];
-  T v[kSegItems];
-  uint32_t heads = 0;
-  const uint32_t prev0 = (r0 > 0 && r0 - 1 < n) ? sk[r0 - 1] : 0;
-  {
-    uint32_t prev = prev0;
+  P v[kSegItems];
+  if (nv == kSegItems) {
+    const uint4* kq = (const uint4*)(sk + l0);
+    const uint4* vq = (const uint4*)(sv + l0);
+#pragma unroll
+    for (int q = 0; q < kSegItems / 4; ++q) {
+      const uint4 a = kq[q];
+      k[4 * q] = a.x;
+      k[4 * q + 1] = a.y;
+      k[4 * q + 2] = a.z;
+      k[4 * q + 3] = a.w;
+    }
+    constexpr int VQ = kSegItems * (int)sizeof(P) / 16;
+#pragma unroll
+    for (int q = 0; q < VQ; ++q) {
+      const uint4 a = vq[q];
+      const uint32_t w[4] = {a.x, a.y, a.z, a.w};
+      memcpy((char*)v + 16 * q, w, 16);
+    }
+  } else {
 #pragma unroll
     for (int i = 0; i < kSegItems; ++i) {
-      const int64_t r = r0 + i;
-      k[i] = r < n ? sk[r] : 0;
-      v[i] = r < n ? sv_val<DT>(sv[r]) : T(0);
-      if (r < n && (r == 0 || k[i] != prev)) heads |= 1u << i;
-      prev = k[i];
+      k[i] = i < nv ? sk[l0 + i] : 0u;
+      v[i] = i < nv ? sv[l0 + i] : P(0);
     }
   }
-  const uint32_t excl = block_excl_scan256((uint32_t)__popc(heads));
-  const int nv = (int)(r0 < n ? (n - r0 < kSegItems ? n - r0 : kSegItems) : 0);
-  const bool next_is_head = (r0 + kSegItems >= n) || (nv == kSegItems && sk[r0 + kSegItems] != k[kSegItems - 1]);
-  // run index of the run holding row r0 (the run continuing from the left, or the first head's)
-  uint32_t run = tile_first_run[blockIdx.x] + excl - ((heads & 1u) ? 0u : 1u);
-  Piece first{}, last{};
-  bool have_first = false, have_last = false;
-  uint32_t first_key = 0, last_key = 0, first_run = 0, last_run = 0;
-  // current piece
-  bool open = false, open_at_head = false;
-  uint32_t pk = 0;
-  Piece cur{};
-  F cs = 0, cc = 0;  // compensated float sum of the current piece
-  long long isum = 0;
-  auto close_piece = [&](bool ends_here) {
-    cur.sum = (DT == AGG_F32 || DT == AGG_F64) ? (unsigned long long)__double_as_longlong((double)cs + (double)cc)
-                                               : (unsigned long long)isum;
-    const bool complete = open_at_head && ends_here;
-    if (complete) {
-      store_run<DT, MM>(o, run, pk, cur);
-    } else if (!open_at_head) {
-      first = cur; first_key = pk; first_run = run; have_first = true;
-    } else {
-      last = cur; last_key = pk; last_run = run; have_last = true;
-    }
-  };
+  uint32_t before = __shfl_up_sync(0xffffffffu, k[kSegItems - 1], 1);  // key of the row before this lane's first
+  if (lane == 0) before = r0 > 0 ? sk[r0 - 1] : 0u;
+  uint32_t hb = 0;  // run heads among this lane's rows
+#pragma unroll
+  for (int i = 0; i < kSegItems; ++i)
+    if (i < nv && (l0 + i == 0 || k[i] != (i ? k[i - 1] : before))) hb |= 1u << i;
+  const uint32_t nh = (uint32_t)__popc(hb);
+  uint32_t hin = nh;  // inclusive scan of head counts over the warp's lanes
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, hin, d);
+    if (lane >= d) hin += y;
+  }
+  const uint32_t hx = hin - nh;  // heads in earlier lanes of the chunk
+  const uint32_t heads_in_chunk = __shfl_sync(0xffffffffu, hin, 31);
+  const uint32_t cf = chunk_first[chunk];
+  // Fold the lane's rows: rows before its first head form the prefix (the end
+  // of a run begun earlier); a run begun and ended in the lane is final here;
+  // the run begun at its last head stays open.
+  SAcc<DT> pre = acc_of<DT, MM>(false, sv_val<DT>(P(0)));
+  SAcc<DT> cur = pre;
+  bool open = false;
+  uint32_t next_run = cf + hx, cur_run = 0, cur_key = 0;
 #pragma unroll
   for (int i = 0; i < kSegItems; ++i) {
-    if (i >= nv) break;
-    const bool h = (heads >> i) & 1u;
-    if (h && open) {
-      close_piece(true);
-      ++run;
-    }
-    if (!open || h) {
-      open = true;
-      open_at_head = h;
-      pk = k[i];
-      cur.cnt = 0;
-      cur.mn = ~0ull;
-      cur.mx = 0;
-      cs = 0; cc = 0; isum = 0;
-    }
-    cur.cnt += 1;
-    if (DT == AGG_F32 || DT == AGG_F64) {
-      F t, e;
-      two_sum(cs, (F)v[i], t, e);
-      cs = t;
-      cc += e;
-    } else {
-      isum += (long long)v[i];
-    }
-    if (MM) {
-      const uint64_t m = sv_img<DT>(v[i]);
-      cur.mn = min(cur.mn, (unsigned long long)m);
-      cur.mx = max(cur.mx, (unsigned long long)m);
+    if (i < nv) {
+      const SAcc<DT> a = acc_of<DT, MM>(true, sv_val<DT>(v[i]));
+      if ((hb >> i) & 1u) {
+        if (open) store_final<DT, MM>(o, cur_run, cur_key, cur);
+        open = true;
+        cur = a;
+        cur_run = next_run++;
+        cur_key = k[i];
+      } else if (open) {
+        cur = acc_combine<DT, MM>(cur, a);
+      } else {
+        pre = acc_combine<DT, MM>(pre, a);
+      }
     }
   }
-  if (open) close_piece(next_is_head);
-  // A piece that neither starts at a head nor ends here is both first and last.
-  warp_emit<DT, MM>(o, have_first, first_run, first_key, first);
-  warp_emit<DT, MM>(o, have_last, last_run, last_key, last);
+  // Segmented inclusive scan over the lanes of the open parts: a lane with a
+  // head starts a new run; a lane without one extends the run open before it.
+  SAcc<DT> x = open ? cur : pre;
+  const uint32_t fm = __ballot_sync(0xffffffffu, open);
+  const uint32_t le = lane == 31 ? 0xffffffffu : ((2u << lane) - 1u);
+  const uint32_t fle = fm & le;
+  const int seg0 = fle ? 31 - __clz(fle) : 0;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const SAcc<DT> b = acc_shfl<DT, MM, true>(x, d);
+    if (lane - d >= seg0) x = acc_combine<DT, MM>(b, x);
+  }
+  SAcc<DT> left = acc_shfl<DT, MM, true>(x, 1);  // the run open at the end of the previous lane
+  if (lane == 0) left = acc_of<DT, MM>(false, sv_val<DT>(P(0)));
+  // A lane with a head ends, with its prefix, the run open before it.
+  bool wrote_first = false;
+  if (open) {
+    const SAcc<DT> tot = acc_combine<DT, MM>(left, pre);
+    if (tot.cnt > 0) {
+      if (hx == 0) {  // begun before the chunk: a piece
+        store_piece<DT, MM>(&pieces[2 * chunk], cf - 1, before, tot);
+        wrote_first = true;
+      } else {
+        store_final<DT, MM>(o, cf + hx - 1, before, tot);
+      }
+    }
+  }
+  wrote_first = __any_sync(0xffffffffu, wrote_first);
+  // The run open at the end of the chunk.
+  const SAcc<DT> xl = acc_shfl<DT, MM, false>(x, 31);
+  if (lane == 0) {
+    const int64_t last = (r0 + kSegChunk < n ? r0 + kSegChunk : n) - 1;
+    const uint32_t last_key = sk[last];
+    const bool ends = last + 1 >= n || sk[last + 1] != last_key;
+    const uint32_t run = cf + heads_in_chunk - 1;
+    if (ends && heads_in_chunk > 0) {
+      store_final<DT, MM>(o, run, last_key, xl);
+      pieces[2 * chunk + 1].run = kNoRun;
+    } else {
+      store_piece<DT, MM>(&pieces[2 * chunk + 1], run, last_key, xl);
+    }
+    if (!wrote_first) pieces[2 * chunk].run = kNoRun;
+  }
 }
 
+// Targets of pieces: clear count and sum, set MIN/MAX accumulators (the
+// complement of the MIN image and the MAX image, both combined with atomicMax).
+template <bool MM>
+__global__ void seg_piece_clear(const SegPiece* __restrict__ pieces, int64_t np, SegOut o) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t run = pieces[p].run;
+    if (run == kNoRun) continue;
+    o.count[run] = 0;
+    o.sum[run] = 0;
+    if (MM) {
+      o.min[run] = 0;
+      o.max[run] = 0;
+    }
+  }
+}
+
+// Add the pieces; pieces of one run in a warp are combined first.
+template <int DT, bool MM>
+__global__ void seg_piece_add(const SegPiece* __restrict__ pieces, int64_t np, SegOut o) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t b = (int64_t)blockIdx.x * blockDim.x; b < np; b += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t p = b + threadIdx.x;
+    SegPiece q;
+    q.run = kNoRun;
+    if (p < np) q = pieces[p];
+    const bool has = q.run != kNoRun;
+    const uint32_t vm = __ballot_sync(0xffffffffu, has);
+    if (has) {
+    const uint32_t peers = __match_any_sync(vm, q.run);
+    const bool leader = (peers & ((1u << lane) - 1u)) == 0;
+    unsigned long long cnt = q.cnt, sum = q.sum, mn = q.mn, mx = q.mx;
+    // gather the peers' parts into the leader (peers form one set per run)
+    for (int src = 0; src < 32; ++src) {
+      if (!((vm >> src) & 1u)) continue;
+      const unsigned long long c2 = __shfl_sync(vm, cnt, src);
+      const unsigned long long s2 = __shfl_sync(vm, sum, src);
+      const unsigned long long n2 = MM ? __shfl_sync(vm, mn, src) : 0ull;
+      const unsigned long long x2 = MM ? __shfl_sync(vm, mx, src) : 0ull;
+      if (leader && src != lane && ((peers >> src) & 1u)) {
+        cnt += c2;
+        if (is_fp(DT))
+          sum = (unsigned long long)__double_as_longlong(__longlong_as_double((long long)sum) +
+                                                         __longlong_as_double((long long)s2));
+        else
+          sum += s2;
+        if (MM) {
+          mn = min(mn, n2);
+          mx = max(mx, x2);
+        }
+      }
+    }
+    if (leader) {
+      o.keys[q.run] = q.key;
+      atomicAdd(&o.count[q.run], cnt);
+      if (is_fp(DT)) atomicAdd((double*)&o.sum[q.run], __longlong_as_double((long long)sum));
+      else atomicAdd(&o.sum[q.run], sum);
+      if (MM) {
+        atomicMax(&o.min[q.run], ~mn);
+        atomicMax(&o.max[q.run], mx);
+      }
+    }
+    }
+  }
+}
+
+// Bring each piece target to the raw form of store_final, once per run: from
+// the first piece slot of its run (the previous valid slot, one or two back,
+// holds another run or none).
+template <int DT, bool MM>
+__global__ void seg_piece_finish(const SegPiece* __restrict__ pieces, int64_t np, SegOut o) {
+  for (int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; p < np; p += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t run = pieces[p].run;
+    if (run == kNoRun) continue;
+    uint32_t prev = kNoRun;
+    if (p >= 1) prev = pieces[p - 1].run;
+    if (prev == kNoRun && p >= 2) prev = pieces[p - 2].run;
+    if (prev == run) continue;
+    if (DT == AGG_F32) {  // float64 total -> (s, c) float pair
+      const double d = __longlong_as_double((long long)o.sum[run]);
+      const float hi = (float)d;
+      const float lo = (float)(d - (double)hi);
+      o.sum[run] = ((unsigned long long)__float_as_uint(lo) << 32) | (unsigned long long)__float_as_uint(hi);
+    }
+    if (MM) o.min[run] = ~o.min[run];
+  }
+}
+
+// Every group: the output encodings and AVG = SUM / COUNT in float64.
 template <int DT, bool MM>
 __global__ void seg_finalize(SegOut o, int64_t d) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < d; i += (int64_t)gridDim.x * blockDim.x) {
     const unsigned long long c = o.count[i];
-    const unsigned long long s = o.sum[i];
-    double fs = (DT == AGG_F32 || DT == AGG_F64) ? __longlong_as_double((long long)s) : (double)(long long)s;
+    const double fs = fsum_of_raw<DT>(o.sum[i]);
+    if (DT == AGG_F32) o.sum[i] = (unsigned long long)__double_as_longlong(fs);
     o.avg[i] = fs / (double)c;
     if (MM) {
-      const uint64_t mn = ~o.minc[i], mx = o.mx[i];
-      double dmn, dmx;
-      if (DT == AGG_F32) {
-        dmn = (double)f32_of_img((uint32_t)mn);
-        dmx = (double)f32_of_img((uint32_t)mx);
-        o.minc[i] = (unsigned long long)__double_as_longlong(dmn);
-        o.mx[i] = (unsigned long long)__double_as_longlong(dmx);
-      } else if (DT == AGG_F64) {
-        o.minc[i] = (unsigned long long)__double_as_longlong(f64_of_img(mn));
-        o.mx[i] = (unsigned long long)__double_as_longlong(f64_of_img(mx));
-      } else {
-        o.minc[i] = (unsigned long long)i64_of_img(mn);
-        o.mx[i] = (unsigned long long)i64_of_img(mx);
-      }
+      o.min[i] = out_of_img<DT>(o.min[i]);
+      o.max[i] = out_of_img<DT>(o.max[i]);
     }
   }
 }
@@ -294,22 +473,26 @@ static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t
     *gout = g;
     return AGG_OK;
   }
-  const int64_t ntiles = (n + kSegTile - 1) / kSegTile;
+  const int64_t nchunks = (n + kSegChunk - 1) / kSegChunk;
+  const int64_t nblocks = (nchunks + kSegChunksPerBlock - 1) / kSegChunksPerBlock;
+  const int64_t np = 2 * nchunks;
   const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255);
   const size_t vb = ((size_t)n * sizeof(P) + 255) & ~size_t(255);
   const size_t rt = (radix_tmp_bytes(n) + 255) & ~size_t(255);
-  const size_t tc = ((size_t)(ntiles + 1) * 4 + 255) & ~size_t(255);
-  const size_t st_b = (scan_tmp_bytes(ntiles) + 255) & ~size_t(255);
+  const size_t tc = ((size_t)(nchunks + 1) * 4 + 255) & ~size_t(255);
+  const size_t st_b = (scan_tmp_bytes(nchunks) + 255) & ~size_t(255);
+  const size_t pb = ((size_t)np * sizeof(SegPiece) + 255) & ~size_t(255);
   void* tmp = nullptr;
-  AGG_CUDA_TRY(dev_malloc_async(&tmp, 2 * kb + 2 * vb + rt + tc + st_b + 256, s));
+  AGG_CUDA_TRY(dev_malloc_async(&tmp, 2 * kb + 2 * vb + rt + tc + st_b + pb + 256, s));
   char* c = (char*)tmp;
   uint32_t* kA = (uint32_t*)c; c += kb;
   uint32_t* kB = (uint32_t*)c; c += kb;
   P* vA = (P*)c; c += vb;
   P* vB = (P*)c; c += vb;
   void* rtmp = c; c += rt;
-  uint32_t* tile_counts = (uint32_t*)c; c += tc;
+  uint32_t* chunk_first = (uint32_t*)c; c += tc;
   void* stmp = c; c += st_b;
+  SegPiece* pieces = (SegPiece*)c; c += pb;
   uint32_t* total = (uint32_t*)c;
   auto release = [&]() { cudaFreeAsync(tmp, s); };
   uint32_t* sk = nullptr;
@@ -321,9 +504,9 @@ static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t
   }
   if (st != AGG_OK) { release(); return st; }
   PhaseTimer pt_seg(AGG_PHASE_SEGREDUCE, s);
-  seg_heads<<<(unsigned)ntiles, kSegThreads, 0, s>>>(sk, n, tile_counts);
+  seg_count<<<(unsigned)nblocks, kSegThreads, 0, s>>>(sk, n, chunk_first);
   note_launch();
-  st = scan_exclusive_u32(tile_counts, tile_counts, ntiles, total, stmp, s);
+  st = scan_exclusive_u32(chunk_first, chunk_first, nchunks, total, stmp, s);
   if (st != AGG_OK) { release(); return st; }
   uint32_t* hb = (uint32_t*)stream_pinned(s, 64, &st);
   if (!hb) { release(); return st; }
@@ -342,19 +525,22 @@ static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t
   o.keys = g->keys;
   o.count = (unsigned long long*)g->count;
   o.sum = (unsigned long long*)g->sum;
-  o.minc = (unsigned long long*)g->min;
-  o.mx = (unsigned long long*)g->max;
+  o.min = (unsigned long long*)g->min;
+  o.max = (unsigned long long*)g->max;
   o.avg = g->avg;
-  // count, sum, min, max are contiguous 256-aligned arrays of d 8-byte words: clear them
-  const size_t a8r = ((size_t)(d > 0 ? d : 1) * 8 + 255) & ~size_t(255);
-  cudaMemsetAsync(g->count, 0, 4 * a8r, s);
-  seg_reduce<DT, MM><<<(unsigned)ntiles, kSegThreads, 0, s>>>(sk, sv, n, tile_counts, o);
+  seg_reduce<DT, MM><<<(unsigned)nblocks, kSegThreads, 0, s>>>(sk, sv, n, chunk_first, o, pieces);
   const DeviceInfo& di = device_info();
+  int64_t pg = (np + 255) / 256;
+  if (pg > (int64_t)di.sm_count * 8) pg = (int64_t)di.sm_count * 8;
+  if (pg < 1) pg = 1;
+  seg_piece_clear<MM><<<(unsigned)pg, 256, 0, s>>>(pieces, np, o);
+  seg_piece_add<DT, MM><<<(unsigned)pg, 256, 0, s>>>(pieces, np, o);
+  seg_piece_finish<DT, MM><<<(unsigned)pg, 256, 0, s>>>(pieces, np, o);
   int64_t fg = (d + 255) / 256;
   if (fg > (int64_t)di.sm_count * 8) fg = (int64_t)di.sm_count * 8;
   if (fg < 1) fg = 1;
   seg_finalize<DT, MM><<<(unsigned)fg, 256, 0, s>>>(o, d);
-  note_launch(2);
+  note_launch(5);
   e = cudaGetLastError();
   release();
   cudaError_t e2 = cudaStreamSynchronize(s);
