@@ -75,13 +75,28 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
       if (hasnx[u]) nx[u] = keys[p + 1];
     }
   }
+  {  // key range and adjacent repeats: reduced per warp, one atomic each per warp
+    uint32_t lmin = 0xFFFFFFFFu, lmax = 0, ladj = 0;
+#pragma unroll
+    for (int u = 0; u < kPer; ++u) {
+      if (!have[u]) continue;
+      lmin = min(lmin, kk[u]);
+      lmax = max(lmax, kk[u]);
+      ladj += (hasnx[u] && nx[u] == kk[u]) ? 1u : 0u;
+    }
+    lmin = __reduce_min_sync(0xffffffffu, lmin);
+    lmax = __reduce_max_sync(0xffffffffu, lmax);
+    ladj = __reduce_add_sync(0xffffffffu, ladj);
+    if ((tid & 31) == 0) {
+      atomicMin(&s_kmin, lmin);
+      atomicMax(&s_kmax, lmax);
+      if (ladj) atomicAdd(&s_adj, ladj);
+    }
+  }
 #pragma unroll
   for (int u = 0; u < kPer; ++u) {
     if (!have[u]) continue;
     const uint32_t k = kk[u];
-    if (hasnx[u] && nx[u] == k) atomicAdd(&s_adj, 1u);
-    atomicMin(&s_kmin, k);
-    atomicMax(&s_kmax, k);
     const unsigned long long tag = ((unsigned long long)k << 1) | 1ull;
     uint32_t h = fmix32(k) & (kSketchSlots - 1);
     for (;;) {  // at most m < kSketchSlots occupied slots: an empty or matching one exists
@@ -95,16 +110,29 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
   __syncthreads();
   double ent = 0.0;
   const float mf = (float)(m > 0 ? m : 1);
-  for (int i = tid; i < kSketchSlots; i += kSketchThreads) {
-    const uint32_t c = cnt[i];
-    if (c == 0) continue;
-    atomicAdd(&s_d, 1u);
-    if (c == 1) atomicAdd(&s_f1, 1u);
-    if (c == 2) atomicAdd(&s_f2, 1u);
-    atomicAdd(&hist[c], 1u);
-    atomicMax(&s_maxc, c);
-    const float p = (float)c / mf;
-    ent -= (double)(p * logf(p));
+  {
+    uint32_t ld = 0, lf1 = 0, lf2 = 0, lmaxc = 0;
+    for (int i = tid; i < kSketchSlots; i += kSketchThreads) {  // same trip count in every thread
+      const uint32_t c = cnt[i];
+      if (c == 0) continue;
+      ld += 1;
+      lf1 += c == 1 ? 1u : 0u;
+      lf2 += c == 2 ? 1u : 0u;
+      lmaxc = max(lmaxc, c);
+      atomicAdd(&hist[c], 1u);
+      const float p = (float)c / mf;
+      ent -= (double)(p * logf(p));
+    }
+    ld = __reduce_add_sync(0xffffffffu, ld);
+    lf1 = __reduce_add_sync(0xffffffffu, lf1);
+    lf2 = __reduce_add_sync(0xffffffffu, lf2);
+    lmaxc = __reduce_max_sync(0xffffffffu, lmaxc);
+    if ((tid & 31) == 0) {
+      atomicAdd(&s_d, ld);
+      atomicAdd(&s_f1, lf1);
+      atomicAdd(&s_f2, lf2);
+      atomicMax(&s_maxc, lmaxc);
+    }
   }
   ent = block_sum_d(ent, red);
   const int R = (int)(s_d < 32 ? s_d : 32);
