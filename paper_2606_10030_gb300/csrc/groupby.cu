@@ -153,17 +153,24 @@ int64_t table_slots_from_sketch(const float* f, int64_t n) {
 }
 
 // The AUTO rule:
-//  - few distinct keys (a shared table holds them) or strong skew: SMEM;
-//  - columns of 2^20 rows or more: SORT when the sample is flat and leaves the
-//    number of keys open (about m^2/4 or more), else SMEM on hash-partitioned
-//    rows (the partitioning is chosen with the plan);
-//  - smaller columns: one global table.
+//  - few distinct keys (a shared table holds them): SMEM;
+//  - columns of 2^20 rows or more: SMEM (on hash-partitioned rows when the
+//    keys overflow a shared table) when the sample covers at least 97% of the
+//    mass, or is flat with a reliable Chao1; otherwise SORT, which needs no
+//    estimate of the key count (a long tail of rare keys, or a flat column
+//    whose key count the sample leaves open);
+//  - smaller columns: SMEM under strong skew (the hot keys stay in shared
+//    memory), else one global table.
 int rule_strategy(const float* f, uint32_t ops) {
   const KeyEstimate e = key_estimate(f);
   const int cap = ops_minmax(ops) ? 1536 : 3072;  // 3/4 of the largest shared tables
-  if (e.plan <= cap || f[F_TOP8] >= 0.05f) return AGG_STRAT_SMEM;
-  if (f[F_LOG2N] >= 20.0f) return (!e.reliable && e.flat) ? AGG_STRAT_SORT : AGG_STRAT_SMEM;
-  return AGG_STRAT_GLOBAL;
+  if (e.plan <= cap) return AGG_STRAT_SMEM;
+  if (f[F_LOG2N] >= 20.0f) {
+    const double coverage = 1.0 - (double)f[F_F1];  // F_F1 = f1 / m
+    if (coverage >= 0.97 || (e.flat && e.reliable)) return AGG_STRAT_SMEM;
+    return AGG_STRAT_SORT;
+  }
+  return f[F_TOP8] >= 0.05f ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
 }
 
 agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_groups** out) {
@@ -231,8 +238,14 @@ class HashRun {
     AGG_CUDA_TRY(cudaMemsetAsync(mem_, 0, aux_off_, s_));
     status_ = (int*)((char*)mem_ + status_off_);
     counter_ = (unsigned long long*)((char*)mem_ + status_off_ + 64);
+    progress_ = (unsigned long long*)((char*)mem_ + status_off_ + 192);
     return AGG_OK;
   }
+
+  // After finish returned TABLE_FULL: rows the build went through, and rows
+  // that found no slot.
+  uint64_t rows_seen() const { return rows_seen_; }
+  uint64_t rows_failed() const { return rows_failed_; }
 
   // Enqueue the build over rows [0, n) of (keys, vals).
   agg_status build(const uint32_t* keys, const void* vals, int64_t n) {
@@ -255,6 +268,7 @@ class HashRun {
     a.smem_slots = use_smem ? plan_.smem_slots : 0;
     a.smem_cap = use_smem ? (plan_.smem_slots * 3) / 4 : 0;
     a.status = status_;
+    a.progress = progress_;
     if (plan_.partition && n >= kPartTileRows) return build_partitioned(a, use_smem);
     KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec);
     const size_t smem = use_smem ? stab_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;
@@ -419,6 +433,7 @@ class HashRun {
     }
     cudaError_t e1 = cudaMemcpyAsync(hb, counter_, 8, cudaMemcpyDeviceToHost, s_);
     cudaError_t e2 = cudaMemcpyAsync(hb + 1, status_, 4, cudaMemcpyDeviceToHost, s_);
+    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(hb + 2, progress_, 16, cudaMemcpyDeviceToHost, s_);
     cudaError_t e3 = cudaStreamSynchronize(s_);
     if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
       set_error("group-by read-back failed: %s",
@@ -427,6 +442,8 @@ class HashRun {
       return AGG_ERR_CUDA;
     }
     if (*(int*)(hb + 1) != 0) {
+      rows_seen_ = (uint64_t)hb[2];
+      rows_failed_ = (uint64_t)hb[3];
       agg_groups_free(g);
       set_error("global hash table of %lld slots is full", (long long)plan_.slots);
       return AGG_ERR_TABLE_FULL;
@@ -450,6 +467,8 @@ class HashRun {
   bool small_ = true;
   size_t status_off_ = 0, aux_off_ = 0;
   int* status_ = nullptr;
+  unsigned long long* progress_ = nullptr;
+  uint64_t rows_seen_ = 0, rows_failed_ = 0;
   unsigned long long* counter_ = nullptr;
 };
 
@@ -555,16 +574,37 @@ static bool needs_sketch(const agg_options& o) {
 }
 
 // Run the hash plan over a device column, regrowing the table on overflow.
+// Slots for the next table after a table of `slots` slots filled: the build
+// went through `seen` rows, of which `failed` found no slot, so those rows had
+// at most slots + failed distinct keys; that bound is scaled to all n rows and
+// doubled (load <= 1/2). At least 4x the old table, at most 2n (a table of 2n
+// slots holds any key set of n rows) and 2^31. Columns of up to 2^22 rows go
+// straight to 2n slots (at most 256 MB): a further retry would cost more.
+static int64_t regrow_slots(int64_t slots, int64_t n, uint64_t seen, uint64_t failed) {
+  const double nn = (double)std::max<int64_t>(n, 1);
+  double keys = (double)slots + (double)failed;
+  if (seen > 0 && (double)seen < nn) keys *= nn / (double)seen;
+  double want = std::max(4.0 * (double)slots, 2.0 * std::min(keys, nn));
+  if (n <= (int64_t(1) << 22)) want = std::max(want, 2.0 * nn);
+  const double cap = std::min(2.0 * nn, (double)(int64_t(1) << 31));
+  if (want > cap) want = std::max(cap, 4.0 * (double)slots);
+  const int64_t p = next_pow2((int64_t)std::ceil(want));
+  return std::min<int64_t>(p, int64_t(1) << 31);
+}
+
 static agg_status hash_device(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
                               HashPlan plan, cudaStream_t s, agg_groups** g) {
   int retries = 0;
   for (;;) {
     agg_status st;
+    uint64_t seen = 0, failed = 0;
     {
       HashRun run(vdt, ops, plan, s);
       st = run.init();
       if (st == AGG_OK) st = run.build(keys, vals, n);
       if (st == AGG_OK) st = run.finish(g);
+      seen = run.rows_seen();
+      failed = run.rows_failed();
     }
     if (st == AGG_OK) {
       (*g)->retries = retries;
@@ -573,7 +613,7 @@ static agg_status hash_device(const uint32_t* keys, const void* vals, int64_t n,
     if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
       return st;
     ++retries;
-    plan.slots = std::min<int64_t>(plan.slots * 4, int64_t(1) << 31);
+    plan.slots = regrow_slots(plan.slots, n, seen, failed);
   }
 }
 
@@ -800,6 +840,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     HashPlan plan = c.plan;
     int retries = 0;
     for (;;) {
+      uint64_t seen = 0, failed = 0;
       {
         HashRun run(vdt, ops, plan, s);
         st = run.init();
@@ -813,6 +854,8 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
           cudaEventRecord(pipe->freed[b], s);
         }
         if (st == AGG_OK) st = run.finish(&g);
+        seen = run.rows_seen();  // rough: chunks enqueued after the table filled count too
+        failed = run.rows_failed();
       }
       if (st == AGG_OK) {
         g->retries = retries;
@@ -821,7 +864,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
       if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
         return st;
       ++retries;
-      plan.slots = std::min<int64_t>(plan.slots * 4, int64_t(1) << 31);
+      plan.slots = regrow_slots(plan.slots, n, seen, failed);
       next_copy = 0;  // copy the column again
       fresh_ring = false;
     }

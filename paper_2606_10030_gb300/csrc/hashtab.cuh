@@ -78,6 +78,7 @@ struct BuildArgs {
   int smem_slots;      // S (power of two) for SMEM, else 0
   int smem_cap;        // max keys inserted into the shared table
   int* status;
+  unsigned long long* progress;  // rows folded before a full table stopped the build (or null)
 };
 
 // Global slot of key (insert if absent); -1 if no slot within the probe bound.
@@ -292,26 +293,29 @@ __device__ __forceinline__ void g_add_row_cached(GSlot<MM>& s, typename GV<DT>::
 }
 
 template <int DT, bool MM>
-__device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
+__device__ __forceinline__ bool g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
   const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
   if (g < 0) {
     *(volatile int*)a.status = kStatusFull;
-    return;
+    return false;
   }
   g_add_row_cached<DT, MM>(tab[g], v);
+  return true;
 }
 
-// Fold a batch of N rows (valid[r] false = skip).
+// Fold a batch of N rows (valid[r] false = skip); rows that found no global
+// slot (a full table) are counted in fails.
 template <int DT, bool MM, bool SMEM, int N>
 __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
-                                           const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
+                                           const typename GV<DT>::T (&val)[N], const bool (&valid)[N],
+                                           uint32_t& fails) {
   using T = typename GV<DT>::T;
   using U = typename SImg<DT>::U;
   if (!SMEM) {
 #pragma unroll
     for (int r = 0; r < N; ++r)
-      if (valid[r]) g_row<DT, MM>(a, key[r], val[r]);
+      if (valid[r] && !g_row<DT, MM>(a, key[r], val[r])) ++fails;
     return;
   }
   int j[N];
@@ -382,7 +386,7 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
   }
 #pragma unroll
   for (int r = 0; r < N; ++r)
-    if (j[r] == -1) g_row<DT, MM>(a, key[r], val[r]);
+    if (j[r] == -1 && !g_row<DT, MM>(a, key[r], val[r])) ++fails;
 }
 
 // ---------------------------------------------------------------------------
@@ -485,12 +489,12 @@ __device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, con
 }
 
 template <int DT, bool MM>
-__device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, const Partial4<DT>& p) {
+__device__ __forceinline__ bool g_add_partial(const BuildArgs& a, uint32_t key, const Partial4<DT>& p) {
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
   const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
   if (g < 0) {
     *(volatile int*)a.status = kStatusFull;
-    return;
+    return false;
   }
   GSlot<MM>& gs = tab[g];
   atomicAdd(&gs.cnt, p.cnt);
@@ -503,13 +507,15 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
     if (~mn > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~mn);
     if (mx > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)mx);
   }
+  return true;
 }
 
 // The warp reduces the rows marked in take (all of one key) and lane 0 folds
-// the partial into the tables.
+// the partial into the tables (rows it could not place are added to fails).
 template <int DT, bool MM, bool SMEM>
 __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
-                                              const typename GV<DT>::T (&v)[4], const bool (&take)[4]) {
+                                              const typename GV<DT>::T (&v)[4], const bool (&take)[4],
+                                              uint32_t& fails) {
   Partial4<DT> p = partial_of<DT, MM>(v, take);
   warp_reduce_partial<DT, MM>(p);
   if ((threadIdx.x & 31) != 0) return;
@@ -521,7 +527,7 @@ __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT,
       return;
     }
   }
-  g_add_partial<DT, MM>(a, key, p);
+  if (!g_add_partial<DT, MM>(a, key, p)) fails += p.cnt;
 }
 
 template <class T>
@@ -541,6 +547,23 @@ __device__ __forceinline__ void unpack4(const uint4& lo, const uint4& hi, T* v) 
   }
 }
 
+// After a build stopped on a full table: add the rows this warp went through
+// and the rows it could not place to a.progress[0] and [1] (one atomic each
+// per warp); the host sizes the next table from them. Every lane of the warp
+// calls this; the status is read once per warp.
+__device__ __forceinline__ void note_progress(const BuildArgs& a, uint32_t rows, uint32_t fails) {
+  if (a.progress == nullptr) return;
+  const int lane = threadIdx.x & 31;
+  const int full = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)a.status : 0, 0);
+  if (!full) return;
+  const uint32_t wr = __reduce_add_sync(0xffffffffu, rows);
+  const uint32_t wf = __reduce_add_sync(0xffffffffu, fails);
+  if (lane == 0) {
+    atomicAdd(&a.progress[0], (unsigned long long)wr);
+    atomicAdd(&a.progress[1], (unsigned long long)wf);
+  }
+}
+
 // Rows [0, a.n) of a column folded by threads tid, tid + nthreads, ...
 // VEC: 16-byte vector loads of 4 keys and 4 values per quad, kQuadsPerIter
 // quads per thread per iteration (all loads issued before any row is folded).
@@ -551,7 +574,7 @@ constexpr int kQuadsPerIter = AGG_QUADS_PER_ITER;
 
 template <int DT, bool MM, bool SMEM, bool VEC>
 __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
-                                           int64_t nthreads) {
+                                           int64_t nthreads, uint32_t& rows_seen, uint32_t& fails) {
   using T = typename GV<DT>::T;
   const uint32_t* keys = a.keys;
   const T* vals = (const T*)a.vals;
@@ -565,11 +588,11 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
       ok1[0] = tid < a.head;
       k1[0] = ok1[0] ? keys[tid] : 0u;
       v1[0] = ok1[0] ? vals[tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1, fails);
       ok1[0] = tid < a.n - tail0;
       k1[0] = ok1[0] ? keys[tail0 + tid] : 0u;
       v1[0] = ok1[0] ? vals[tail0 + tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1, fails);
     }
     const uint4* kq = (const uint4*)(keys + a.head);
     const uint4* vq = (const uint4*)(vals + a.head);
@@ -604,7 +627,7 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
           }
           const unsigned tot = __reduce_add_sync(0xffffffffu, nm);
           if (tot >= (unsigned)kDominantRows) {
-            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, taken);
+            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, taken, fails);
             if (tot == 128u) continue;
           } else {
 #pragma unroll
@@ -616,26 +639,29 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
           bool ok[1] = {has[u] && !taken[r]};
-          fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok);
+          fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok, fails);
         }
       }
       if ((++it & 15) == 0 && *(volatile int*)a.status) break;  // table full: the build is redone
     }
+    rows_seen += (uint32_t)it * 4u * kQuadsPerIter;
   } else {
     int it = 0;
     for (int64_t i = tid; i < a.n; i += nthreads) {
       uint32_t k1[1] = {keys[i]};
       T v1[1] = {vals[i]};
       bool ok1[1] = {true};
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1, fails);
       if ((++it & 63) == 0 && *(volatile int*)a.status) break;
     }
+    rows_seen += (uint32_t)it;
   }
 }
 
-// Merge a block's shared table into the global table (after a barrier).
+// Merge a block's shared table into the global table (after a barrier); rows
+// of slots that found no global slot are added to fails.
 template <int DT, bool MM>
-__device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM>& st) {
+__device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM>& st, uint32_t& fails) {
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
   const int S = a.smem_slots;
   for (int j = threadIdx.x; j <= S; j += blockDim.x) {
@@ -645,6 +671,7 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
     if (g < 0) {
       *(volatile int*)a.status = kStatusFull;
+      fails += c;
       continue;
     }
     GSlot<MM>& gs = tab[g];
@@ -677,11 +704,14 @@ __global__ void gb_build(BuildArgs a) {
     st.clear(a.smem_slots);
     __syncthreads();
   }
+  uint32_t rows_seen = 0, fails = 0;
   build_rows<DT, MM, SMEM, VEC>(a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                (int64_t)gridDim.x * blockDim.x);
-  if (!SMEM) return;
-  __syncthreads();
-  flush_smem<DT, MM>(a, st);
+                                (int64_t)gridDim.x * blockDim.x, rows_seen, fails);
+  if (SMEM) {
+    __syncthreads();
+    flush_smem<DT, MM>(a, st, fails);
+  }
+  note_progress(a, rows_seen, fails);
 }
 
 // Tile-queue build for hash-partitioned input: blocks pull 64 Ki-row tiles in
@@ -697,12 +727,15 @@ __global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile, int64
   __shared__ int64_t s_t;
   STab<DT, MM> st;
   st.carve(smem, a.smem_slots);
+  uint32_t rows_seen = 0, fails = 0;
   for (;;) {
-    if (threadIdx.x == 0) s_t = (int64_t)atomicAdd(next_tile, 1ull);
+    // no new tile once the table is full (the build is redone with a larger one)
+    if (threadIdx.x == 0) s_t = *(volatile int*)a.status ? -1 : (int64_t)atomicAdd(next_tile, 1ull);
     __syncthreads();
-    const int64_t r0 = s_t * tile_rows;
+    const int64_t t = s_t;
+    const int64_t r0 = t * tile_rows;
     __syncthreads();
-    if (r0 >= a.n) return;
+    if (t < 0 || r0 >= a.n) break;
     BuildArgs b = a;
     b.keys = a.keys + r0;
     b.vals = (const T*)a.vals + r0;
@@ -710,11 +743,12 @@ __global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile, int64
     b.head = 0;
     st.clear(a.smem_slots);
     __syncthreads();
-    build_rows<DT, MM, true, VEC>(b, st, threadIdx.x, blockDim.x);
+    build_rows<DT, MM, true, VEC>(b, st, threadIdx.x, blockDim.x, rows_seen, fails);
     __syncthreads();
-    flush_smem<DT, MM>(b, st);
+    flush_smem<DT, MM>(b, st, fails);
     __syncthreads();
   }
+  note_progress(a, rows_seen, fails);
 }
 
 // ---------------------------------------------------------------------------

@@ -125,6 +125,12 @@ def test_rule_strategy_is_a_host_call(L):
     # flat with repeats (about 65536 keys, f2 well above 2): partitioned shared-memory build
     f[0], f[4], f[5], f[6], f[8], f[12] = 28, 3970 / 4096, 3846 / 4096, 124 / 4096, 17 / 4096, 20
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
-    # strongly skewed: shared-memory tables keep the hot keys
+    # strongly skewed with a long tail the sample does not cover: the sort needs no key count
     f[8] = 0.2
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SORT
+    # ... on a small column: shared-memory tables keep the hot keys
+    f[0] = 16
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
+    # a sample covering 98 % of the mass of a large column: shared-memory tables
+    f[0], f[4], f[5], f[6], f[8] = 28, 2000 / 4096, 80 / 4096, 200 / 4096, 0.01
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM

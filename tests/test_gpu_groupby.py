@@ -141,10 +141,22 @@ def test_strategies_return_identical_results(dt):
 def test_table_regrows_when_undersized():
     keys, vals = make_case("uniform50k", "i64", seed=5)
     res, meta = run(keys, vals, agg.AGG_STRAT_GLOBAL, table_slots=1024)
-    assert meta[1] >= 1 and meta[2] >= 65536
+    assert meta[1] == 1 and meta[2] >= 65536  # a column this small regrows once, to 2n slots
     check_groups(res, keys, vals)
     res, meta = run(keys, vals, agg.AGG_STRAT_SMEM, table_slots=2048, smem_slots=256)
     assert meta[1] >= 1
+    check_groups(res, keys, vals)
+
+
+@pytest.mark.parametrize("strategy", [agg.AGG_STRAT_SMEM, agg.AGG_STRAT_GLOBAL])
+def test_large_table_regrows_from_the_folded_fraction(strategy):
+    """2^24 rows over about 2^22 keys into a 2^16-slot table: the first build stops when the table
+    fills, and the next table is sized from the fraction of rows folded by then."""
+    n = 1 << 24
+    keys = dg.keys_uniform(n, 1 << 22, 7)
+    vals = dg.values("i64", n, 7)
+    res, meta = run(keys, vals, strategy, table_slots=1 << 16)
+    assert 1 <= meta[1] <= 2
     check_groups(res, keys, vals)
 
 
