@@ -65,19 +65,19 @@ __device__ void batch_tile(const BQ& q, int64_t r0, int64_t r1, unsigned char* s
   a.smem_slots = SMEM ? q.smem_slots : 0;
   a.smem_cap = SMEM ? q.smem_cap : 0;
   a.status = q.status;
-  a.progress = nullptr;
+  a.progress = nullptr;  // the plan regrows a full table 4x
+  a.block_fails = nullptr;
   STab<DT, MM> st;
   if (SMEM) {
     st.carve(smem, a.smem_slots);
     st.clear(a.smem_slots);
     __syncthreads();
   }
-  uint32_t rows_seen = 0, fails = 0;  // unused: the plan regrows a full table 4x
-  if (q.vec) build_rows<DT, MM, SMEM, true>(a, st, threadIdx.x, blockDim.x, rows_seen, fails);
-  else build_rows<DT, MM, SMEM, false>(a, st, threadIdx.x, blockDim.x, rows_seen, fails);
+  if (q.vec) build_rows<DT, MM, SMEM, true>(a, st, threadIdx.x, blockDim.x);
+  else build_rows<DT, MM, SMEM, false>(a, st, threadIdx.x, blockDim.x);
   if (SMEM) {
     __syncthreads();
-    flush_smem<DT, MM>(a, st, fails);
+    flush_smem<DT, MM>(a, st);
   }
 }
 

@@ -340,7 +340,10 @@ class HashRun {
         int bps = occupancy(bk, threads, smem);
         if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
         int64_t grid = (int64_t)di.sm_count * bps;
+        // tiles of up to 64 Ki rows (32 Ki after two levels), smaller (down to
+        // 4 Ki) when the column would give each resident block fewer than two
         int64_t tile_rows = plan_.partition_passes == 2 ? kPartTileRows / 2 : kPartTileRows;
+        while (tile_rows > 4096 && n < 2 * grid * tile_rows) tile_rows >>= 1;
         const int64_t tiles = (n + tile_rows - 1) / tile_rows;
         if (tiles < grid) grid = tiles;
         void* args[] = {&a, &next_tile, &tile_rows};

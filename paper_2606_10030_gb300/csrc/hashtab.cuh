@@ -78,7 +78,9 @@ struct BuildArgs {
   int smem_slots;      // S (power of two) for SMEM, else 0
   int smem_cap;        // max keys inserted into the shared table
   int* status;
-  unsigned long long* progress;  // rows folded before a full table stopped the build (or null)
+  unsigned long long* progress;  // [0] rows gone through, [1] rows that found no slot, counted
+                                 // when a full table stopped the build (or null)
+  uint32_t* block_fails;         // this block's count of rows that found no slot (shared memory, or null)
 };
 
 // Global slot of key (insert if absent); -1 if no slot within the probe bound.
@@ -86,12 +88,13 @@ struct BuildArgs {
 // shares its top bits (one partition of a hash-partitioned input) live in one
 // contiguous region of the table.
 template <bool MM>
-__device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, int shift, uint32_t key) {
+__device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, int shift, uint32_t key,
+                                          int max_probe = kGlobalProbe) {
   if (key == 0xFFFFFFFFu) return (int64_t)mask + 1;
   const uint32_t k1 = key + 1;
   uint32_t h = fmix32(key) >> shift;
 #pragma unroll 1
-  for (int p = 0; p < kGlobalProbe; ++p) {
+  for (int p = 0; p < max_probe; ++p) {
     uint32_t cur = *(volatile uint32_t*)&tab[h].key1;
     if (cur == k1) return h;
     if (cur == 0) {
@@ -292,30 +295,39 @@ __device__ __forceinline__ void g_add_row_cached(GSlot<MM>& s, typename GV<DT>::
   }
 }
 
-template <int DT, bool MM>
-__device__ __forceinline__ bool g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
-  GSlot<MM>* tab = (GSlot<MM>*)a.table;
-  const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
-  if (g < 0) {
-    *(volatile int*)a.status = kStatusFull;
-    return false;
-  }
-  g_add_row_cached<DT, MM>(tab[g], v);
-  return true;
+// Count rows that found no global slot in the block's shared counter.
+__device__ __forceinline__ void note_fail(const BuildArgs& a, uint32_t rows) {
+  *(volatile int*)a.status = kStatusFull;
+  if (a.block_fails) atomicAdd(a.block_fails, rows);
 }
 
-// Fold a batch of N rows (valid[r] false = skip); rows that found no global
-// slot (a full table) are counted in fails.
+// Fold a row into the global table. Once a row of this block found the table
+// full, rows probe only kShortProbe slots: the build is redone, and the rows
+// folded before the block notices should not each walk the whole probe bound.
+constexpr int kShortProbe = 8;
+
+template <int DT, bool MM>
+__device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename GV<DT>::T v) {
+  GSlot<MM>* tab = (GSlot<MM>*)a.table;
+  const bool met_full = a.block_fails && *(volatile uint32_t*)a.block_fails != 0;
+  const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key, met_full ? kShortProbe : kGlobalProbe);
+  if (g < 0) {
+    note_fail(a, 1);
+    return;
+  }
+  g_add_row_cached<DT, MM>(tab[g], v);
+}
+
+// Fold a batch of N rows (valid[r] false = skip).
 template <int DT, bool MM, bool SMEM, int N>
 __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
-                                           const typename GV<DT>::T (&val)[N], const bool (&valid)[N],
-                                           uint32_t& fails) {
+                                           const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
   using T = typename GV<DT>::T;
   using U = typename SImg<DT>::U;
   if (!SMEM) {
 #pragma unroll
     for (int r = 0; r < N; ++r)
-      if (valid[r] && !g_row<DT, MM>(a, key[r], val[r])) ++fails;
+      if (valid[r]) g_row<DT, MM>(a, key[r], val[r]);
     return;
   }
   int j[N];
@@ -386,7 +398,7 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
   }
 #pragma unroll
   for (int r = 0; r < N; ++r)
-    if (j[r] == -1 && !g_row<DT, MM>(a, key[r], val[r])) ++fails;
+    if (j[r] == -1) g_row<DT, MM>(a, key[r], val[r]);
 }
 
 // ---------------------------------------------------------------------------
@@ -489,12 +501,12 @@ __device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, con
 }
 
 template <int DT, bool MM>
-__device__ __forceinline__ bool g_add_partial(const BuildArgs& a, uint32_t key, const Partial4<DT>& p) {
+__device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, const Partial4<DT>& p) {
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
   const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
   if (g < 0) {
-    *(volatile int*)a.status = kStatusFull;
-    return false;
+    note_fail(a, p.cnt);
+    return;
   }
   GSlot<MM>& gs = tab[g];
   atomicAdd(&gs.cnt, p.cnt);
@@ -507,15 +519,13 @@ __device__ __forceinline__ bool g_add_partial(const BuildArgs& a, uint32_t key, 
     if (~mn > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~mn);
     if (mx > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)mx);
   }
-  return true;
 }
 
 // The warp reduces the rows marked in take (all of one key) and lane 0 folds
-// the partial into the tables (rows it could not place are added to fails).
+// the partial into the tables.
 template <int DT, bool MM, bool SMEM>
 __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
-                                              const typename GV<DT>::T (&v)[4], const bool (&take)[4],
-                                              uint32_t& fails) {
+                                              const typename GV<DT>::T (&v)[4], const bool (&take)[4]) {
   Partial4<DT> p = partial_of<DT, MM>(v, take);
   warp_reduce_partial<DT, MM>(p);
   if ((threadIdx.x & 31) != 0) return;
@@ -527,7 +537,7 @@ __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT,
       return;
     }
   }
-  if (!g_add_partial<DT, MM>(a, key, p)) fails += p.cnt;
+  g_add_partial<DT, MM>(a, key, p);
 }
 
 template <class T>
@@ -547,21 +557,18 @@ __device__ __forceinline__ void unpack4(const uint4& lo, const uint4& hi, T* v) 
   }
 }
 
-// After a build stopped on a full table: add the rows this warp went through
-// and the rows it could not place to a.progress[0] and [1] (one atomic each
-// per warp); the host sizes the next table from them. Every lane of the warp
-// calls this; the status is read once per warp.
-__device__ __forceinline__ void note_progress(const BuildArgs& a, uint32_t rows, uint32_t fails) {
-  if (a.progress == nullptr) return;
-  const int lane = threadIdx.x & 31;
-  const int full = __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)a.status : 0, 0);
-  if (!full) return;
-  const uint32_t wr = __reduce_add_sync(0xffffffffu, rows);
-  const uint32_t wf = __reduce_add_sync(0xffffffffu, fails);
-  if (lane == 0) {
-    atomicAdd(&a.progress[0], (unsigned long long)wr);
-    atomicAdd(&a.progress[1], (unsigned long long)wf);
-  }
+// Per-block counts reported after a build: when a full table stopped it, the
+// rows the block went through and those that found no slot are added to
+// a.progress, from which the host sizes the next table. Call after a barrier
+// that follows every thread's count_seen.
+struct BlockCounts {
+  uint32_t seen, fails;
+};
+
+__device__ __forceinline__ void report_counts(const BuildArgs& a, const BlockCounts& c) {
+  if (threadIdx.x != 0 || a.progress == nullptr || *(volatile int*)a.status == 0) return;
+  atomicAdd(&a.progress[0], (unsigned long long)c.seen);
+  atomicAdd(&a.progress[1], (unsigned long long)c.fails);
 }
 
 // Rows [0, a.n) of a column folded by threads tid, tid + nthreads, ...
@@ -572,9 +579,10 @@ __device__ __forceinline__ void note_progress(const BuildArgs& a, uint32_t rows,
 #endif
 constexpr int kQuadsPerIter = AGG_QUADS_PER_ITER;
 
+// Returns the number of rows this thread went through (the vector body's).
 template <int DT, bool MM, bool SMEM, bool VEC>
-__device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
-                                           int64_t nthreads, uint32_t& rows_seen, uint32_t& fails) {
+__device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
+                                               int64_t nthreads) {
   using T = typename GV<DT>::T;
   const uint32_t* keys = a.keys;
   const T* vals = (const T*)a.vals;
@@ -588,11 +596,11 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
       ok1[0] = tid < a.head;
       k1[0] = ok1[0] ? keys[tid] : 0u;
       v1[0] = ok1[0] ? vals[tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1, fails);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
       ok1[0] = tid < a.n - tail0;
       k1[0] = ok1[0] ? keys[tail0 + tid] : 0u;
       v1[0] = ok1[0] ? vals[tail0 + tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1, fails);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
     }
     const uint4* kq = (const uint4*)(keys + a.head);
     const uint4* vq = (const uint4*)(vals + a.head);
@@ -627,7 +635,7 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
           }
           const unsigned tot = __reduce_add_sync(0xffffffffu, nm);
           if (tot >= (unsigned)kDominantRows) {
-            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, taken, fails);
+            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, taken);
             if (tot == 128u) continue;
           } else {
 #pragma unroll
@@ -639,29 +647,28 @@ __device__ __forceinline__ void build_rows(const BuildArgs& a, const STab<DT, MM
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
           bool ok[1] = {has[u] && !taken[r]};
-          fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok, fails);
+          fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok);
         }
       }
       if ((++it & 15) == 0 && *(volatile int*)a.status) break;  // table full: the build is redone
     }
-    rows_seen += (uint32_t)it * 4u * kQuadsPerIter;
+    return (uint32_t)it * 4u * kQuadsPerIter;
   } else {
     int it = 0;
     for (int64_t i = tid; i < a.n; i += nthreads) {
       uint32_t k1[1] = {keys[i]};
       T v1[1] = {vals[i]};
       bool ok1[1] = {true};
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1, fails);
+      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
       if ((++it & 63) == 0 && *(volatile int*)a.status) break;
     }
-    rows_seen += (uint32_t)it;
+    return (uint32_t)it;
   }
 }
 
-// Merge a block's shared table into the global table (after a barrier); rows
-// of slots that found no global slot are added to fails.
+// Merge a block's shared table into the global table (after a barrier).
 template <int DT, bool MM>
-__device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM>& st, uint32_t& fails) {
+__device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM>& st) {
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
   const int S = a.smem_slots;
   for (int j = threadIdx.x; j <= S; j += blockDim.x) {
@@ -670,8 +677,7 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     const uint32_t key = j == S ? 0xFFFFFFFFu : st.key1[j] - 1;
     const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
     if (g < 0) {
-      *(volatile int*)a.status = kStatusFull;
-      fails += c;
+      note_fail(a, c);
       continue;
     }
     GSlot<MM>& gs = tab[g];
@@ -698,20 +704,24 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
 template <int DT, bool MM, bool SMEM, bool VEC>
 __global__ void gb_build(BuildArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ BlockCounts s_cnt;
+  if (threadIdx.x == 0) s_cnt = BlockCounts{0u, 0u};
+  a.block_fails = &s_cnt.fails;
   STab<DT, MM> st;
   if (SMEM) {
     st.carve(smem, a.smem_slots);
     st.clear(a.smem_slots);
-    __syncthreads();
   }
-  uint32_t rows_seen = 0, fails = 0;
-  build_rows<DT, MM, SMEM, VEC>(a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                (int64_t)gridDim.x * blockDim.x, rows_seen, fails);
+  __syncthreads();
+  const uint32_t seen = build_rows<DT, MM, SMEM, VEC>(a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
+                                                      (int64_t)gridDim.x * blockDim.x);
+  atomicAdd(&s_cnt.seen, seen);
   if (SMEM) {
     __syncthreads();
-    flush_smem<DT, MM>(a, st, fails);
+    flush_smem<DT, MM>(a, st);
   }
-  note_progress(a, rows_seen, fails);
+  __syncthreads();
+  report_counts(a, s_cnt);
 }
 
 // Tile-queue build for hash-partitioned input: blocks pull 64 Ki-row tiles in
@@ -725,9 +735,11 @@ __global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile, int64
   using T = typename GV<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_t;
+  __shared__ BlockCounts s_cnt;
+  if (threadIdx.x == 0) s_cnt = BlockCounts{0u, 0u};
+  a.block_fails = &s_cnt.fails;
   STab<DT, MM> st;
   st.carve(smem, a.smem_slots);
-  uint32_t rows_seen = 0, fails = 0;
   for (;;) {
     // no new tile once the table is full (the build is redone with a larger one)
     if (threadIdx.x == 0) s_t = *(volatile int*)a.status ? -1 : (int64_t)atomicAdd(next_tile, 1ull);
@@ -743,12 +755,12 @@ __global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile, int64
     b.head = 0;
     st.clear(a.smem_slots);
     __syncthreads();
-    build_rows<DT, MM, true, VEC>(b, st, threadIdx.x, blockDim.x, rows_seen, fails);
+    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC>(b, st, threadIdx.x, blockDim.x));
     __syncthreads();
-    flush_smem<DT, MM>(b, st, fails);
+    flush_smem<DT, MM>(b, st);
     __syncthreads();
   }
-  note_progress(a, rows_seen, fails);
+  report_counts(a, s_cnt);
 }
 
 // ---------------------------------------------------------------------------
