@@ -392,8 +392,8 @@ class HashRun {
       uint32_t* ck = (uint32_t*)aux;
       uint32_t* cs = ck + nslots_;
       const int cgrid = (int)((nslots_ + 255) / 256);
-      if (mm_) gb_compact<true><<<cgrid, 256, 0, s_>>>((const GSlot<true>*)mem_, mask, ck, cs, counter_);
-      else gb_compact<false><<<cgrid, 256, 0, s_>>>((const GSlot<false>*)mem_, mask, ck, cs, counter_);
+      if (mm_) gb_compact<true, 1><<<cgrid, 256, 0, s_>>>((const GSlot<true>*)mem_, mask, ck, cs, counter_);
+      else gb_compact<false, 1><<<cgrid, 256, 0, s_>>>((const GSlot<false>*)mem_, mask, ck, cs, counter_);
       note_launch();
       const int rgrid = (int)((nslots_ + kRankThreads - 1) / kRankThreads);
       void* args[] = {&mem_, &ck, &cs, &o};

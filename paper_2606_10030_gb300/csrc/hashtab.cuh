@@ -837,9 +837,9 @@ __global__ void __launch_bounds__(kRankThreads) gb_rank_gather(const GSlot<MM>* 
 }
 
 // Large tables: compact occupied slots into (key, slot) pairs.
-constexpr int kCompactPer = 8;  // slots per thread per run of the compaction
-
-template <bool MM>
+// PER slots per thread per run of the compaction (1 for small tables, whose
+// few slots are best spread over all threads; 8 for large ones).
+template <bool MM, int kCompactPer = 8>
 __global__ void gb_compact(const GSlot<MM>* tab, uint32_t mask, uint32_t* okeys, uint32_t* oslot,
                            unsigned long long* counter) {
   // each block takes runs of kCompactPer * blockDim.x slots and reserves its

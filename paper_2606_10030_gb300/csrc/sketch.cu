@@ -13,7 +13,9 @@ constexpr int kSketchThreads = 1024;
 constexpr int kSketchSlots = 2 * kSketchSample;  // hash slots for the sample (load <= 1/2)
 constexpr size_t kSketchSmem = (size_t)kSketchSlots * 8 + (size_t)kSketchSlots * 4 + (kSketchSample + 1) * 4 + 64 * 4;
 
-// Block-wide sum in a fixed order (deterministic).
+// Block-wide sum in a fixed order (deterministic). One thread adds the warp
+// sums: GB300's float64 pipe is narrow, so the block does not repeat that
+// serial chain in every thread.
 __device__ double block_sum_d(double v, double* red) {
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -21,8 +23,13 @@ __device__ double block_sum_d(double v, double* red) {
   __syncthreads();
   if (l == 0) red[w] = v;
   __syncthreads();
-  double t = 0;
-  for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+  if (threadIdx.x == 0) {
+    double t = 0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    red[32] = t;
+  }
+  __syncthreads();
+  const double t = red[32];
   __syncthreads();
   return t;
 }
@@ -39,7 +46,7 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
   uint32_t* cnt = (uint32_t*)(slot + kSketchSlots);              // kSketchSlots
   uint32_t* hist = cnt + kSketchSlots;                           // kSketchSample + 1
   uint32_t* top = hist + kSketchSample + 1;                      // 32 (+ pad)
-  __shared__ double red[32];
+  __shared__ double red[33];
   __shared__ unsigned int s_d, s_f1, s_f2, s_adj, s_kmin, s_kmax, s_maxc, s_ntop;
   const int tid = threadIdx.x;
   for (int i = tid; i < kSketchSlots; i += kSketchThreads) {
@@ -108,7 +115,7 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
     atomicAdd(&cnt[h], 1u);
   }
   __syncthreads();
-  double ent = 0.0;
+  float ent_t = 0.f;  // this thread's few entropy terms; the block sum is float64
   const float mf = (float)(m > 0 ? m : 1);
   {
     uint32_t ld = 0, lf1 = 0, lf2 = 0, lmaxc = 0;
@@ -121,7 +128,7 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
       lmaxc = max(lmaxc, c);
       atomicAdd(&hist[c], 1u);
       const float p = (float)c / mf;
-      ent -= (double)(p * logf(p));
+      ent_t -= p * logf(p);
     }
     ld = __reduce_add_sync(0xffffffffu, ld);
     lf1 = __reduce_add_sync(0xffffffffu, lf1);
@@ -134,7 +141,7 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
       atomicMax(&s_maxc, lmaxc);
     }
   }
-  ent = block_sum_d(ent, red);
+  const double ent = block_sum_d((double)ent_t, red);
   const int R = (int)(s_d < 32 ? s_d : 32);
   if (tid < 32) {  // warp 0: the R largest counts, in descending order
     const int lane = tid;
@@ -154,11 +161,30 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
     }
   }
   __syncthreads();
+  // Least-squares slope of log(count) on log(rank) over the R largest counts:
+  // lane r - 1 of warp 0 takes rank r, and the sums are warp reductions in a
+  // fixed order (float64, few serial steps).
+  __shared__ double s_slope;
+  if (tid < 32) {
+    const int r = tid + 1;
+    const bool in = r <= R;
+    const double x = in ? (double)logf((float)r) : 0.0, y = in ? (double)logf((float)top[r - 1]) : 0.0;
+    double sx = x, sy = y, sxx = x * x, sxy = x * y;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+      sx += __shfl_xor_sync(0xffffffffu, sx, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+      sxx += __shfl_xor_sync(0xffffffffu, sxx, o);
+      sxy += __shfl_xor_sync(0xffffffffu, sxy, o);
+    }
+    if (tid == 0) s_slope = R >= 2 ? (R * sxy - sx * sy) / (R * sxx - sx * sx) : 0.0;
+  }
+  __syncthreads();
   if (tid != 0) return;
   const double md = m > 0 ? (double)m : 1.0;
   const double d = (double)s_d, f1 = (double)s_f1, f2 = (double)s_f2;
   float* f = feat;
-  f[F_LOG2N] = n > 0 ? (float)log2((double)n) : 0.f;
+  f[F_LOG2N] = n > 0 ? log2f((float)n) : 0.f;
   f[F_VBYTES] = (float)vbytes;
   f[F_NOPS] = (float)nops;
   f[F_FP] = (float)fp;
@@ -173,26 +199,19 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
   double top8 = 0;
   for (int r = 0; r < 8 && r < R; ++r) top8 += (double)top[r];
   f[F_TOP8] = (float)(top8 / md);
-  double slope = 0.0;
-  if (R >= 2) {
-    double sx = 0, sy = 0, sxx = 0, sxy = 0;
-    for (int r = 1; r <= R; ++r) {
-      const double x = (double)logf((float)r), y = (double)logf((float)top[r - 1]);
-      sx += x; sy += y; sxx += x * x; sxy += x * y;
-    }
-    slope = (R * sxy - sx * sy) / (R * sxx - sx * sx);
-  }
-  f[F_SLOPE] = (float)slope;
+  f[F_SLOPE] = (float)s_slope;
   f[F_ENTROPY] = m > 1 ? (float)(ent / (double)logf(mf)) : 0.f;
   f[F_ADJ_EQ] = (float)((double)s_adj / md);
-  double gee = sqrt((double)n / md) * f1 + (d - f1);
-  if (gee < 1.0) gee = 1.0;
-  if (gee > (double)n) gee = (double)n;
-  f[F_LOG2_GEE] = (float)log2(gee);
-  const double tbytes = 2.0 * gee * (double)slot_bytes;
-  f[F_SMEM_RATIO] = (float)log2(1.0 + tbytes / smem_bytes);
-  f[F_L2_RATIO] = (float)log2(1.0 + tbytes / l2_bytes);
-  f[F_LOG2_RANGE] = (float)log2((double)(s_kmax - s_kmin) + 1.0);
+  // float32 from here on: the features are float32, and float64 library
+  // calls on one thread are slow on GB300's narrow float64 pipe
+  float gee = sqrtf((float)n / (float)md) * (float)f1 + (float)(d - f1);
+  if (gee < 1.f) gee = 1.f;
+  if (gee > (float)n) gee = (float)n;
+  f[F_LOG2_GEE] = log2f(gee);
+  const float tbytes = 2.f * gee * (float)slot_bytes;
+  f[F_SMEM_RATIO] = log2f(1.f + tbytes / (float)smem_bytes);
+  f[F_L2_RATIO] = log2f(1.f + tbytes / (float)l2_bytes);
+  f[F_LOG2_RANGE] = log2f((float)(s_kmax - s_kmin) + 1.f);
 }
 
 __global__ void __launch_bounds__(kSketchThreads) sketch_kernel(const uint32_t* __restrict__ keys, int64_t n,
