@@ -475,8 +475,10 @@ class HashRun {
   unsigned long long* counter_ = nullptr;
 };
 
+// Sort-based GROUP BY; feat (nullable) is the column's sketch, whose sampled
+// key range can spare the exact range pass.
 agg_status sort_groupby(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops, cudaStream_t s,
-                        agg_groups** gout);
+                        agg_groups** gout, const float* feat);
 
 static int smem_slots_for(double est, bool mm) {
   const int maxs = mm ? 2048 : 4096;
@@ -649,7 +651,7 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
       st = choose(keys, vals, n, vdt, ops, o2, feat, have, s, &c);
       if (st != AGG_OK) return st;
       agg_groups* g = nullptr;
-      if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g);
+      if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g, feat);
       else st = hash_device(keys, vals, n, vdt, ops, c.plan, s, &g);
       if (st != AGG_OK) return st;
       std::memcpy(g->features, feat, sizeof(feat));
@@ -664,7 +666,7 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
   st = choose(keys, vals, n, vdt, ops, o, feat, have, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
-  if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g);
+  if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g, have ? feat : nullptr);
   else st = hash_device(keys, vals, n, vdt, ops, c.plan, s, &g);
   if (st != AGG_OK) return st;
   std::memcpy(g->features, feat, sizeof(feat));
@@ -836,7 +838,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
       AGG_CUDA_TRY(cudaMemcpyAsync(fv + (size_t)r0 * es, vbuf(b), (size_t)rows * es, cudaMemcpyDeviceToDevice, s));
     }
     cudaStreamWaitEvent(s, done_ev, 0);
-    if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(fk, fv, n, vdt, ops, s, &g);
+    if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(fk, fv, n, vdt, ops, s, &g, have ? feat : nullptr);
     else st = hash_device(fk, fv, n, vdt, ops, c.plan, s, &g);
     if (st != AGG_OK) return st;
   } else {

@@ -129,17 +129,18 @@ __device__ __forceinline__ int64_t rows_of(int64_t n_cap, const int64_t* n_dev) 
   return n < n_cap ? n : n_cap;
 }
 
-// Digit of a key: 8 bits of the key itself, or (HASHED) of its MurmurHash3
-// fmix32 image, which spreads any key distribution evenly over the digits.
+// Digit of a key: 8 bits of key - kbase (kbase <= every key, so the order is
+// the keys' order), or (HASHED) of the key's MurmurHash3 fmix32 image, which
+// spreads any key distribution evenly over the digits.
 template <bool HASHED>
-__device__ __forceinline__ uint32_t digit_of(uint32_t key, int shift) {
-  return ((HASHED ? fmix32(key) : key) >> shift) & 0xFFu;
+__device__ __forceinline__ uint32_t digit_of(uint32_t key, int shift, uint32_t kbase) {
+  return ((HASHED ? fmix32(key) : key - kbase) >> shift) & 0xFFu;
 }
 
 template <bool HASHED>
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __restrict__ keys, int64_t n_cap,
-                                                           const int64_t* n_dev, int shift, int64_t ntiles,
-                                                           uint32_t* __restrict__ counts) {
+                                                           const int64_t* n_dev, int shift, uint32_t kbase,
+                                                           int64_t ntiles, uint32_t* __restrict__ counts) {
   __shared__ uint32_t h[256];
   const int64_t n = rows_of(n_cap, n_dev);
   const int64_t base = (int64_t)blockIdx.x * kSortTile;
@@ -154,7 +155,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
-    if (j < n) atomicAdd(&h[digit_of<HASHED>(k[i], shift)], 1u);
+    if (j < n) atomicAdd(&h[digit_of<HASHED>(k[i], shift, kbase)], 1u);
   }
   __syncthreads();
   if (threadIdx.x < 256) counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -175,8 +176,8 @@ template <class P, bool HASHED>
 __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t* __restrict__ keys,
                                                               const P* __restrict__ vals, uint32_t* __restrict__ okeys,
                                                               P* __restrict__ ovals, int64_t n_cap,
-                                                              const int64_t* n_dev, int shift, int64_t ntiles,
-                                                              const uint32_t* __restrict__ offsets) {
+                                                              const int64_t* n_dev, int shift, uint32_t kbase,
+                                                              int64_t ntiles, const uint32_t* __restrict__ offsets) {
   constexpr int kWarps = kSortThreads / 32;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   P* stage_v = (P*)sm_raw;                                // kSortTile
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t*
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
     const bool ok = j < n;
-    const uint32_t d = ok ? digit_of<HASHED>(kr[r], shift) : 0u;
+    const uint32_t d = ok ? digit_of<HASHED>(kr[r], shift, kbase) : 0u;
     // lanes holding the same digit: one ballot per digit bit
     uint32_t peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t*
     const int64_t j = wbase + r * 32 + lane;
     if (j < n) {
       const uint32_t key = kr[r];
-      const uint32_t d = digit_of<HASHED>(key, shift);
+      const uint32_t d = digit_of<HASHED>(key, shift, kbase);
       const uint32_t lp = whist[w * 256 + d] + lr[r];
       stage_k[lp] = key;
       stage_v[lp] = vals[j];
@@ -260,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t*
   const int cnt = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
   for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
     const uint32_t key = stage_k[i];
-    const uint32_t d = digit_of<HASHED>(key, shift);
+    const uint32_t d = digit_of<HASHED>(key, shift, kbase);
     const int64_t pos = (int64_t)(uint32_t)(gbase[d] + (uint32_t)i);
     okeys[pos] = key;
     ovals[pos] = stage_v[i];
@@ -282,7 +283,7 @@ size_t radix_tmp_bytes(int64_t n_cap) {
 template <class P>
 agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* va, uint32_t* kb, P* vb,
                             int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
-                            uint32_t** kout, P** vout) {
+                            uint32_t** kout, P** vout, uint32_t kbase) {
   *kout = const_cast<uint32_t*>(kin);
   *vout = const_cast<P*>(vin);
   const int64_t ntiles = (n_cap + kSortTile - 1) / kSortTile;
@@ -299,11 +300,11 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
   for (int shift = 0; shift < bits; shift += 8, ++pass) {
     uint32_t* ko = (pass & 1) ? kb : ka;
     P* vo = (pass & 1) ? vb : va;
-    radix_hist<false><<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, ntiles, counts);
+    radix_hist<false><<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, kbase, ntiles, counts);
     agg_status st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
     if (st != AGG_OK) return st;
-    radix_scatter<P, false><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, ntiles,
-                                                                        counts);
+    radix_scatter<P, false><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, kbase,
+                                                                        ntiles, counts);
     note_launch(2);
     AGG_CUDA_TRY(cudaGetLastError());
     ki = ko;
@@ -341,11 +342,11 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
   uint32_t* counts = (uint32_t*)tmp;
   const size_t cbytes = ((size_t)256 * ntiles * sizeof(uint32_t) + 255) & ~size_t(255);
   void* stmp = (char*)tmp + cbytes;
-  radix_hist<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, nullptr, shift, ntiles, counts);
+  radix_hist<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, nullptr, shift, 0u, ntiles, counts);
   st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
   if (st != AGG_OK) return st;
   radix_scatter<P, true><<<(unsigned)ntiles, kSortThreads, scatter_smem<P>(), s>>>(kin, vin, kout, vout, n, nullptr,
-                                                                                    shift, ntiles, counts);
+                                                                                    shift, 0u, ntiles, counts);
   note_launch(2);
   AGG_CUDA_TRY(cudaGetLastError());
   return AGG_OK;
@@ -358,9 +359,9 @@ template agg_status radix_partition_hashed<uint64_t>(const uint32_t*, const uint
 
 template agg_status radix_sort_pairs<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                                uint32_t*, int64_t, const int64_t*, int, void*, cudaStream_t,
-                                               uint32_t**, uint32_t**);
+                                               uint32_t**, uint32_t**, uint32_t);
 template agg_status radix_sort_pairs<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, uint32_t*,
                                                uint64_t*, int64_t, const int64_t*, int, void*, cudaStream_t,
-                                               uint32_t**, uint64_t**);
+                                               uint32_t**, uint64_t**, uint32_t);
 
 }  // namespace agg

@@ -17,7 +17,9 @@ size_t scan_tmp_bytes(int64_t n);
 agg_status scan_exclusive_u32(const uint32_t* in, uint32_t* out, int64_t n, uint32_t* total_dev, void* tmp,
                               cudaStream_t s);
 
-// Stable LSD radix sort by key bits [0, bits) (bits a multiple of 8, <= 32).
+// Stable LSD radix sort by bits [0, bits) of key - kbase (bits a multiple of
+// 8, <= 32; kbase must not exceed any key, and bits must cover the largest
+// key - kbase).
 // Sorts n_cap pairs, or, if n_dev is not null, the first *n_dev of them (the
 // count is read on the device; n_cap bounds it). The first pass reads
 // (kin, vin); passes then alternate between the buffers (ka, va) and
@@ -27,7 +29,7 @@ size_t radix_tmp_bytes(int64_t n_cap);
 template <class P>
 agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* va, uint32_t* kb, P* vb,
                             int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
-                            uint32_t** kout, P** vout);
+                            uint32_t** kout, P** vout, uint32_t kbase = 0);
 
 // One stable radix pass on bits [shift, shift + 8) of fmix32(key) (shift 24:
 // the top 8 bits; a pass at 16 followed by a pass at 24 orders rows by the top

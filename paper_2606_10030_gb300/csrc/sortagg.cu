@@ -460,9 +460,36 @@ __global__ void seg_finalize(SegOut o, int64_t d) {
   }
 }
 
+// Exact key range for the sort: grid-stride min and max, one atomic pair per
+// warp into mm[0] (min) and mm[1] (max).
+__global__ void __launch_bounds__(256) key_range(const uint32_t* __restrict__ k, int64_t n, uint32_t* mm) {
+  uint32_t lo = 0xFFFFFFFFu, hi = 0u;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  for (; i + 3 * stride < n; i += 4 * stride) {  // four loads in flight per thread
+    const uint32_t a = k[i], b = k[i + stride], c = k[i + 2 * stride], d = k[i + 3 * stride];
+    lo = min(min(lo, a), min(b, min(c, d)));
+    hi = max(max(hi, a), max(b, max(c, d)));
+  }
+  for (; i < n; i += stride) {
+    lo = min(lo, k[i]);
+    hi = max(hi, k[i]);
+  }
+  lo = __reduce_min_sync(0xffffffffu, lo);
+  hi = __reduce_max_sync(0xffffffffu, hi);
+  if ((threadIdx.x & 31) == 0) {
+    atomicMin(&mm[0], lo);
+    atomicMax(&mm[1], hi);
+  }
+}
+
+// Columns of at least this many rows sort only the bits their key range needs
+// (one pass fewer per 8 bits; the range costs one read of the keys and a sync).
+constexpr int64_t kRangeRows = int64_t(1) << 16;
+
 template <int DT, bool MM>
 static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t n, uint32_t ops, cudaStream_t s,
-                                 agg_groups** gout) {
+                                 agg_groups** gout, const float* feat) {
   using P = typename SV<DT>::P;
   if (n == 0) {
     agg_groups* g = nullptr;
@@ -500,7 +527,32 @@ static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t
   agg_status st;
   {
     PhaseTimer pt(AGG_PHASE_SORT, s);
-    st = radix_sort_pairs<P>(keys, (const P*)vals, kA, vA, kB, vB, n, nullptr, 32, rtmp, s, &sk, &sv);
+    int bits = 32;
+    uint32_t kbase = 0;
+    // a sampled key range already wider than 2^24 needs all four passes
+    const bool wide = feat != nullptr && feat[F_LOG2_RANGE] > 24.5f;
+    if (n >= kRangeRows && !wide) {  // digits of key - min cover max - min: the passes that range needs
+      uint32_t* mm = total + 2;
+      cudaMemsetAsync(mm, 0xFF, 4, s);
+      cudaMemsetAsync(mm + 1, 0, 4, s);
+      const DeviceInfo& di = device_info();
+      key_range<<<(unsigned)(di.sm_count * 8), 256, 0, s>>>(keys, n, mm);
+      note_launch();
+      uint32_t* hr = (uint32_t*)stream_pinned(s, 64, &st);
+      if (!hr) { release(); return st; }
+      cudaMemcpyAsync(hr, mm, 8, cudaMemcpyDeviceToHost, s);
+      const cudaError_t er = cudaStreamSynchronize(s);
+      if (er != cudaSuccess) {
+        set_error("sort group-by: %s", cudaGetErrorString(er));
+        release();
+        return AGG_ERR_CUDA;
+      }
+      kbase = hr[0];
+      const uint32_t span = hr[1] - hr[0];
+      const int need = span ? 32 - __builtin_clz(span) : 1;  // bits of the largest key - kbase
+      bits = ((need + 7) / 8) * 8;  // at least one pass, so the result lands in aligned scratch
+    }
+    st = radix_sort_pairs<P>(keys, (const P*)vals, kA, vA, kB, vB, n, nullptr, bits, rtmp, s, &sk, &sv, kbase);
   }
   if (st != AGG_OK) { release(); return st; }
   PhaseTimer pt_seg(AGG_PHASE_SEGREDUCE, s);
@@ -556,10 +608,11 @@ static agg_status sort_groupby_t(const uint32_t* keys, const void* vals, int64_t
 }
 
 agg_status sort_groupby(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops, cudaStream_t s,
-                        agg_groups** gout) {
+                        agg_groups** gout, const float* feat) {
   const bool mm = ops_minmax(ops);
 #define AGG_S(D) \
-  case D: return mm ? sort_groupby_t<D, true>(keys, vals, n, ops, s, gout) : sort_groupby_t<D, false>(keys, vals, n, ops, s, gout);
+  case D:        \
+    return mm ? sort_groupby_t<D, true>(keys, vals, n, ops, s, gout, feat) : sort_groupby_t<D, false>(keys, vals, n, ops, s, gout, feat);
   switch (vdt) { AGG_S(AGG_I32) AGG_S(AGG_I64) AGG_S(AGG_U32) AGG_S(AGG_F32) AGG_S(AGG_F64) }
 #undef AGG_S
   set_error("invalid dtype");

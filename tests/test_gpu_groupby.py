@@ -47,6 +47,10 @@ def make_case(case: str, dt: str, seed: int = 0):
     elif case == "onekey":  # every row on one key, the sentinel key in a tail run
         keys = np.full(262_147, 77, dtype=np.uint32)
         keys[-70_000:] = 0xFFFFFFFF
+    elif case == "dense":  # keys in a narrow integer range: the sort needs fewer passes
+        keys = (1000 + rng.integers(0, 50_000, 200_003)).astype(np.uint32)
+    elif case == "highnarrow":  # a narrow range far from zero: digits of key - min
+        keys = (0x80000000 + rng.integers(0, 300, 150_001)).astype(np.uint32)
     elif case == "sentinel":
         keys = dg.keys_uniform(50_001, 5, seed)
         keys[::3] = 0xFFFFFFFF
@@ -98,7 +102,8 @@ def run(keys, vals, strategy, ops=agg.AGG_ALL, **kw):
     return res, meta
 
 
-CASES = ["empty", "one", "few", "uniform1k", "uniform50k", "zipf", "distinct", "sentinel", "runs", "onekey"]
+CASES = ["empty", "one", "few", "uniform1k", "uniform50k", "zipf", "distinct", "sentinel", "runs", "onekey", "dense",
+         "highnarrow"]
 
 
 @pytest.mark.parametrize("strategy", STRATS)
