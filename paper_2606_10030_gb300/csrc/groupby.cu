@@ -152,25 +152,31 @@ int64_t table_slots_from_sketch(const float* f, int64_t n) {
   return p;
 }
 
-// The AUTO rule:
-//  - few distinct keys (a shared table holds them): SMEM;
-//  - columns of 2^20 rows or more: SMEM (on hash-partitioned rows when the
-//    keys overflow a shared table) when the sample covers at least 97% of the
-//    mass, or is flat with a reliable Chao1; otherwise SORT, which needs no
-//    estimate of the key count (a long tail of rare keys, or a flat column
-//    whose key count the sample leaves open);
-//  - smaller columns: SMEM under strong skew (the hot keys stay in shared
-//    memory), else one global table.
+// The AUTO rule (thresholds from the autotuner's timings of 5000 labelled
+// queries; m = 4096 sampled keys, coverage = 1 - f1 / m):
+//  - the sample covers >= 97% of the mass: SMEM (partitioned when the keys
+//    overflow a shared table);
+//  - columns under 2^20 rows: SMEM for few keys or a skewed sample, else one
+//    global table;
+//  - a skewed sample covering 90-97% (a hot head and a long tail of rare
+//    keys): SORT, which needs no key count;
+//  - few keys: SMEM;
+//  - a flat sample: SMEM on hash-partitioned rows while Chao1 is reliable and
+//    below 10^5 keys; otherwise SORT (a flat sample of a large key domain
+//    often hides a mildly skewed column with many more keys than Chao1);
+//  - a skewed sample far from covering the column: SMEM on hash-partitioned
+//    rows from 2^25 rows on, SORT below.
 int rule_strategy(const float* f, uint32_t ops) {
   const KeyEstimate e = key_estimate(f);
   const int cap = ops_minmax(ops) ? 1536 : 3072;  // 3/4 of the largest shared tables
+  const double coverage = 1.0 - (double)f[F_F1];  // F_F1 = f1 / m
+  const float log2n = f[F_LOG2N];
+  if (coverage >= 0.97) return AGG_STRAT_SMEM;
+  if (log2n < 20.0f) return (e.plan <= cap || !e.flat) ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
+  if (!e.flat && coverage >= 0.9) return AGG_STRAT_SORT;
   if (e.plan <= cap) return AGG_STRAT_SMEM;
-  if (f[F_LOG2N] >= 20.0f) {
-    const double coverage = 1.0 - (double)f[F_F1];  // F_F1 = f1 / m
-    if (coverage >= 0.97 || (e.flat && e.reliable)) return AGG_STRAT_SMEM;
-    return AGG_STRAT_SORT;
-  }
-  return f[F_TOP8] >= 0.05f ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
+  if (e.flat) return (e.reliable && e.chao1 < 1e5) ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
+  return log2n >= 25.0f ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
 }
 
 agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_groups** out) {
