@@ -248,7 +248,7 @@ agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uin
  * query's strategy (query.strategy: AUTO = the rule, LEARNED = the installed
  * network, or SMEM / GLOBAL) and table sizes, and allocates everything; one
  * host synchronisation. In a batch every query runs a hash strategy: a query
- * for which SORT is chosen runs on the global table (identical results).
+ * for which SORT is chosen runs on shared-memory tables (identical results).
  * agg_batch_run performs the device work (tables cleared, one persistent
  * build kernel over (query, 64 Ki-row tile) work items pulled from a device
  * counter, batched finalisation into ascending key order) as a CUDA graph

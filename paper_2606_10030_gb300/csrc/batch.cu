@@ -580,7 +580,10 @@ static void plan_sizes(agg_batch_plan* P, const std::vector<int>& learned) {
     int strat = q.strategy;
     if (strat == AGG_STRAT_LEARNED) strat = learned[i] >= 0 ? learned[i] : rule_strategy(f, q.ops);
     else if (strat == AGG_STRAT_AUTO || strat == AGG_STRAT_AUTOTUNE) strat = rule_strategy(f, q.ops);
-    qp.strategy = strat == AGG_STRAT_SMEM ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
+    // the batch runs hash strategies only: a query the selector would sort gets
+    // shared-memory tables (hot keys stay in shared memory; a global table
+    // alone would serialize their atomics)
+    qp.strategy = strat == AGG_STRAT_GLOBAL ? AGG_STRAT_GLOBAL : AGG_STRAT_SMEM;
     bool covered = false;
     const double est = q.n > 0 ? distinct_estimate(f, &covered) : 1.0;
     const int64_t slots = q.n > 0 ? table_slots_from_sketch(f, q.n) : 1024;

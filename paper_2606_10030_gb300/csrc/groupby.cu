@@ -20,14 +20,18 @@ namespace agg {
 using KernelPtr = const void*;
 
 template <int DT, bool MM>
-static KernelPtr build_kernel(bool smem, bool vec) {
-  if (smem) return vec ? (KernelPtr)gb_build<DT, MM, true, true> : (KernelPtr)gb_build<DT, MM, true, false>;
-  return vec ? (KernelPtr)gb_build<DT, MM, false, true> : (KernelPtr)gb_build<DT, MM, false, false>;
+static KernelPtr build_kernel(bool smem, bool vec, bool multi) {
+  if (smem) {
+    if (!vec) return (KernelPtr)gb_build<DT, MM, true, false, false>;
+    return multi ? (KernelPtr)gb_build<DT, MM, true, true, true> : (KernelPtr)gb_build<DT, MM, true, true, false>;
+  }
+  if (!vec) return (KernelPtr)gb_build<DT, MM, false, false, false>;
+  return multi ? (KernelPtr)gb_build<DT, MM, false, true, true> : (KernelPtr)gb_build<DT, MM, false, true, false>;
 }
 
-static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec) {
+static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec, bool multi) {
 #define AGG_B(D) \
-  case D: return mm ? build_kernel<D, true>(smem, vec) : build_kernel<D, false>(smem, vec);
+  case D: return mm ? build_kernel<D, true>(smem, vec, multi) : build_kernel<D, false>(smem, vec, multi);
   switch (dt) { AGG_B(AGG_I32) AGG_B(AGG_I64) AGG_B(AGG_U32) AGG_B(AGG_F32) AGG_B(AGG_F64) }
 #undef AGG_B
   return nullptr;
@@ -219,6 +223,7 @@ struct HashPlan {
   int smem_slots;   // shared slots (power of two) for SMEM
   int threads;
   int blocks_per_sm;
+  bool multi_keys = true;  // per-warp reduction of several frequent keys (see build_rows)
 };
 
 // One hash aggregation: a zeroed global table, any number of build launches
@@ -276,7 +281,7 @@ class HashRun {
     a.status = status_;
     a.progress = progress_;
     if (plan_.partition && n >= kPartTileRows) return build_partitioned(a, use_smem);
-    KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec);
+    KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec, plan_.multi_keys);
     const size_t smem = use_smem ? stab_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;
     const int threads = plan_.threads;
     int bps = occupancy(bk, threads, smem);
@@ -355,7 +360,7 @@ class HashRun {
         void* args[] = {&a, &next_tile, &tile_rows};
         e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, smem, s_);
       } else {
-        KernelPtr bk = pick_build(vdt_, mm_, false, true);
+        KernelPtr bk = pick_build(vdt_, mm_, false, true, true);
         const int threads = plan_.threads;
         int bps = occupancy(bk, threads, 0);
         if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
@@ -562,6 +567,9 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   c->plan.slots = tslots ? tslots : (have_feat ? table_slots_from_sketch(feat, n) : 2048);
   c->plan.smem_slots = sslots ? sslots : smem_slots_for(est, ops_minmax(ops));
   c->plan.threads = o.block_threads ? o.block_threads : (strategy == AGG_STRAT_SMEM ? 512 : 256);
+  // frequent keys (a key with >= 3% of the sample, or a handful of keys) make
+  // the warp-level reduction of several keys pay; without a sketch, assume so
+  c->plan.multi_keys = !have_feat || feat[F_TOP1] >= 0.03f || est <= 32.0;
   c->plan.blocks_per_sm = o.blocks_per_sm;
   // Partition the rows by hash first when the shared tables would spill (more
   // distinct keys than a shared table admits) or the global table exceeds

@@ -402,13 +402,14 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
 }
 
 // ---------------------------------------------------------------------------
-// Dominant keys: when at least a quarter of the 128 rows a warp holds carry
-// the key of lane 0's first row (hot keys of a partitioned or clustered
-// input), the warp reduces those rows with shuffles and applies one partial
-// aggregate; the remaining rows take the per-row path. This removes the
-// same-slot atomic conflicts that hot keys cause.
+// Frequent keys: when at least kDominantRows of the 128 rows a warp holds
+// carry one key (hot keys of a skewed, partitioned or clustered input, or a
+// column with a handful of keys), the warp reduces those rows with shuffles
+// and applies one partial aggregate; the remaining rows take the per-row path.
+// This removes the same-slot atomic conflicts that frequent keys cause.
 // ---------------------------------------------------------------------------
-constexpr int kDominantRows = 32;
+constexpr int kDominantRows = 8;  // rows of one key (of 128) that make a reduced update pay
+constexpr int kMaxWarpKeys = 8;   // keys reduced per warp and quad of rows, at most
 template <int DT>
 struct Partial4 {  // partial aggregate of rows with one key
   uint32_t cnt;
@@ -419,7 +420,7 @@ struct Partial4 {  // partial aggregate of rows with one key
 };
 
 template <int DT, bool MM>
-__device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)[4], const bool (&take)[4]) {
+__device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)[4], uint32_t take) {
   Partial4<DT> p;
   p.cnt = 0;
   p.isum = 0;
@@ -430,7 +431,7 @@ __device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)
   p.mx = 0;
 #pragma unroll
   for (int r = 0; r < 4; ++r) {
-    if (!take[r]) continue;
+    if (!((take >> r) & 1u)) continue;
     p.cnt += 1;
     if (DT == AGG_F32) {
       float t, e;
@@ -521,11 +522,11 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
   }
 }
 
-// The warp reduces the rows marked in take (all of one key) and lane 0 folds
-// the partial into the tables.
+// The warp reduces the rows marked in take (a 4-bit mask per lane; all of
+// one key) and lane 0 folds the partial into the tables.
 template <int DT, bool MM, bool SMEM>
 __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
-                                              const typename GV<DT>::T (&v)[4], const bool (&take)[4]) {
+                                              const typename GV<DT>::T (&v)[4], uint32_t take) {
   Partial4<DT> p = partial_of<DT, MM>(v, take);
   warp_reduce_partial<DT, MM>(p);
   if ((threadIdx.x & 31) != 0) return;
@@ -580,7 +581,11 @@ __device__ __forceinline__ void report_counts(const BuildArgs& a, const BlockCou
 constexpr int kQuadsPerIter = AGG_QUADS_PER_ITER;
 
 // Returns the number of rows this thread went through (the vector body's).
-template <int DT, bool MM, bool SMEM, bool VEC>
+// MULTI: up to kMaxWarpKeys frequent keys per warp and quad of rows get a
+// reduced update (columns with a handful of keys or hot keys); without it
+// every row takes the per-row path (for columns whose sketch shows no
+// frequent key: the warp then never waits for its slowest lane).
+template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true>
 __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
                                                int64_t nthreads) {
   using T = typename GV<DT>::T;
@@ -605,8 +610,14 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
     const uint4* kq = (const uint4*)(keys + a.head);
     const uint4* vq = (const uint4*)(vals + a.head);
     constexpr int VPQ = sizeof(T) == 4 ? 1 : 2;  // 16-byte value vectors per quad
+    // The loop runs per warp: its condition is the warp's first quad, so all
+    // 32 lanes stay in every iteration (lanes past the end have has = false)
+    // and the warp-wide reductions below see the whole warp. tid and nthreads
+    // are multiples of 32 apart within a warp (blocks of whole warps).
+    const int lane = (int)(tid & 31);
     int it = 0;
-    for (int64_t q = tid; q < nq; q += kQuadsPerIter * nthreads) {
+    for (int64_t qw = tid - lane; qw < nq; qw += kQuadsPerIter * nthreads) {
+      const int64_t q = qw + lane;
       uint4 kk[kQuadsPerIter], va[kQuadsPerIter], vb[kQuadsPerIter];
       bool has[kQuadsPerIter];
 #pragma unroll
@@ -622,35 +633,43 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
         const uint32_t key[4] = {kk[u].x, kk[u].y, kk[u].z, kk[u].w};
         T val[4];
         unpack4<T>(va[u], vb[u], val);
-        // rows on the key of lane 0's first row, if it dominates the warp's
-        // 128 rows, go through one reduced update
-        bool taken[4] = {false, false, false, false};
-        if (__activemask() == 0xffffffffu) {
-          const uint32_t k0 = __shfl_sync(0xffffffffu, key[0], 0);
-          unsigned nm = 0;
+        // Frequent keys among the warp's 128 rows go through one reduced
+        // update each: first the key of lane 0's first row; while a key had
+        // at least kDominantRows rows, the next candidate is the first row not
+        // yet folded. The remaining rows take the per-row path.
+        uint32_t rem = has[u] ? 0xFu : 0u;  // this lane's rows not yet folded
+        if (MULTI) {  // every lane of the warp is here (lane 0 always has rows)
+          uint32_t k0 = __shfl_sync(0xffffffffu, key[0], 0);
+          constexpr int kKeys = kMaxWarpKeys;
+#pragma unroll 1
+          for (int w = 0; w < kKeys; ++w) {
+            uint32_t take = 0;
 #pragma unroll
-          for (int r = 0; r < 4; ++r) {
-            taken[r] = has[u] && key[r] == k0;
-            nm += taken[r] ? 1u : 0u;
+            for (int r = 0; r < 4; ++r) take |= (((rem >> r) & 1u) && key[r] == k0) ? (1u << r) : 0u;
+            if (__reduce_add_sync(0xffffffffu, (unsigned)__popc(take)) < (unsigned)kDominantRows) break;
+            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, take);
+            rem &= ~take;
+            if (w + 1 == kKeys) break;
+            const uint32_t lanes = __ballot_sync(0xffffffffu, rem != 0u);
+            if (lanes == 0u) break;
+            uint32_t next = key[3];  // this lane's first row not yet folded
+            if (rem & 4u) next = key[2];
+            if (rem & 2u) next = key[1];
+            if (rem & 1u) next = key[0];
+            k0 = __shfl_sync(0xffffffffu, next, __ffs(lanes) - 1);
           }
-          const unsigned tot = __reduce_add_sync(0xffffffffu, nm);
-          if (tot >= (unsigned)kDominantRows) {
-            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, taken);
-            if (tot == 128u) continue;
-          } else {
-#pragma unroll
-            for (int r = 0; r < 4; ++r) taken[r] = false;
-          }
+          if (rem == 0u) continue;  // this lane's rows are all folded
         }
 #pragma unroll
         for (int r = 0; r < 4; ++r) {
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
-          bool ok[1] = {has[u] && !taken[r]};
+          bool ok[1] = {((rem >> r) & 1u) != 0u};
           fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok);
         }
       }
-      if ((++it & 15) == 0 && *(volatile int*)a.status) break;  // table full: the build is redone
+      // table full: the build is redone (status read by lane 0, so the whole warp leaves)
+      if ((++it & 15) == 0 && __shfl_sync(0xffffffffu, lane == 0 ? *(volatile int*)a.status : 0, 0)) break;
     }
     return (uint32_t)it * 4u * kQuadsPerIter;
   } else {
@@ -701,8 +720,8 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
 }
 
 // The build kernel of one query: grid-stride over all rows.
-template <int DT, bool MM, bool SMEM, bool VEC>
-__global__ void gb_build(BuildArgs a) {
+template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI>
+__global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlockCounts s_cnt;
   if (threadIdx.x == 0) s_cnt = BlockCounts{0u, 0u};
@@ -713,8 +732,8 @@ __global__ void gb_build(BuildArgs a) {
     st.clear(a.smem_slots);
   }
   __syncthreads();
-  const uint32_t seen = build_rows<DT, MM, SMEM, VEC>(a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x,
-                                                      (int64_t)gridDim.x * blockDim.x);
+  const uint32_t seen = build_rows<DT, MM, SMEM, VEC, MULTI>(
+      a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
   atomicAdd(&s_cnt.seen, seen);
   if (SMEM) {
     __syncthreads();
@@ -731,7 +750,8 @@ __global__ void gb_build(BuildArgs a) {
 constexpr int64_t kPartTileRows = int64_t(1) << 16;
 
 template <int DT, bool MM, bool VEC>
-__global__ void gb_build_tiles(BuildArgs a, unsigned long long* next_tile, int64_t tile_rows) {
+__global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
+                                                        int64_t tile_rows) {
   using T = typename GV<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_t;
