@@ -440,29 +440,29 @@ class HashRun {
       agg_groups_free(g);
       return AGG_ERR_CUDA;
     }
-    int64_t* hb = (int64_t*)stream_pinned(s_, 64, &st);
+    // one copy of the status block: status (+0), group count (+64), and the
+    // rows seen / failed of a build stopped by a full table (+192, +200)
+    unsigned char* hb = (unsigned char*)stream_pinned(s_, 256, &st);
     if (!hb) {
       agg_groups_free(g);
       return st;
     }
-    cudaError_t e1 = cudaMemcpyAsync(hb, counter_, 8, cudaMemcpyDeviceToHost, s_);
-    cudaError_t e2 = cudaMemcpyAsync(hb + 1, status_, 4, cudaMemcpyDeviceToHost, s_);
-    if (e2 == cudaSuccess) e2 = cudaMemcpyAsync(hb + 2, progress_, 16, cudaMemcpyDeviceToHost, s_);
-    cudaError_t e3 = cudaStreamSynchronize(s_);
-    if (e1 != cudaSuccess || e2 != cudaSuccess || e3 != cudaSuccess) {
-      set_error("group-by read-back failed: %s",
-                cudaGetErrorString(e3 != cudaSuccess ? e3 : (e1 != cudaSuccess ? e1 : e2)));
+    const cudaError_t e1 = cudaMemcpyAsync(hb, status_, 208, cudaMemcpyDeviceToHost, s_);
+    const cudaError_t e3 = cudaStreamSynchronize(s_);
+    if (e1 != cudaSuccess || e3 != cudaSuccess) {
+      set_error("group-by read-back failed: %s", cudaGetErrorString(e3 != cudaSuccess ? e3 : e1));
       agg_groups_free(g);
       return AGG_ERR_CUDA;
     }
-    if (*(int*)(hb + 1) != 0) {
-      rows_seen_ = (uint64_t)hb[2];
-      rows_failed_ = (uint64_t)hb[3];
+    const int64_t groups = *(const int64_t*)(hb + 64);
+    if (*(const int*)hb != 0) {
+      rows_seen_ = *(const uint64_t*)(hb + 192);
+      rows_failed_ = *(const uint64_t*)(hb + 200);
       agg_groups_free(g);
       set_error("global hash table of %lld slots is full", (long long)plan_.slots);
       return AGG_ERR_TABLE_FULL;
     }
-    g->num_groups = hb[0];
+    g->num_groups = groups;
     g->table_slots = plan_.slots;
     g->smem_slots = plan_.strategy == AGG_STRAT_SMEM ? plan_.smem_slots : 0;
     g->strategy = plan_.strategy;
