@@ -162,12 +162,14 @@ int64_t table_slots_from_sketch(const float* f, int64_t n) {
 //    overflow a shared table);
 //  - columns under 2^20 rows: SMEM for few keys or a skewed sample, else one
 //    global table;
-//  - a skewed sample covering 90-97% (a hot head and a long tail of rare
-//    keys): SORT, which needs no key count;
+//  - a skewed sample covering 90-97% whose singletons suggest at least half
+//    as many unseen keys as seen ones (f1^2 / 2 f2 >= d / 2: a hot head and a
+//    long tail of rare keys): SORT, which needs no key count;
 //  - few keys: SMEM;
 //  - a flat sample: SMEM on hash-partitioned rows while Chao1 is reliable and
-//    below 10^5 keys; otherwise SORT (a flat sample of a large key domain
-//    often hides a mildly skewed column with many more keys than Chao1);
+//    below 10^5 keys (any reliable Chao1 from 2^28 rows on); otherwise SORT (a
+//    flat sample of a large key domain often hides a mildly skewed column with
+//    many more keys than Chao1);
 //  - a skewed sample far from covering the column: SMEM on hash-partitioned
 //    rows from 2^25 rows on, SORT below.
 int rule_strategy(const float* f, uint32_t ops) {
@@ -177,9 +179,12 @@ int rule_strategy(const float* f, uint32_t ops) {
   const float log2n = f[F_LOG2N];
   if (coverage >= 0.97) return AGG_STRAT_SMEM;
   if (log2n < 20.0f) return (e.plan <= cap || !e.flat) ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
-  if (!e.flat && coverage >= 0.9) return AGG_STRAT_SORT;
+  const double m = std::min(std::exp2((double)log2n), (double)kSketchSample);
+  const double d = (double)f[F_DISTINCT] * m, f1 = (double)f[F_F1] * m, f2 = (double)f[F_F2] * m;
+  const double unseen = f1 * (f1 - 1.0) / (2.0 * (f2 + 1.0));  // Chao1's unseen keys
+  if (!e.flat && coverage >= 0.9 && unseen >= 0.5 * d) return AGG_STRAT_SORT;
   if (e.plan <= cap) return AGG_STRAT_SMEM;
-  if (e.flat) return (e.reliable && e.chao1 < 1e5) ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
+  if (e.flat) return (e.reliable && (e.chao1 < 1e5 || log2n >= 28.0f)) ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
   return log2n >= 25.0f ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
 }
 

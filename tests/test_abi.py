@@ -125,10 +125,12 @@ def test_rule_strategy_is_a_host_call(L):
     # flat with repeats (about 65536 keys, f2 well above 2): partitioned shared-memory build
     f[0], f[4], f[5], f[6], f[8], f[12] = 28, 3970 / 4096, 3846 / 4096, 124 / 4096, 17 / 4096, 20
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
-    # flat with few repeats (Chao1 about 7e5): sort
+    # flat with few repeats (Chao1 about 7e5): sort below 2^28 rows, partitioned tables from there on
     f[5], f[6] = 4060 / 4096, 11 / 4096
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
+    f[0] = 26
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SORT
-    f[5], f[6] = 3846 / 4096, 124 / 4096
+    f[0], f[5], f[6] = 28, 3846 / 4096, 124 / 4096
     # skewed and far from covered, on 2^28 rows: partitioned shared-memory build
     f[8] = 0.2
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
@@ -141,6 +143,9 @@ def test_rule_strategy_is_a_host_call(L):
     # a hot head covering 94 % of the mass and a long tail, on 2^30 rows: sort
     f[0], f[4], f[5], f[6], f[8] = 30, 400 / 4096, 250 / 4096, 60 / 4096, 0.65
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SORT
+    # a skewed sample of a small domain (most seen keys repeat): shared-memory tables
+    f[4], f[5], f[6], f[8] = 900 / 4096, 200 / 4096, 200 / 4096, 0.1
+    assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
     # a sample covering 98 % of the mass of a large column: shared-memory tables
     f[0], f[4], f[5], f[6], f[8] = 28, 2000 / 4096, 80 / 4096, 200 / 4096, 0.01
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
