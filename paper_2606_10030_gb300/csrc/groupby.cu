@@ -349,7 +349,12 @@ class HashRun {
       PhaseTimer pt(AGG_PHASE_BUILD, s_);
       if (use_smem) {
         unsigned long long* next_tile = (unsigned long long*)((char*)mem_ + status_off_ + 128);
-        AGG_CUDA_TRY(cudaMemsetAsync(next_tile, 0, 8, s_));
+        e = cudaMemsetAsync(next_tile, 0, 8, s_);
+        if (e != cudaSuccess) {
+          cudaFreeAsync(tmp, s_);
+          set_error("partitioned build: %s", cudaGetErrorString(e));
+          return AGG_ERR_CUDA;
+        }
         KernelPtr bk = pick_tiles(vdt_, mm_);
         const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
         const int threads = plan_.threads;
