@@ -416,7 +416,7 @@ class HashRun {
       if (mm_) gb_compact<true, 1><<<cgrid, 256, 0, s_>>>((const GSlot<true>*)mem_, mask, ck, cs, counter_);
       else gb_compact<false, 1><<<cgrid, 256, 0, s_>>>((const GSlot<false>*)mem_, mask, ck, cs, counter_);
       note_launch();
-      const int rgrid = (int)((nslots_ + kRankThreads - 1) / kRankThreads);
+      const int rgrid = (int)((nslots_ + kRankKeys - 1) / kRankKeys);
       void* args[] = {&mem_, &ck, &cs, &o};
       e = cudaLaunchKernel(pick_small(vdt_, mm_), dim3(rgrid), dim3(kRankThreads), args, 0, s_);
       note_launch();

@@ -839,6 +839,8 @@ __device__ __forceinline__ uint32_t key_of(const GSlot<MM>* tab, uint32_t mask, 
 // ranks are a permutation and the output is in ascending key order.
 constexpr int kSmallRank = 4097;
 constexpr int kRankThreads = 256;
+constexpr int kRankSplit = 4;                             // threads counting one key's rank
+constexpr int kRankKeys = kRankThreads / kRankSplit;      // keys ranked per block
 
 template <int DT, bool MM>
 __global__ void __launch_bounds__(kRankThreads) gb_rank_gather(const GSlot<MM>* tab, const uint32_t* ckeys,
@@ -847,13 +849,17 @@ __global__ void __launch_bounds__(kRankThreads) gb_rank_gather(const GSlot<MM>* 
   const int d = (int)*(const unsigned long long*)o.d;
   for (int t = threadIdx.x; t < d; t += kRankThreads) sk[t] = ckeys[t];
   __syncthreads();
-  const int i = blockIdx.x * kRankThreads + threadIdx.x;
-  if (i >= d) return;
-  const uint32_t key = sk[i];
+  // kRankSplit neighbouring lanes count the smaller keys of one key, each over
+  // every kRankSplit-th key, and add their counts with shuffles
+  const int i = blockIdx.x * kRankKeys + (int)threadIdx.x / kRankSplit;
+  const int part = (int)threadIdx.x % kRankSplit;
+  const uint32_t key = i < d ? sk[i] : 0u;
   int rank = 0;
 #pragma unroll 8
-  for (int t = 0; t < d; ++t) rank += sk[t] < key ? 1 : 0;
-  write_group<DT, MM>(o, rank, key, tab[cslot[i]]);
+  for (int t = part; t < d; t += kRankSplit) rank += sk[t] < key ? 1 : 0;
+#pragma unroll
+  for (int m = 1; m < kRankSplit; m <<= 1) rank += __shfl_xor_sync(0xffffffffu, rank, m);
+  if (i < d && part == 0) write_group<DT, MM>(o, rank, key, tab[cslot[i]]);
 }
 
 // Large tables: compact occupied slots into (key, slot) pairs.
