@@ -1,6 +1,6 @@
 // Autotuner (step a8): time the GROUP BY candidates on the actual query and
 // cache the fastest by query signature. The exhaustive pick also labels the
-// training data of the learned selector and judges its regret.
+// training data of the learned selector and measures its regret.
 #include <cmath>
 #include <cstdio>
 #include <cstring>
