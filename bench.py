@@ -297,9 +297,22 @@ def extra_scan(steps: int, peaks: dict) -> dict:
     gbs = n * 4 / (ms * 1e-3) / 1e9
     del col
     torch.cuda.empty_cache()
+    # the small ungrouped case (2^20 int32 rows, L2-resident): time per call over 1000
+    # back-to-back calls (scan and merge, launch-bound at this size)
+    small = dgc.values("i32", 1 << 20, seed=0)
+    for _ in range(10):
+        agg.agg_reduce(small, agg.AGG_ALL, out=out)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(1000):
+        agg.agg_reduce(small, agg.AGG_ALL, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    small_us = a.elapsed_time(b) / 1000 * 1e3
     return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30 int32 rows (4 GiB)", "ms": round(ms, 4),
             "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
-            "frac_of_nominal_8TBs": round(gbs / 8000.0, 4), "steps": steps}
+            "frac_of_nominal_8TBs": round(gbs / 8000.0, 4), "steps": steps,
+            "small_2p20_int32_us_per_call_back_to_back": round(small_us, 2)}
 
 
 def extra_batched(steps: int, nq: int = 512) -> dict:
