@@ -38,9 +38,32 @@ __device__ double block_sum_d(double v, double* red) {
 // (64-bit slots holding key << 1 | 1, so every key value is representable),
 // their counts histogrammed, and the 32 largest counts read off the histogram
 // from the top by one warp.
+// The sample: row p_j = (offset + j * (n / m)) mod n for j < m, and the row
+// after it (for the adjacent-repeat feature).
+__device__ __forceinline__ int64_t sample_row(int64_t n, int m, uint64_t offset, int j) {
+  const int64_t stride = m > 0 ? n / m : 1;
+  const uint64_t off = n > 0 ? offset % (uint64_t)n : 0;
+  const uint64_t q = off + (uint64_t)j * (uint64_t)stride;  // < 2n
+  return (int64_t)(q >= (uint64_t)n ? q - (uint64_t)n : q);
+}
+
+// Gathers the sampled keys (pre[j]) and their successors (pre[kSketchSample +
+// j]) with many blocks: one block issuing 8192 scattered loads is bound by its
+// own load queue.
+__global__ void sketch_gather(const uint32_t* __restrict__ keys, int64_t n, uint64_t offset,
+                              uint32_t* __restrict__ pre) {
+  const int m = (int)(n < kSketchSample ? n : kSketchSample);
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= m) return;
+  const int64_t p = sample_row(n, m, offset, j);
+  pre[j] = keys[p];
+  pre[kSketchSample + j] = p + 1 < n ? keys[p + 1] : 0u;
+}
+
+// pre: the gathered sample (sketch_gather), or null to load it here.
 __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int vbytes, int nops, int fp,
                              int slot_bytes, uint64_t offset, double smem_bytes, double l2_bytes,
-                             float* __restrict__ feat) {
+                             float* __restrict__ feat, const uint32_t* __restrict__ pre) {
   extern __shared__ __align__(16) unsigned char sm[];
   unsigned long long* slot = (unsigned long long*)sm;            // kSketchSlots
   uint32_t* cnt = (uint32_t*)(slot + kSketchSlots);              // kSketchSlots
@@ -60,8 +83,6 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
     s_kmax = 0;
   }
   const int m = (int)(n < kSketchSample ? n : kSketchSample);
-  const int64_t stride = m > 0 ? n / m : 1;
-  const uint64_t off = n > 0 ? offset % (uint64_t)n : 0;
   __syncthreads();
   constexpr int kPer = kSketchSample / kSketchThreads;  // sampled keys per thread
   uint32_t kk[kPer], nx[kPer];
@@ -74,12 +95,15 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
     kk[u] = 0;
     nx[u] = 0;
     if (have[u]) {
-      // (offset + j * stride) mod n, with off + j * stride < 2n
-      const uint64_t q = off + (uint64_t)j * (uint64_t)stride;
-      const int64_t p = (int64_t)(q >= (uint64_t)n ? q - (uint64_t)n : q);
-      kk[u] = keys[p];
+      const int64_t p = sample_row(n, m, offset, j);
       hasnx[u] = p + 1 < n;
-      if (hasnx[u]) nx[u] = keys[p + 1];
+      if (pre) {
+        kk[u] = pre[j];
+        nx[u] = pre[kSketchSample + j];
+      } else {
+        kk[u] = keys[p];
+        if (hasnx[u]) nx[u] = keys[p + 1];
+      }
     }
   }
   {  // key range and adjacent repeats: reduced per warp, one atomic each per warp
@@ -217,8 +241,9 @@ __device__ void sketch_block(const uint32_t* __restrict__ keys, int64_t n, int v
 __global__ void __launch_bounds__(kSketchThreads) sketch_kernel(const uint32_t* __restrict__ keys, int64_t n,
                                                                 int vbytes, int nops, int fp, int slot_bytes,
                                                                 uint64_t offset, double smem_bytes, double l2_bytes,
-                                                                float* __restrict__ feat) {
-  sketch_block(keys, n, vbytes, nops, fp, slot_bytes, offset, smem_bytes, l2_bytes, feat);
+                                                                float* __restrict__ feat,
+                                                                const uint32_t* __restrict__ pre) {
+  sketch_block(keys, n, vbytes, nops, fp, slot_bytes, offset, smem_bytes, l2_bytes, feat, pre);
 }
 
 // One block per query of a batch.
@@ -227,7 +252,7 @@ __global__ void __launch_bounds__(kSketchThreads) sketch_batch_kernel(const Sket
                                                                       float* __restrict__ feat) {
   const SketchJob j = jobs[blockIdx.x];
   sketch_block(j.keys, j.n, j.vbytes, j.nops, j.fp, j.slot_bytes, j.offset, smem_bytes, l2_bytes,
-               feat + (size_t)blockIdx.x * F_COUNT);
+               feat + (size_t)blockIdx.x * F_COUNT, nullptr);
 }
 
 agg_status sketch_batch_launch(const SketchJob* jobs_dev, int nq, float* feat_dev, cudaStream_t s) {
@@ -255,11 +280,22 @@ agg_status sketch_launch(const uint32_t* keys, int64_t n, int vdt, uint32_t ops,
     AGG_CUDA_TRY(cudaFuncSetAttribute(sketch_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSketchSmem));
     attr_set[di.device] = true;
   }
+  // the gathered sample sits at 64 KiB of the stream scratch (transient; the
+  // scratch block is at least 1 MiB, so this request never moves it)
+  agg_status st = AGG_OK;
+  char* scr = (char*)stream_scratch(s, (size_t)96 << 10, &st);
+  if (!scr) return st;
+  uint32_t* pre = (uint32_t*)(scr + ((size_t)64 << 10));
   PhaseTimer pt(AGG_PHASE_SKETCH, s);
+  const int m = (int)(n < kSketchSample ? n : kSketchSample);
+  if (m > 0) {
+    sketch_gather<<<(m + 255) / 256, 256, 0, s>>>(keys, n, offset, pre);
+    note_launch();
+  }
   note_launch();
   sketch_kernel<<<1, kSketchThreads, kSketchSmem, s>>>(keys, n, (int)dtype_size(vdt), __builtin_popcount(ops),
                                              dtype_is_fp(vdt) ? 1 : 0, gslot_bytes(ops_minmax(ops)), offset,
-                                             (double)di.smem_per_block_optin, (double)di.l2_bytes, feat_dev);
+                                             (double)di.smem_per_block_optin, (double)di.l2_bytes, feat_dev, pre);
   AGG_CUDA_TRY(cudaGetLastError());
   return AGG_OK;
 }
