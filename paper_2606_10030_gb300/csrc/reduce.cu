@@ -14,7 +14,9 @@
 //   integers  int64 sum (wraps mod 2^64), min and max in the value type;
 //   float32   TwoSum-compensated float32 pair (s, c), order-preserving
 //             uint32 images for min/max;
-//   float64   TwoSum-compensated float64 pair, uint64 images.
+//   float64   TwoSum-compensated float64 pair fed with plain sums of each
+//             iteration's 8 rows (GB300 issues few float64 operations), uint64
+//             images.
 // Block partials carry the sum as a float64 pair (hi, lo); the final merge is
 // a float64 double-double sum in a fixed order, so the result is
 // deterministic for a given grid.
@@ -126,6 +128,36 @@ struct Acc<DT, SUM, MM, true> {
       fold(__longlong_as_double((long long)(((uint64_t)r.y << 32) | r.x)));
       fold(__longlong_as_double((long long)(((uint64_t)r.w << 32) | r.z)));
     }
+  }
+  // float64 SUM over the K vectors of one loop iteration (2K rows; a vector
+  // past the end is all zero bits, i.e. +0.0, which adds nothing): the rows
+  // are added plainly in a fixed tree and the group's sum enters (s, c) with
+  // one TwoSum. That is a quarter of the float64 operations of a TwoSum per
+  // row (GB300 issues few float64 operations per clock); the plain additions
+  // add at most (2K - 1) 2^-53 sum|x| of error, far inside the bound of the
+  // result. MIN/MAX take only the valid vectors.
+  template <int K>
+  __device__ __forceinline__ void fold_group(const uint4 (&r)[K], const bool (&ok)[K]) {
+    double g[K];
+#pragma unroll
+    for (int u = 0; u < K; ++u) {
+      const double x0 = __longlong_as_double((long long)(((uint64_t)r[u].y << 32) | r[u].x));
+      const double x1 = __longlong_as_double((long long)(((uint64_t)r[u].w << 32) | r[u].z));
+      g[u] = x0 + x1;
+      if (MM && ok[u]) {
+        const U m0 = FpImg<T>::img(x0), m1 = FpImg<T>::img(x1);
+        mn = min(mn, min(m0, m1));
+        mx = max(mx, max(m0, m1));
+      }
+    }
+#pragma unroll
+    for (int w = 1; w < K; w <<= 1)
+#pragma unroll
+      for (int u = 0; u + w < K; u += 2 * w) g[u] += g[u + w];
+    T t, e;
+    two_sum(s, (T)g[0], t, e);
+    s = t;
+    c += e;
   }
   __device__ void to_partial(Partial& p) const {
     p.si = 0;
@@ -251,9 +283,16 @@ __global__ void __launch_bounds__(kBlock) reduce_scan(const typename Traits<DT>:
         const int64_t i = base + (int64_t)u * kBlock;
         r[u] = i < nv ? ld_stream_v4(v + i) : make_uint4(0, 0, 0, 0);
       }
+      if constexpr (DT == AGG_F64 && SUM) {
+        bool ok[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        if (base + (int64_t)u * kBlock < nv) a.fold_vec(r[u]);
+        for (int u = 0; u < kUnroll; ++u) ok[u] = base + (int64_t)u * kBlock < nv;
+        a.fold_group(r, ok);
+      } else {
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          if (base + (int64_t)u * kBlock < nv) a.fold_vec(r[u]);
+        }
       }
     }
   }
