@@ -309,10 +309,28 @@ def extra_scan(steps: int, peaks: dict) -> dict:
     b.record()
     torch.cuda.synchronize()
     small_us = a.elapsed_time(b) / 1000 * 1e3
+    del small
+    # the other value types, 2^30 rows each (int64 and float64: 8 GiB), all five ops
+    by_dtype = {"i32": round(gbs, 1)}
+    for dt, esz in (("i64", 8), ("f32", 4), ("f64", 8)):
+        col = dgc.values(dt, n, seed=0)
+        for _ in range(3):
+            agg.agg_reduce(col, agg.AGG_ALL, out=out)
+        torch.cuda.synchronize()
+        reps = 20
+        a.record()
+        for _ in range(reps):
+            agg.agg_reduce(col, agg.AGG_ALL, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        by_dtype[dt] = round(n * esz / (a.elapsed_time(b) / reps * 1e-3) / 1e9, 1)
+        del col
+        torch.cuda.empty_cache()
     return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30 int32 rows (4 GiB)", "ms": round(ms, 4),
             "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
             "frac_of_nominal_8TBs": round(gbs / 8000.0, 4), "steps": steps,
-            "small_2p20_int32_us_per_call_back_to_back": round(small_us, 2)}
+            "small_2p20_int32_us_per_call_back_to_back": round(small_us, 2),
+            "GB/s_by_value_type_2p30_rows": by_dtype}
 
 
 def extra_batched(steps: int, nq: int = 512) -> dict:

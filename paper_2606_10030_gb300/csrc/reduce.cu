@@ -14,9 +14,9 @@
 //   integers  int64 sum (wraps mod 2^64), min and max in the value type;
 //   float32   TwoSum-compensated float32 pair (s, c), order-preserving
 //             uint32 images for min/max;
-//   float64   TwoSum-compensated float64 pair fed with plain sums of each
-//             iteration's 8 rows (GB300 issues few float64 operations), uint64
-//             images.
+//   float64   a 128-bit fixed-point integer at the scale of the largest
+//             exponent seen (integer operations only: GB300 issues few
+//             float64 operations), uint64 images for min/max.
 // Block partials carry the sum as a float64 pair (hi, lo); the final merge is
 // a float64 double-double sum in a fixed order, so the result is
 // deterministic for a given grid.
@@ -97,22 +97,114 @@ template <> struct FpImg<double> {
   __device__ static uint64_t widen(U m) { return m; }
 };
 
+// float64 SUM on the integer pipes: a 128-bit two's-complement fixed-point
+// number (hi:lo) scaled to the largest exponent field E seen so far, worth
+// (hi:lo) x 2^(E - 1075 - kFixGuard). A row with significand m (53 bits,
+// implicit bit included) and exponent field e >= 1 is worth m x 2^(e - 1075),
+// i.e. m shifted left by kFixGuard - (E - e) units. Rows more than kFixGuard
+// binades below E keep their bits above the unit (each loses less than
+// 2^(E - 1075 - kFixGuard)); a row with a larger exponent shifts the sum right
+// (again less than a unit lost). Sums of up to 2^27 rows per thread cannot
+// overflow (|m x 2^kFixGuard| < 2^100). Infinities and NaNs are added in
+// float64 on the side, so that a column holding one sums to a non-finite
+// value (which one is unspecified, as for the other float paths).
+// GB300 issues few float64 operations per clock (a TwoSum per row held the
+// float64 scan to 0.6 TB/s); this takes only integer operations per row.
+constexpr int kFixGuard = 47;
+
+struct Fix128 {
+  uint64_t lo, hi;
+  int E;
+  double special;
+  __device__ void init() {
+    lo = 0;
+    hi = 0;
+    E = 0;
+    special = 0.0;
+  }
+  __device__ __forceinline__ void rescale(int e) {  // e > E
+    const int k = e - E;
+    if (k >= 127) {
+      lo = (int64_t)hi < 0 ? ~0ull : 0ull;
+      hi = lo;
+    } else if (k >= 64) {
+      lo = (uint64_t)((int64_t)hi >> (k - 64));
+      hi = (uint64_t)((int64_t)hi >> 63);
+    } else {
+      lo = (lo >> k) | (hi << (64 - k));
+      hi = (uint64_t)((int64_t)hi >> k);
+    }
+    E = e;
+  }
+  __device__ __forceinline__ void add(uint64_t u) {
+    const int ef = (int)(u >> 52) & 0x7FF;
+    if (ef == 0x7FF) {  // infinity or NaN
+      special += __longlong_as_double((long long)u);
+      return;
+    }
+    const int e = ef > 0 ? ef : 1;  // subnormals: exponent 1, no implicit bit
+    const uint64_t m = (u & 0x000FFFFFFFFFFFFFull) | ((uint64_t)(ef > 0) << 52);
+    if (e > E) rescale(e);
+    const int d = E - e;
+    uint64_t vlo, vhi;
+    if (d <= kFixGuard) {
+      const int sh = kFixGuard - d;  // 0 .. kFixGuard
+      vlo = m << sh;
+      vhi = sh > 0 ? m >> (64 - sh) : 0ull;
+    } else {
+      const int r = d - kFixGuard;
+      vlo = r < 64 ? m >> r : 0ull;
+      vhi = 0ull;
+    }
+    if ((int64_t)u < 0) {  // two's-complement negation of vhi:vlo
+      vlo = ~vlo + 1ull;
+      vhi = ~vhi + (vlo == 0ull ? 1ull : 0ull);
+    }
+    lo += vlo;
+    hi += vhi + (lo < vlo ? 1ull : 0ull);
+  }
+  // The sum as an unevaluated float64 pair (rel. error about 2^-106 before
+  // scaling): the 128-bit integer in three chunks that float64 holds exactly,
+  // added with TwoSum, then scaled by 2^(E - 1075 - kFixGuard).
+  __device__ void to_pair(double& h, double& l) const {
+    const uint64_t m43 = (1ull << 43) - 1ull;
+    const double q0 = (double)(lo & m43);
+    const double q1 = (double)(((lo >> 43) | (hi << 21)) & m43);
+    const double q2 = (double)((int64_t)hi >> 22);
+    double s1, e1, s2, e2;
+    two_sum(ldexp(q2, 86), ldexp(q1, 43), s1, e1);
+    two_sum(s1, q0, s2, e2);
+    double t, f;
+    two_sum(s2, e1 + e2, t, f);
+    const int sc = E - 1075 - kFixGuard;
+    h = ldexp(t, sc) + special;
+    l = special == 0.0 ? ldexp(f, sc) : 0.0;
+  }
+};
+
 template <int DT, bool SUM, bool MM>
 struct Acc<DT, SUM, MM, true> {
   using T = typename Traits<DT>::T;
   using U = typename FpImg<T>::U;
-  T s, c;
+  static constexpr bool F64 = sizeof(T) == 8;
+  T s, c;       // float32: TwoSum-compensated pair
+  Fix128 fx;    // float64
   U mn, mx;
   __device__ void init() {
     s = 0; c = 0;
+    if (F64) fx.init();
     mn = (U)~(U)0; mx = 0;
   }
   __device__ __forceinline__ void fold(T v) {
     if (SUM) {
-      T t, e;
-      two_sum(s, v, t, e);
-      s = t;
-      c += e;
+      if (F64) {
+        fx.add((uint64_t)__double_as_longlong((double)v));
+      } else {
+        T t, e;
+        two_sum(s, v, t, e);
+        s = t;
+        c += e;
+      }
     }
     if (MM) {
       U m = FpImg<T>::img(v);
@@ -129,40 +221,14 @@ struct Acc<DT, SUM, MM, true> {
       fold(__longlong_as_double((long long)(((uint64_t)r.w << 32) | r.z)));
     }
   }
-  // float64 SUM over the K vectors of one loop iteration (2K rows; a vector
-  // past the end is all zero bits, i.e. +0.0, which adds nothing): the rows
-  // are added plainly in a fixed tree and the group's sum enters (s, c) with
-  // one TwoSum. That is a quarter of the float64 operations of a TwoSum per
-  // row (GB300 issues few float64 operations per clock); the plain additions
-  // add at most (2K - 1) 2^-53 sum|x| of error, far inside the bound of the
-  // result. MIN/MAX take only the valid vectors.
-  template <int K>
-  __device__ __forceinline__ void fold_group(const uint4 (&r)[K], const bool (&ok)[K]) {
-    double g[K];
-#pragma unroll
-    for (int u = 0; u < K; ++u) {
-      const double x0 = __longlong_as_double((long long)(((uint64_t)r[u].y << 32) | r[u].x));
-      const double x1 = __longlong_as_double((long long)(((uint64_t)r[u].w << 32) | r[u].z));
-      g[u] = x0 + x1;
-      if (MM && ok[u]) {
-        const U m0 = FpImg<T>::img(x0), m1 = FpImg<T>::img(x1);
-        mn = min(mn, min(m0, m1));
-        mx = max(mx, max(m0, m1));
-      }
-    }
-#pragma unroll
-    for (int w = 1; w < K; w <<= 1)
-#pragma unroll
-      for (int u = 0; u + w < K; u += 2 * w) g[u] += g[u + w];
-    T t, e;
-    two_sum(s, (T)g[0], t, e);
-    s = t;
-    c += e;
-  }
   __device__ void to_partial(Partial& p) const {
     p.si = 0;
-    p.hi = (double)s;
-    p.lo = (double)c;
+    if (F64 && SUM) {
+      fx.to_pair(p.hi, p.lo);
+    } else {
+      p.hi = (double)s;
+      p.lo = (double)c;
+    }
     p.mn = FpImg<T>::widen(mn);
     p.mx = FpImg<T>::widen(mx);
   }
@@ -283,16 +349,9 @@ __global__ void __launch_bounds__(kBlock) reduce_scan(const typename Traits<DT>:
         const int64_t i = base + (int64_t)u * kBlock;
         r[u] = i < nv ? ld_stream_v4(v + i) : make_uint4(0, 0, 0, 0);
       }
-      if constexpr (DT == AGG_F64 && SUM) {
-        bool ok[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) ok[u] = base + (int64_t)u * kBlock < nv;
-        a.fold_group(r, ok);
-      } else {
-#pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          if (base + (int64_t)u * kBlock < nv) a.fold_vec(r[u]);
-        }
+      for (int u = 0; u < kUnroll; ++u) {
+        if (base + (int64_t)u * kBlock < nv) a.fold_vec(r[u]);
       }
     }
   }

@@ -132,6 +132,29 @@ def test_compensated_sum_wide_exponents(dt):
     assert abs(got["sum"] - 0.25) <= 1e-6 * max(0.25, 2.0 ** -24 * float(np.abs(y.astype(np.float64)).sum()))
 
 
+@pytest.mark.parametrize("case", ["subnormal", "extreme_exponents", "tiny_beside_huge", "near_max"])
+def test_float64_sum_edge_cases(case):
+    """The float64 sum is kept as a 128-bit fixed-point number at the scale of the
+    largest exponent: subnormal rows, exponents across the whole range, rows far
+    below the largest, and sums near the top of the range."""
+    rng = np.random.default_rng(5)
+    n = 100_003
+    if case == "subnormal":
+        x = rng.integers(1, 1000, n).astype(np.float64) * 5e-324 * rng.choice([-1.0, 1.0], n)
+    elif case == "extreme_exponents":
+        x = rng.standard_normal(n) * np.exp2(rng.integers(-1020, 1000, n).astype(np.float64))
+    elif case == "tiny_beside_huge":
+        x = np.concatenate([np.full(1000, 1e300), rng.standard_normal(5000), np.full(1000, -1e300)])
+    else:
+        x = np.full(4096, 1.7e308 / 8192) * rng.choice([0.5, 1.0], 4096)
+    check(run_dev(x), x)
+
+
+def test_float64_sum_of_a_column_with_an_infinity_is_not_finite():
+    x = np.concatenate([np.ones(5000), [np.inf], np.ones(3000)])
+    assert not math.isfinite(run_dev(x, agg.AGG_SUM)["sum"])
+
+
 @pytest.mark.parametrize("dt", [np.float32, np.float64])
 def test_fp_sum_is_deterministic(dt):
     t = torch.from_numpy(make(dt, 5_000_000, seed=1)).cuda()
