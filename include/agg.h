@@ -150,8 +150,23 @@ typedef struct agg_options {
                               shared tables would spill or the global table exceeds half of L2; two
                               levels above ~600k distinct keys), 1 = one level (256 partitions),
                               2 = two levels (65536 partitions), -1 = never */
-  int32_t reserved[2];
+  int32_t flags;           /* AGG_FLAG_* bits; 0 = none */
+  int32_t reserved;        /* must be 0 */
 } agg_options;
+
+/*
+ * AGG_FLAG_EXACT_SUM -- float columns: every group's SUM is the exact real sum
+ * of its rows rounded once to float64 (to nearest, ties to even) and AVG that
+ * sum divided by the count, so the result is identical bit for bit across
+ * strategies, grids and runs. After the strategy has built the groups, the
+ * rows are added again as integers in units of the column's lowest exponent
+ * (base-2^28 digits per group, as many as the column's exponent span needs;
+ * at most 84 x 8 bytes per group), with one extra pass over the column and a
+ * read-back. AGG_ERR_INVALID if the column holds an infinity or a NaN, and
+ * from agg_groupby_host (the pass reads the device columns). Integer columns
+ * ignore the flag (their sums are exact).
+ */
+#define AGG_FLAG_EXACT_SUM 1
 
 /*
  * GROUP BY result, owned by the library (free with agg_groups_free).

@@ -20,6 +20,7 @@ LIB_PATH = os.path.join(_PKG, "libagg.so")
 AGG_I32, AGG_I64, AGG_U32, AGG_F32, AGG_F64 = range(5)
 AGG_SUM, AGG_MIN, AGG_MAX, AGG_COUNT, AGG_AVG = 1, 2, 4, 8, 16
 AGG_ALL = 31
+AGG_FLAG_EXACT_SUM = 1  # options(flags=...): exactly rounded float sums, identical across strategies
 AGG_OK, AGG_ERR_INVALID, AGG_ERR_OOM, AGG_ERR_CUDA, AGG_ERR_TABLE_FULL, AGG_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 
 DTYPE_NAMES = {AGG_I32: "i32", AGG_I64: "i64", AGG_U32: "u32", AGG_F32: "f32", AGG_F64: "f64"}
@@ -79,7 +80,8 @@ class AggOptions(ctypes.Structure):
         ("sample_offset", ctypes.c_uint64),
         ("items_per_thread", ctypes.c_int32),
         ("partition", ctypes.c_int32),
-        ("reserved", ctypes.c_int32 * 2),
+        ("flags", ctypes.c_int32),
+        ("reserved", ctypes.c_int32),
     ]
 
 

@@ -700,11 +700,24 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
 
 }  // namespace agg
 
+namespace agg {
+agg_status exact_fp_sums(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
+                         agg_groups* g, cudaStream_t s);
+}
+
 static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
                                const agg_options* opt, cudaStream_t s, agg_groups** out) {
   agg_options o{};
   if (opt) o = *opt;
-  return groupby_with(keys, vals, n, vdt, ops, o, s, out, nullptr);
+  agg_status st = groupby_with(keys, vals, n, vdt, ops, o, s, out, nullptr);
+  if (st == AGG_OK && (o.flags & AGG_FLAG_EXACT_SUM) && dtype_is_fp(vdt) && (ops & (AGG_SUM | AGG_AVG))) {
+    st = exact_fp_sums(keys, vals, n, vdt, ops, *out, s);
+    if (st != AGG_OK) {
+      agg_groups_free(*out);
+      *out = nullptr;
+    }
+  }
+  return st;
 }
 
 // ---------------------------------------------------------------------------
@@ -925,6 +938,7 @@ static agg_status check_groupby_args(const uint32_t* keys, const void* vals, int
                                                opt->block_threads % 32 == 0),
                   "block_threads must be 0 or a multiple of 32 in [64, 1024]");
     AGG_CHECK_ARG(opt->blocks_per_sm >= 0, "blocks_per_sm must be >= 0");
+    AGG_CHECK_ARG((opt->flags & ~AGG_FLAG_EXACT_SUM) == 0, "unknown flags 0x%x", (unsigned)opt->flags);
   }
   return AGG_OK;
 }
@@ -978,6 +992,8 @@ extern "C" agg_status agg_groupby_host(const uint32_t* keys_host, const void* va
   clear_error();
   agg_status st = check_groupby_args(keys_host, vals_host, n, vdtype, ops, opt, out);
   if (st != AGG_OK) return st;
+  AGG_CHECK_ARG(!opt || !(opt->flags & AGG_FLAG_EXACT_SUM),
+                "AGG_FLAG_EXACT_SUM needs device columns (agg_groupby)");
   *out = nullptr;
   return groupby_host_impl(keys_host, vals_host, n, vdtype, ops, opt, (cudaStream_t)stream, out);
 }
