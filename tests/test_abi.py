@@ -79,6 +79,13 @@ def test_groupby_batch_and_network_reject_bad_arguments_without_launching(L):
         o = agg.options(**bad) if "strategy" not in bad else agg.options(bad["strategy"])
         assert L.agg_groupby(k, v, 10, agg.AGG_I32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
                              None) == agg.AGG_ERR_INVALID, bad
+    o = agg.options(flags=2)
+    assert L.agg_groupby(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
+                         None) == agg.AGG_ERR_INVALID
+    assert "flags" in agg.last_error()
+    o = agg.options(flags=agg.AGG_FLAG_EXACT_SUM)  # the exact float sums read device columns
+    assert L.agg_groupby_host(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
+                              None) == agg.AGG_ERR_INVALID
     assert L.agg_groupby_host(k, v, 10, 9, agg.AGG_SUM, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
     assert L.agg_sketch(k, 10, 9, agg.AGG_SUM, 0, v, None) == agg.AGG_ERR_INVALID
     assert L.agg_sketch(k, 10, agg.AGG_I32, agg.AGG_SUM, 0, None, None) == agg.AGG_ERR_INVALID
