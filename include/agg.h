@@ -256,7 +256,7 @@ agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uin
                       uint64_t sample_offset, float* features_dev, void* stream);
 
 /*
- * Batched GROUP BY (step a9): many independent queries in one persistent
+ * Batched GROUP BY: many independent queries in one persistent
  * kernel captured in a CUDA graph.
  *
  * agg_batch_plan_create sketches every query (one batched launch), picks each
@@ -296,7 +296,7 @@ void agg_batch_plan_free(agg_batch_plan* plan);
 agg_status agg_batch(const agg_query* queries, int nq, agg_groups** outs, void* stream);
 
 /*
- * Autotuner (step a8; the paper's related work tunes the configuration
+ * Autotuner (the paper's related work tunes the configuration
  * parameters of GPU hash group-by, Sec. 7). Candidates: SMEM with the
  * sketch-sized and the largest shared table at 256 and 512 threads, GLOBAL at
  * 256 and 512 threads, and SORT. Each is run on the actual query and timed
@@ -328,7 +328,7 @@ agg_status agg_autotune_save(const char* path);
 agg_status agg_autotune_load(const char* path);
 
 /*
- * Learned strategy selector (step a11): an MLP 16 -> 64 -> 64 -> 3 (ReLU,
+ * Learned strategy selector: an MLP 16 -> 64 -> 64 -> 3 (ReLU,
  * softmax) over the standardised sketch features, classes 0 = SMEM,
  * 1 = GLOBAL, 2 = SORT, trained on the GPU by these kernels from the
  * autotuner's timings (the related work of Sec. 7 models aggregation time to

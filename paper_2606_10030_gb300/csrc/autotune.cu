@@ -1,4 +1,4 @@
-// Autotuner (step a8): time the GROUP BY candidates on the actual query and
+// Autotuner: time the GROUP BY candidates on the actual query and
 // cache the fastest by query signature. The exhaustive pick also labels the
 // training data of the learned selector and measures its regret.
 #include <cmath>

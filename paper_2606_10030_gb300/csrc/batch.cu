@@ -1,4 +1,4 @@
-// Batched GROUP BY (step a9): many queries of uneven sizes, key
+// Batched GROUP BY: many queries of uneven sizes, key
 // distributions and value types in one persistent kernel, captured in a CUDA
 // graph.
 //

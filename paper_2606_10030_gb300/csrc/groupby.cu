@@ -1,4 +1,4 @@
-// GROUP BY driver (steps a5, a5g, a5s, a6, a7): sketch, strategy choice,
+// GROUP BY driver: sketch, strategy choice,
 // table sizing and regrowth, the single-query hash path, the host-fed
 // (end-to-end) path and the C entry points. The device code of the hash
 // strategies is in hashtab.cuh; the sort strategy in sortagg.cu.

@@ -1,4 +1,4 @@
-// Device side of the hash GROUP BY (steps a5, a5g, a6), shared by the
+// Device side of the hash GROUP BY (build and finalisation), shared by the
 // single-query driver (groupby.cu) and the batched persistent kernel
 // (batch.cu): slot layouts, shared- and global-table probing and updates, the
 // build kernel and the finalise kernels.

@@ -1,4 +1,4 @@
-// Learned strategy selector (step a11): a 16 -> 64 -> 64 -> 3 MLP (ReLU,
+// Learned strategy selector: a 16 -> 64 -> 64 -> 3 MLP (ReLU,
 // softmax, cross-entropy) with hand-written forward, backward and Adam
 // kernels, trained on the GPU from the autotuner's labels. The paper's related
 // work models the processing time of aggregation to choose a configuration

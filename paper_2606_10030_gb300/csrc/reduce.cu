@@ -1,4 +1,4 @@
-// Ungrouped aggregation: the column scan (steps a1-a4).
+// Ungrouped aggregation: the column scan, per-thread fold, block tree and grid merge.
 //
 // One fused kernel in the spirit of the paper's specialised GPU design
 // (Sec. 3.2, "GPU Optimizations"): the grid is a multiple of the SM count,

@@ -1,4 +1,4 @@
-// Key sketch (step a10): 16 features of a strided sample of m = min(n, 4096)
+// Key sketch: 16 features of a strided sample of m = min(n, 4096)
 // keys, computed by one block. The strategy selectors (the rule and the MLP)
 // read them; the global table is sized from the GEE distinct-count estimate
 // (Charikar, Chaudhuri, Motwani and Narasayya, PODS 2000).

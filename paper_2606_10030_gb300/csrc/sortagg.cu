@@ -1,4 +1,4 @@
-// GROUP BY by sorting (step a5s; the sort-based group-by of Sec. 7).
+// GROUP BY by sorting (the sort-based group-by of Sec. 7).
 //
 // 1. Stable LSD radix sort of the (key, value) pairs by key.
 // 2. seg_count: each warp owns a chunk of 512 consecutive sorted rows and
