@@ -116,7 +116,7 @@ agg_status agg_reduce(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t 
  * (Sec. 5.3: host-to-device transfer is part of the measured time).
  *
  *  col_host  host pointer to n elements (pinned memory gives full link
- *            bandwidth; pageable memory works but is staged by the driver).
+ *            bandwidth; pageable memory works but is staged by the CUDA driver).
  *  out_host  host pointer to one agg_scalar, valid when the call returns.
  *
  * The column is copied in chunks into a ring of device buffers on a copy
