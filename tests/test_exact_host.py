@@ -92,3 +92,19 @@ def test_digits_cover_the_exponent_span(lib):
     assert d <= 6  # 53 bits + 32 for the row count + a sign, in 28-bit digits, + 2
     _, d = host_sum(lib, np.array([5e-324, 1.7e308]))
     assert d <= 84
+
+
+@pytest.mark.parametrize("dt", [np.float64, np.float32])
+def test_exactly_rounded_on_random_columns(lib, dt):
+    """Random lengths, exponent ranges, signs and cancellations, each against the rational sum."""
+    rng = np.random.default_rng(2024 if dt == np.float64 else 2025)
+    lim = 1000 if dt == np.float64 else 120
+    for _ in range(150):
+        n = int(rng.integers(1, 400))
+        lo = int(rng.integers(-lim, lim))
+        hi = min(lim, lo + int(rng.integers(0, 200)))
+        x = (rng.standard_normal(n) * np.exp2(rng.integers(lo, hi + 1, n).astype(np.float64))).astype(dt)
+        if rng.random() < 0.3:  # cancel most of the column
+            x = np.concatenate([x, -x[: n // 2]])
+        got, _ = host_sum(lib, x)
+        assert same(got, exact(x)), (x.tolist(), got, exact(x))
