@@ -26,8 +26,11 @@
  *  - Integer SUM accumulates in int64 and wraps mod 2^64; uint32 values are
  *    zero-extended. It is exact and bit-identical for any reduction order.
  *  - Float SUM is returned in float64. Float32 columns are summed with
- *    TwoSum-compensated float32 partials whose final merge runs in float64;
- *    float64 columns with TwoSum-compensated float64 partials.
+ *    TwoSum-compensated float32 partials whose final merge runs in float64.
+ *    The ungrouped scan sums float64 columns per thread as 128-bit
+ *    fixed-point integers (scaled to the largest exponent the thread has
+ *    seen) and merges them as float64 pairs; GROUP BY adds float64 values in
+ *    float64.
  *  - MIN/MAX of floats use the total order -0.0 < +0.0; inputs hold no NaN.
  *  - AVG = (double)SUM / (double)COUNT.
  */
@@ -212,8 +215,10 @@ typedef struct agg_groups {
  * Synchronous: the call returns once the result is complete (it reads back
  * the group count and the table status). The strategy is chosen by `opt`
  * (AUTO when NULL) from a 16-feature sketch of 4096 strided keys. A global
- * table that fills up (AGG_ERR_TABLE_FULL inside) is regrown 4x and the build
- * repeated, until the table has 4n slots (or 2^31). Every strategy returns identical keys, counts,
+ * table that fills up (AGG_ERR_TABLE_FULL inside) is regrown and the build
+ * repeated: the next table holds twice the distinct keys the full build can
+ * have met, scaled from the rows it went through to all n rows (at least 4x
+ * the old table, at most 2n slots and 2^31). Every strategy returns identical keys, counts,
  * integer sums, min/max and integer averages; float sums and averages agree
  * within rounding (atomic order).
  * Errors: AGG_ERR_INVALID, AGG_ERR_OOM, AGG_ERR_CUDA, AGG_ERR_TABLE_FULL (the
@@ -235,7 +240,14 @@ agg_status agg_groupby_host(const uint32_t* keys_host, const void* vals_host, in
 agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* count, void* sum, void* min,
                               void* max, double* avg);
 
-/* Release a result (NULL is allowed). */
+/*
+ * Release a result (NULL is allowed). The result's device memory is returned
+ * in stream order on the stream passed to the call that produced it, so the
+ * call does not wait for the GPU: that stream must still exist, and work the
+ * caller queued on other streams that reads the arrays must be ordered before
+ * the stream's next work (or finished). Batch results release their share of
+ * the batch's output block.
+ */
 void agg_groups_free(agg_groups* g);
 
 /*
@@ -381,7 +393,11 @@ int agg_rule_strategy(const float* features_host, uint32_t ops);
  * a message; no call allocates (no cudaMalloc, cudaFree or allocating library
  * routine). The first call on a device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. All calls share the one array: each call clears
+ * before any stream capture, and before the caller reserves the device's
+ * memory for its own pool: under lazy module loading (the CUDA default) that
+ * first lookup, and the first launch of each scan kernel, can make the driver
+ * load the library's device code and this array into device memory. A warm-up
+ * call per value type right after loading the library does both. All calls share the one array: each call clears
  * the ticket it needs at zero, and calls whose work overlaps on the GPU (for
  * example on two streams) race on the array and give wrong results.
  */
@@ -413,6 +429,17 @@ enum {
   AGG_PHASES = 8
 };
 int64_t agg_launch_count(void);
+/*
+ * agg_stream_release -- drop the library's per-stream state of `stream` on
+ * the current device: the device scratch that agg_reduce, GROUP BY and the
+ * exact sums cache per (device, stream) (at least 1 MiB, kept until the
+ * process exits otherwise) is freed in stream order on `stream`, and the small
+ * pinned read-back buffer after the stream has drained. Call it before
+ * destroying a stream the library was used on: a later stream that received
+ * the same handle would otherwise inherit the old scratch. The next call on
+ * the stream allocates afresh. Errors: AGG_ERR_CUDA.
+ */
+agg_status agg_stream_release(void* stream);
 /* Test hook: the countdown-th device allocation the library makes from now on
    fails as if the device were out of memory (1 = the next one; 0 disables). */
 void agg_debug_fail_alloc(int64_t countdown);

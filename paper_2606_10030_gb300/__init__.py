@@ -172,6 +172,7 @@ SIGNATURES = {
     "agg_batch_plan_free": (None, [_vp]),
     "agg_batch": (_i32, [_vp, _i32, _vp, _vp]),
     "agg_launch_count": (ctypes.c_int64, []),
+    "agg_stream_release": (_i32, [_vp]),
     "agg_debug_fail_alloc": (None, [_i64]),
     "agg_profile_enable": (None, [_i32]),
     "agg_profile_read": (_i32, [_vp, _vp]),
@@ -363,6 +364,11 @@ def agg_sketch(keys, vdtype: int, ops: int = AGG_ALL, sample_offset: int = 0, ou
 
 
 PHASES = ["scan", "sketch", "build", "finalize", "sort", "segreduce", "batch", "mlp"]
+
+
+def agg_stream_release(stream) -> None:
+    """Free the library's cached scratch of a stream (call before the stream is destroyed)."""
+    check(lib().agg_stream_release(_stream_ptr(stream)))
 
 
 def launch_count() -> int:

@@ -19,8 +19,8 @@
 // of the group counts and table status follows the graph.
 //
 // The sort strategy needs whole-column passes that a tile queue cannot
-// interleave; in a batch, a query for which SORT is chosen runs on the global
-// hash table (identical results).
+// interleave; in a batch, a query for which SORT is chosen runs on
+// shared-memory tables that spill to its global table (identical results).
 #include <algorithm>
 #include <cmath>
 #include <cstring>

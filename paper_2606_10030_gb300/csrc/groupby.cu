@@ -203,6 +203,7 @@ agg_status groups_alloc(int64_t cap, int vdt, uint32_t ops, cudaStream_t s, agg_
   std::memset(g, 0, sizeof(*g));
   GroupsPriv* p = new GroupsPriv();
   p->block = blk;
+  p->stream = s;
   cudaGetDevice(&p->device);
   char* c = (char*)blk;
   g->keys = (uint32_t*)c;
@@ -979,8 +980,9 @@ extern "C" void agg_groups_free(agg_groups* g) {
     int cur = 0;
     cudaGetDevice(&cur);
     if (cur != p->device) cudaSetDevice(p->device);
-    cudaDeviceSynchronize();  // the block may still be in use by queued work
-    cudaFree(p->block);
+    // stream-ordered: work queued on the producing stream finishes first, and
+    // no other stream or the host has to wait
+    cudaFreeAsync(p->block, p->stream);
     if (cur != p->device) cudaSetDevice(cur);
     delete p;
   }

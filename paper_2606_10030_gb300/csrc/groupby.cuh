@@ -58,6 +58,7 @@ struct GroupsPriv {
   void* block = nullptr;          // one device allocation holding every output array
   SharedBlock* shared = nullptr;  // or a reference to a batch's output block
   int device = 0;
+  cudaStream_t stream = nullptr;  // stream the result was produced on (block freed there)
 };
 
 // Allocate a result with capacity for `cap` rows of every output array.

@@ -125,8 +125,12 @@ cudaError_t dev_malloc(void** p, size_t bytes) {
 
 // A small pinned host buffer per (device, stream) for reading a few result
 // words back without a pageable copy.
+namespace {
+std::map<std::pair<int, cudaStream_t>, Scratch> g_pinned;
+}  // namespace
+
 void* stream_pinned(cudaStream_t s, size_t bytes, agg_status* st) {
-  static std::map<std::pair<int, cudaStream_t>, Scratch> pinned;
+  auto& pinned = g_pinned;
   int dev = 0;
   cudaGetDevice(&dev);
   std::lock_guard<std::mutex> lk(g_mu);
@@ -202,6 +206,36 @@ PhaseTimer::~PhaseTimer() {
 }
 
 }  // namespace agg
+
+// Forget a stream: its device scratch is freed in stream order on the stream
+// itself, its pinned read-back buffer once the stream has drained.
+extern "C" agg_status agg_stream_release(void* stream) {
+  using namespace agg;
+  clear_error();
+  cudaStream_t s = (cudaStream_t)stream;
+  int dev = 0;
+  AGG_CUDA_TRY(cudaGetDevice(&dev));
+  Scratch sc, pin;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    auto it = g_scratch.find({dev, s});
+    if (it != g_scratch.end()) {
+      sc = it->second;
+      g_scratch.erase(it);
+    }
+    auto jt = g_pinned.find({dev, s});
+    if (jt != g_pinned.end()) {
+      pin = jt->second;
+      g_pinned.erase(jt);
+    }
+  }
+  if (sc.ptr) AGG_CUDA_TRY(cudaFreeAsync(sc.ptr, s));
+  if (pin.ptr) {
+    AGG_CUDA_TRY(cudaStreamSynchronize(s));
+    AGG_CUDA_TRY(cudaFreeHost(pin.ptr));
+  }
+  return AGG_OK;
+}
 
 extern "C" void agg_debug_fail_alloc(int64_t countdown) { agg::g_fail_countdown.store(countdown > 0 ? countdown : 0); }
 

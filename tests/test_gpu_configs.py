@@ -1,0 +1,113 @@
+"""GROUP BY at the full sizes of the benchmark workloads, against the CPU oracle.
+
+* 2^28 rows, uint32 keys Zipf(1.0) over 2^24 random keys, float32 values
+  N(0, 1) * 1e3, SUM/AVG: every one of the ~14 M groups of every strategy
+  against the oracle's full map (computed by key class on the host cores).
+* 2^30 rows, uint32 keys / int64 values, all five functions, on a table of
+  2^20 uniform keys and one of 2^26 keys at Zipf 0.5: the shared-memory,
+  global-hash and sort strategies return identical groups; selected groups
+  (the hottest and random ones, plus keys that do not occur) equal the
+  oracle's, and the groups add up to the oracle's ungrouped COUNT, SUM, MIN
+  and MAX of the column.
+"""
+import numpy as np
+import pytest
+import torch
+
+import datagen as dg
+import paper_2606_10030_gb300 as agg
+from datagen import cuda as dgc
+from tests import oracle_par
+from tests.common import FP_REL
+
+pytestmark = pytest.mark.gpu
+
+HASH_SORT = [agg.AGG_STRAT_SMEM, agg.AGG_STRAT_GLOBAL, agg.AGG_STRAT_SORT]
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _build():
+    agg.build()
+    agg.lib()
+
+
+@pytest.fixture(scope="module")
+def zipf_2p28():
+    n, D = 1 << 28, 1 << 24
+    k = dgc.keys_zipf(n, D, 1.0, 0)
+    v = dgc.values("f32", n, 0)
+    ref = oracle_par.groupby(k.cpu().numpy(), v.cpu().numpy(), name="zipf1_2p28_f32_seed0")
+    yield k, v, ref
+    del k, v
+    torch.cuda.empty_cache()
+
+
+def _groups(k, v, ops, **kw):
+    g = agg.agg_groupby(k, v, ops, agg.options(**kw))
+    res = g.to_host()
+    res["strategy"] = g.strategy
+    g.free()
+    return res
+
+
+@pytest.mark.parametrize("strategy", [agg.AGG_STRAT_AUTO] + HASH_SORT)
+def test_2p28_rows_zipf_float32_every_group(zipf_2p28, strategy):
+    k, v, ref = zipf_2p28
+    res = _groups(k, v, agg.AGG_SUM | agg.AGG_AVG, strategy=strategy)
+    assert 0.5 * (1 << 24) < ref["keys"].size <= 1 << 24
+    assert np.array_equal(res["keys"], ref["keys"])
+    assert np.array_equal(res["count"], ref["count"])
+    bar = FP_REL * np.maximum(np.abs(ref["sum"]), 2.0 ** -24 * ref["abs_sum"])
+    err = np.abs(res["sum"] - ref["sum"])
+    assert np.all(err <= bar), float(np.max(err / np.maximum(bar, 1e-300)))
+    assert np.all(np.abs(res["avg"] - ref["avg"]) <= bar / ref["count"])
+
+
+def test_2p28_rows_zipf_float32_exact_sums_are_the_oracles(zipf_2p28):
+    k, v, ref = zipf_2p28
+    res = _groups(k, v, agg.AGG_SUM | agg.AGG_AVG, strategy=agg.AGG_STRAT_AUTO, flags=agg.AGG_FLAG_EXACT_SUM)
+    assert np.array_equal(res["keys"], ref["keys"])
+    assert np.array_equal(res["sum"].view(np.int64), ref["sum"].view(np.int64))
+    assert np.array_equal(res["avg"].view(np.int64), ref["avg"].view(np.int64))
+
+
+@pytest.mark.parametrize("D,s", [(1 << 20, 0.0), (1 << 26, 0.5)])
+def test_2p30_rows_int64_strategies_identical_and_oracle(D, s):
+    n, seed = 1 << 30, 31
+    q = dg.GroupQuery(n, D, s, "i64", agg.AGG_ALL, seed)
+    k, v = dgc.group_column(q)
+    fields = ("keys", "count", "sum", "min", "max", "avg")
+    first = None
+    for strategy in HASH_SORT + [agg.AGG_STRAT_AUTO]:
+        res = _groups(k, v, agg.AGG_ALL, strategy=strategy)
+        if strategy != agg.AGG_STRAT_AUTO:
+            assert res["strategy"] == strategy
+        if first is None:
+            first = res
+            continue
+        for f in fields:
+            assert np.array_equal(res[f].view(np.int64) if f == "avg" else res[f],
+                                  first[f].view(np.int64) if f == "avg" else first[f]), (strategy, f)
+        del res
+    del k, v
+    torch.cuda.empty_cache()
+    d = first["keys"].size
+    assert np.all(np.diff(first["keys"].astype(np.int64)) > 0)
+    assert int(first["count"].sum()) == n
+    rng = np.random.default_rng(seed)
+    hot = np.argsort(first["count"])[::-1][:32]
+    pick = np.unique(np.concatenate([hot, rng.integers(0, d, 224)]))
+    absent = dg.domain_keys(seed, np.arange(D, D + 8))  # domain keys past D never occur
+    ref = oracle_par.table_check(n, D, s, "i64", seed, np.concatenate([first["keys"][pick], absent]))
+    present = np.isin(ref["keys"], first["keys"])
+    assert np.all(ref["count"][~present] == 0)
+    at = np.searchsorted(first["keys"], ref["keys"][present])
+    for f in ("count", "sum", "min", "max"):
+        assert np.array_equal(first[f][at], ref[f][present]), f
+    assert np.array_equal(first["avg"][at].view(np.int64),
+                          (ref["sum"][present].astype(np.float64) / ref["count"][present]).view(np.int64))
+    tot = ref["total"]
+    assert tot["count"] == n
+    with np.errstate(over="ignore"):
+        assert int(first["sum"].view(np.uint64).sum(dtype=np.uint64)) == tot["sum"] % (1 << 64)
+    assert int(first["min"].min()) == tot["min"] and int(first["max"].max()) == tot["max"]

@@ -195,38 +195,6 @@ def test_config_2p26_rows_1024_keys_int64_bit_exact():
     check_groups(res, kh, vh, ops)
 
 
-def test_config_2p28_rows_zipf_float32_sampled():
-    """2^28 rows, keys Zipf(1.0) over 2^24 random keys, float32 N(0,1)*1e3, SUM/AVG.
-    Checked on sampled groups against the oracle (hot keys and random ones) and on
-    properties that hold at any size."""
-    from datagen import cuda as dgc
-    n, D = 1 << 28, 1 << 24
-    k = dgc.keys_zipf(n, D, 1.0, 0)
-    v = dgc.values("f32", n, 0)
-    ops = agg.AGG_SUM | agg.AGG_AVG
-    g = agg.agg_groupby(k, v, ops)
-    res = g.to_host()
-    g.free()
-    d = res["keys"].size
-    assert 0.5 * D < d <= D
-    assert np.all(np.diff(res["keys"].astype(np.int64)) > 0)
-    assert res["count"].sum() == n
-    kh, vh = k.cpu().numpy(), v.cpu().numpy()
-    total = oracle.exact_sum(vh)
-    abs_total = float(np.abs(vh.astype(np.float64)).sum())
-    assert abs(res["sum"].sum() - total) <= FP_REL * max(abs(total), 2.0 ** -24 * abs_total) + 1e-9 * abs_total
-    rng = np.random.default_rng(0)
-    hot = np.argsort(res["count"])[::-1][:40]
-    pick = np.unique(np.concatenate([hot, rng.integers(0, d, 160)]))
-    sel = res["keys"][pick]
-    ref = oracle.groupby_selected(kh, vh, sel)
-    refa = oracle.groupby_selected(kh, np.abs(vh), sel)
-    assert np.array_equal(ref.keys, sel) and np.array_equal(ref.count, res["count"][pick])
-    bar = FP_REL * np.maximum(np.abs(ref.sum), 2.0 ** -24 * refa.sum)
-    assert np.all(np.abs(res["sum"][pick] - ref.sum) <= bar)
-    assert np.all(np.abs(res["avg"][pick] - ref.avg) <= bar / ref.count)
-
-
 @pytest.mark.parametrize("dt", ["i64", "f32"])
 @pytest.mark.parametrize("strategy", STRATS)
 def test_host_fed_groupby(dt, strategy):

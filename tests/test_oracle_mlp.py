@@ -74,3 +74,43 @@ def test_training_steps_reduce_the_loss():
         _, g = mlp.loss_and_grad(p, X, y)
         p, m, v = mlp.adam(p, g, m, v, t, lr=1e-2)
     assert mlp.loss(p, X, y) < 0.3 * L0
+
+
+def test_forward_on_hand_computed_network():
+    """A network worked out by hand, with one negative pre-activation in each
+    hidden layer, so that a dropped or misplaced ReLU changes the output.
+
+    x = (1, -2, 0, ..., 0)
+    layer 1: a1[0] = x0 + 0.5 = 1.5, a1[1] = x1 = -2 -> h1 = (1.5, 0, 0, ...)
+    layer 2: a2[0] = 2 h1[0] + 1 h1[1] = 3, a2[1] = -h1[0] = -1.5 -> h2 = (3, 0, ...)
+    layer 3: z = (h2[0], 5 h2[1] + ln 2, -h2[0]) = (3, ln 2, -3)
+    softmax: (e^3, 2, e^-3) / (e^3 + 2 + e^-3)
+    Without the first ReLU, a2[0] would be 3 - 2 = 1; without the second, z[1]
+    would be ln 2 - 7.5.
+    """
+    w = {name: np.zeros(shape) for name, shape in mlp.SHAPES}
+    w["W1"][0, 0] = 1.0
+    w["W1"][1, 1] = 1.0
+    w["b1"][0] = 0.5
+    w["W2"][0, 0] = 2.0
+    w["W2"][1, 0] = 1.0
+    w["W2"][0, 1] = -1.0
+    w["W3"][0, 0] = 1.0
+    w["W3"][1, 1] = 5.0
+    w["W3"][0, 2] = -1.0
+    w["b3"][1] = math.log(2.0)
+    p = mlp.pack(w)
+    X = np.zeros((1, 16))
+    X[0, 0], X[0, 1] = 1.0, -2.0
+    probs, c = mlp.forward(p, X)
+    den = math.exp(3) + 2.0 + math.exp(-3)
+    expect = np.array([math.exp(3) / den, 2.0 / den, math.exp(-3) / den])
+    assert np.allclose(probs[0], expect, rtol=1e-14, atol=0)
+    assert c["h1"][0, 1] == 0.0 and c["h2"][0, 1] == 0.0
+    # the loss of class 1 is -ln(2 / den)
+    assert abs(mlp.loss(p, X, np.array([1])) - (math.log(den) - math.log(2.0))) < 1e-14
+    # standardisation is applied before layer 1: x' = (x - mean) / std
+    mean = np.full(16, 1.0)
+    std = np.full(16, 2.0)
+    probs2, _ = mlp.forward(p, X * 2.0 + 1.0, mean, std)
+    assert np.allclose(probs2, probs, rtol=1e-14, atol=0)

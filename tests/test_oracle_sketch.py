@@ -70,3 +70,29 @@ def test_sample_positions_wrap_and_small_n():
 def test_empty():
     f = sketch(np.array([], dtype=np.uint32), **ARGS)
     assert f[1] == 8 and f[2] == 4 and f[0] == 0 and np.all(f[4:] == 0)
+
+
+def test_table_size_features_on_closed_form_cases():
+    """Features 13 and 14 compare the estimated table (2 x GEE slots of slot_bytes)
+    with shared memory and with L2. The byte counts below are chosen so that the
+    expected values are integers: a wrong slot size, a missing factor 2, or the
+    two memories swapped gives a different number."""
+    # constant column: GEE = 1, table = 2 * 1 * 32 = 64 bytes
+    args = dict(ARGS, smem_bytes=64.0, l2_bytes=64.0 / 7.0)
+    f = sketch(np.full(50000, 3, dtype=np.uint32), **args)
+    assert f[13] == 1.0            # log2(1 + 64 / 64)
+    assert f[14] == 3.0            # log2(1 + 64 / (64/7)) = log2(8)
+    # all sampled keys distinct with stride 1: GEE = m = 4096, table = 2 * 4096 * 32 = 2^18 bytes
+    args = dict(ARGS, smem_bytes=float(2 ** 18), l2_bytes=float(2 ** 18) / 3.0)
+    f = sketch(np.arange(SAMPLE, dtype=np.uint32), **args)
+    assert f[12] == 12.0
+    assert f[13] == 1.0            # log2(1 + 1)
+    assert f[14] == 2.0            # log2(1 + 3)
+    # n = 64 m distinct keys: GEE = 8 m = 2^15, table = 2^21 bytes; L2 of 2^21 / 15 bytes
+    args = dict(ARGS, slot_bytes=32, smem_bytes=float(2 ** 21) / 3.0, l2_bytes=float(2 ** 21) / 15.0)
+    f = sketch(np.arange(SAMPLE * 64, dtype=np.uint32), **args)
+    assert f[13] == 2.0 and f[14] == 4.0
+    # slot bytes enter linearly: 16-byte slots halve the table
+    args = dict(ARGS, slot_bytes=16, smem_bytes=float(2 ** 20), l2_bytes=float(2 ** 20) / 3.0)
+    f = sketch(np.arange(SAMPLE * 64, dtype=np.uint32), **args)
+    assert f[13] == 1.0 and f[14] == 2.0
