@@ -10,13 +10,22 @@ with the host-to-device copy inside the timed region.
 
 Workloads (synthetic, seeded; they stand in for the paper's TPC-H
 lineitem.suppkey scan, which is not available here):
-  groupby     (default) GROUP BY SUM/COUNT/MIN/MAX over 2^26 rows: uint32 keys
-              drawn uniformly from 1024 random keys, int64 values uniform in
-              [0, 2^32) (768 MiB of input)
+  table2p30   (default) GROUP BY SUM/MIN/MAX/COUNT/AVG over a 2^30-row table:
+              uint32 keys Zipf(1.0) over 2^16 random keys, int64 values uniform
+              in [0, 2^32) (12 GiB), strategy chosen by the learned selector
+  groupby     GROUP BY SUM/COUNT/MIN/MAX over 2^26 rows: uint32 keys drawn
+              uniformly from 1024 random keys, int64 values uniform in [0, 2^32)
   scan        ungrouped SUM/MIN/MAX/COUNT/AVG over a 2^30-row int32 column
               (4 GiB, uniform in [-2^20, 2^20))
-The default run also reports, as extra objects, the 2^30-row scan and the
-high-cardinality GROUP BY (2^28 rows, Zipf(1) keys over 2^24, float32 values).
+The default run also reports, as extra objects: the 2^26-row GROUP BY above;
+the 2^30-row scans of every value type (float sums with their error against
+the oracle); the high-cardinality GROUP BY (2^28 rows, Zipf(1) keys over 2^24,
+float32 values, with every group's error against the exactly rounded sum);
+the 512-query batch against plain per-query calls; and the selector's
+evaluation on 2^30-row tables over 2^4..2^26 keys x Zipf 0..1.5 (on-device
+GB/s, regret against the exhaustive autotuner, end-to-end GB/s on a few).
+The host-link peak (pinned host-to-device copies) is measured once and the
+end-to-end figure given as a fraction of it.
 
 Under torchrun each rank aggregates its own replica of the workload (weak
 scaling, no data-path collective); only the timing uses a MAX all-reduce.
@@ -146,6 +155,11 @@ class ScanWorkload:
     kernel = "reduce_scan"
     phase = "scan"
 
+    def release(self):
+        """Drop the workload's device and host columns."""
+        for a in ("col", "host", "k", "v", "hk", "hv"):
+            self.__dict__.pop(a, None)
+
     def config(self):
         return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30-row int32 column uniform in [-2^20, 2^20)",
                 "rows": self.n, "dtype": "int32", "input_bytes": self.n * self.esize,
@@ -210,6 +224,11 @@ class GroupbyWorkload:
     kernel = "gb_build"
     phase = "build"
 
+    def release(self):
+        """Drop the workload's device and host columns."""
+        for a in ("col", "host", "k", "v", "hk", "hv"):
+            self.__dict__.pop(a, None)
+
     def config(self):
         return {"workload": "GROUP BY SUM/COUNT/MIN/MAX, 2^26 rows, uint32 keys uniform over 1024 random keys, "
                             "int64 values uniform in [0, 2^32)",
@@ -272,7 +291,122 @@ class GroupbyWorkload:
         return rows, t_compute, f"oracle.groupby (std::map) over the first {rows} rows (2^24-row slices)"
 
 
-WORKLOADS = {"groupby": GroupbyWorkload, "scan": ScanWorkload}
+class Table2p30Workload:
+    """GROUP BY SUM/MIN/MAX/COUNT/AVG over a 2^30-row table: uint32 keys Zipf(1.0) over
+    2^16 random keys, int64 values uniform in [0, 2^32); the learned selector picks the
+    strategy (the AUTO rule if no trained weights are installed)."""
+    name = "table2p30"
+    n = 1 << 30
+    D = 1 << 16
+    zipf_s = 1.0
+    dtype = "i64"
+    esize = 12
+    kernel = None  # the phase with the largest share of the step
+
+    def release(self):
+        """Drop the workload's device and host columns."""
+        for a in ("col", "host", "k", "v", "hk", "hv"):
+            self.__dict__.pop(a, None)
+
+    def config(self):
+        return {"workload": "GROUP BY SUM/MIN/MAX/COUNT/AVG, 2^30 rows, uint32 keys Zipf(s=1.0) over D=2^16 random "
+                            "keys, int64 values uniform in [0, 2^32), strategy from the learned selector",
+                "rows": self.n, "distinct_keys_domain": self.D, "zipf_s": self.zipf_s, "key_dtype": "uint32",
+                "value_dtype": "int64", "input_bytes": self.n * self.esize,
+                "strategy": "learned" if self.learned else "auto (no trained weights)",
+                "l2": "input (12 GiB) larger than L2 (129 MB); no flush needed"}
+
+    def bytes_per_step(self):
+        return self.n * self.esize
+
+    def query(self, rank):
+        import datagen as dg
+        return dg.GroupQuery(self.n, self.D, self.zipf_s, self.dtype, 31, rank)
+
+    def setup(self, rank):
+        import torch
+
+        import paper_2606_10030_gb300 as agg
+        from datagen import cuda as dgc
+        from paper_2606_10030_gb300 import selector
+        self.agg = agg
+        self.learned = selector.install_default()
+        self.ops = agg.AGG_ALL
+        self.opts = agg.options(agg.AGG_STRAT_LEARNED if self.learned else agg.AGG_STRAT_AUTO)
+        self.q = self.query(rank)
+        self.k, self.v = dgc.group_column(self.q)
+        torch.cuda.synchronize()
+
+    def step(self):
+        g = self.agg.agg_groupby(self.k, self.v, self.ops, self.opts)
+        self.last_strategy = g.strategy
+        self.groups = g.num_groups
+        g.free()
+        return 0
+
+    def setup_e2e(self):
+        self.hk = self.k.cpu().pin_memory()
+        self.hv = self.v.cpu().pin_memory()
+
+    def step_e2e(self):
+        g = self.agg.agg_groupby_host(self.hk, self.hv, self.ops, self.opts)
+        r = g.to_host()
+        self.e2e_groups = len(r["keys"])
+        g.free()
+        return self.e2e_groups
+
+    def e2e_bytes(self):
+        return self.n * self.esize, getattr(self, "e2e_groups", self.D) * (4 + 5 * 8)
+
+    def cpu_sample(self, budget_s: float):
+        """Oracle GROUP BY on consecutive 2^24-row slices of the same table until budget_s elapses."""
+        import datagen as dg
+        import oracle
+        oracle.build()
+        q = self.query(0)
+        t = dg.zipf_thresholds(q.D, q.zipf_s)
+        rows, start, t_compute = 0, 0, 0.0
+        chunk = 1 << 24
+        t0 = time.perf_counter()
+        while time.perf_counter() - t0 < budget_s and start < self.n:
+            k = dg.keys_zipf(chunk, q.D, q.zipf_s, q.seed, start=start, thresholds=t)
+            v = dg.values(q.dtype, chunk, q.seed, start=start)
+            a = time.perf_counter()
+            oracle.groupby(k, v)
+            t_compute += time.perf_counter() - a
+            rows += chunk
+            start += chunk
+        return rows, t_compute, f"oracle.groupby (std::map) over the first {rows} rows (2^24-row slices)"
+
+
+WORKLOADS = {"table2p30": Table2p30Workload, "groupby": GroupbyWorkload, "scan": ScanWorkload}
+
+# phase of the library's event timers -> the kernels it times
+PHASE_KERNELS = {"scan": "reduce_scan", "sketch": "sketch_gather + sketch_kernel",
+                 "build": "gb_build / gb_build_tiles (hash build)",
+                 "finalize": "gb_compact + key sort + gb_gather (finalise)",
+                 "sort": "radix_hist + radix_scatter (radix partition or sort pass)",
+                 "segreduce": "seg_reduce + seg_finalize", "batch": "batch_build", "mlp": "mlp kernels"}
+
+
+def host_link_peak(gib: int = 1, reps: int = 10) -> dict:
+    """Pinned host-to-device copy bandwidth (best of reps, CUDA events): the end-to-end roofline."""
+    import torch
+    n = gib << 30
+    h = torch.empty(n, dtype=torch.uint8).pin_memory()
+    d = torch.empty(n, dtype=torch.uint8, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    best = float("inf")
+    for _ in range(reps + 1):
+        a.record()
+        d.copy_(h, non_blocking=True)
+        b.record()
+        b.synchronize()
+        best = min(best, a.elapsed_time(b))
+    del h, d
+    torch.cuda.empty_cache()
+    return {"GB/s": round(n / (best * 1e-3) / 1e9, 1), "bytes": n, "reps": reps,
+            "how": "pinned host -> device copy of 1 GiB, best of 10, CUDA events"}
 
 
 def extra_scan(steps: int, peaks: dict) -> dict:
@@ -310,8 +444,11 @@ def extra_scan(steps: int, peaks: dict) -> dict:
     torch.cuda.synchronize()
     small_us = a.elapsed_time(b) / 1000 * 1e3
     del small
-    # the other value types, 2^30 rows each (int64 and float64: 8 GiB), all five ops
+    # the other value types, 2^30 rows each (int64 and float64: 8 GiB), all five ops;
+    # float sums: the error against the oracle's exactly rounded sum, and the bound the
+    # scan computes alongside the sum
     by_dtype = {"i32": round(gbs, 1)}
+    errors = {}
     for dt, esz in (("i64", 8), ("f32", 4), ("f64", 8)):
         col = dgc.values(dt, n, seed=0)
         for _ in range(3):
@@ -324,13 +461,30 @@ def extra_scan(steps: int, peaks: dict) -> dict:
         b.record()
         torch.cuda.synchronize()
         by_dtype[dt] = round(n * esz / (a.elapsed_time(b) / reps * 1e-3) / 1e9, 1)
+        if dt in ("f32", "f64"):
+            r = agg.decode_scalar(out)
+            errors[dt] = float_sum_error(r.sum_f, r.err_bound, col)
         del col
         torch.cuda.empty_cache()
     return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^30 int32 rows (4 GiB)", "ms": round(ms, 4),
             "GB/s": round(gbs, 1), "frac_of_measured_hbm": round(gbs / peaks["hbm_gbs"], 4),
             "frac_of_nominal_8TBs": round(gbs / 8000.0, 4), "steps": steps,
             "small_2p20_int32_us_per_call_back_to_back": round(small_us, 2),
-            "GB/s_by_value_type_2p30_rows": by_dtype}
+            "GB/s_by_value_type_2p30_rows": by_dtype, "float_sum_error_vs_oracle": errors}
+
+
+def float_sum_error(got: float, bound: float, col) -> dict:
+    """Error of a float column's SUM against the oracle's exactly rounded sum."""
+    import numpy as np
+
+    import oracle
+    x = col.cpu().numpy()
+    ref = oracle.exact_sum(x)
+    abs_sum = float(np.abs(x.astype(np.float64)).sum())
+    err = abs(got - ref)
+    return {"abs_err": err, "rel_err": err / abs(ref) if ref else err,
+            "err_bound": bound, "err_bound_rel": bound / abs(ref) if ref else bound,
+            "bar": 1e-6 * max(abs(ref), 2.0 ** -24 * abs_sum), "within_bar": err <= 1e-6 * max(abs(ref), 2.0 ** -24 * abs_sum)}
 
 
 def extra_batched(steps: int, nq: int = 512) -> dict:
@@ -359,21 +513,29 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
     plan_s = time.perf_counter() - t0
     plan.run()  # capture + first replay
     torch.cuda.synchronize()
+    agg.profile_read()
+    agg.profile_enable(True)
     t0 = time.perf_counter()
     for _ in range(steps):
         plan.run()
     torch.cuda.synchronize()
     batch_s = (time.perf_counter() - t0) / steps
+    agg.profile_enable(False)
+    batch_gpu_ms = sum(v[0] for v in agg.profile_read().values()) / steps
     plan.free()
     o = agg.options(strat)
     for k, v, ops in cols[:8]:
         agg.agg_groupby(k, v, ops, o).free()
     torch.cuda.synchronize()
+    agg.profile_read()
+    agg.profile_enable(True)
     t0 = time.perf_counter()
     for k, v, ops in cols:
         agg.agg_groupby(k, v, ops, o).free()
     torch.cuda.synchronize()
     plain_s = time.perf_counter() - t0
+    agg.profile_enable(False)
+    plain_gpu_ms = sum(v[0] for v in agg.profile_read().values())
     del cols
     torch.cuda.empty_cache()
     return {"workload": f"{nq} GROUP BY queries, rows log-uniform in [2^12, 2^24], distinct keys log-uniform in "
@@ -382,11 +544,15 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
             "batched_ms": round(batch_s * 1e3, 3), "batched_GB/s": round(in_bytes / batch_s / 1e9, 1),
             "batched_plan_ms": round(plan_s * 1e3, 1),
             "plain_ms": round(plain_s * 1e3, 3), "plain_GB/s": round(in_bytes / plain_s / 1e9, 1),
-            "speedup": round(plain_s / batch_s, 2), "steps": steps}
+            "speedup": round(plain_s / batch_s, 2),
+            "gpu_ms": {"batched": round(batch_gpu_ms, 3), "plain": round(plain_gpu_ms, 3),
+                       "how": "sum of the library's per-phase CUDA-event times (kernels only)"},
+            "steps": steps}
 
 
 def extra_zipf(steps: int) -> dict:
     """GROUP BY SUM/AVG, 2^28 rows, Zipf(1) keys over 2^24 random keys, float32 N(0,1)*1e3."""
+    import numpy as np
     import torch
 
     import paper_2606_10030_gb300 as agg
@@ -411,11 +577,69 @@ def extra_zipf(steps: int) -> dict:
         torch.cuda.synchronize()
         ms = (time.perf_counter() - t0) * 1e3 / steps
         res[name] = {"ms": round(ms, 3), "GB/s": round(n * 8 / (ms * 1e-3) / 1e9, 1)}
+        # every group's error against its exactly rounded sum (one extra pass, untimed)
+        g = agg.agg_groupby(k, v, ops, agg.options(strat, flags=agg.AGG_FLAG_SUM_ERROR))
+        r = g.to_host()
+        g.free()
+        nz = np.abs(r["sum"]) > 0
+        rel = r["sum_err"][nz] / np.abs(r["sum"][nz])
+        res[name]["sum_error"] = {"groups": int(r["keys"].size), "max_abs_err": float(r["sum_err"].max()),
+                                  "max_rel_err": float(rel.max()), "groups_rel_err_over_1e-6": int((rel > 1e-6).sum())}
     del k, v
     torch.cuda.empty_cache()
     return {"workload": "GROUP BY SUM/AVG, 2^28 rows, Zipf(1.0) keys over 2^24, float32 values",
             "groups": d, "auto_strategy": strategy, "per_strategy": res, "steps": steps}
 
+
+
+def extra_groupby_2p26(steps: int, peaks: dict) -> dict:
+    """GROUP BY SUM/COUNT/MIN/MAX, 2^26 rows over 1024 uniform keys, int64 values: the step and its build kernel."""
+    import torch
+
+    import paper_2606_10030_gb300 as agg
+    W = GroupbyWorkload()
+    W.setup(0)
+    for _ in range(5):
+        W.step()
+    torch.cuda.synchronize()
+    agg.profile_read()
+    agg.profile_enable(True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(steps):
+        W.step()
+    b.record()
+    torch.cuda.synchronize()
+    prof = agg.profile_read()
+    agg.profile_enable(False)
+    ms = a.elapsed_time(b) / steps
+    build_ms = prof["build"][0] / max(1, prof["build"][1])
+    by = W.bytes_per_step()
+    del W
+    torch.cuda.empty_cache()
+    return {"workload": GroupbyWorkload().config()["workload"], "ms": round(ms, 4),
+            "GB/s": round(by / (ms * 1e-3) / 1e9, 1), "frac_of_measured_hbm": round(by / (ms * 1e-3) / 1e9 /
+                                                                                      peaks["hbm_gbs"], 4),
+            "build_kernel": "gb_build", "build_ms": round(build_ms, 4),
+            "build_GB/s": round(by / (build_ms * 1e-3) / 1e9, 1),
+            "build_frac_of_measured_hbm": round(by / (build_ms * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+            "phases_ms_per_step": {k: round(v[0] / steps, 4) for k, v in prof.items() if v[1]}, "steps": steps}
+
+
+def extra_table_grid(link: dict) -> dict:
+    """The learned selector on 2^30-row uint32/int64 tables, 2^4..2^26 keys x Zipf 0..1.5:
+    on-device GB/s of its choice, regret against the exhaustive autotuner (and the AUTO
+    rule's), end-to-end GB/s from pinned host memory on four tables."""
+    from paper_2606_10030_gb300 import selector
+    if not selector.install_default():
+        return {"skipped": "no trained selector weights"}
+    ev = selector.evaluate_large(30, e2e_tables=4, log=lambda *a: None)
+    for r in ev["tables"]:
+        if "e2e_GBps" in r:
+            r["e2e_frac_of_link"] = round(r["e2e_GBps"] / link["GB/s"], 4)
+    ev["workload"] = ("GROUP BY SUM/MIN/MAX/COUNT/AVG over 2^30-row tables, uint32 keys over D = 2^4, 2^6, ..., "
+                      "2^26 random keys, uniform or Zipf s in {0.5, 1.0, 1.5}, int64 values; one table per (D, s)")
+    return ev
 
 
 def kernel_traffic(kernel: str, workload: str):
@@ -480,7 +704,10 @@ def run_ours(args):
     clocks = sampler.stop()
     ms = t0.elapsed_time(t1)
     ms = max_over_ranks(ms, world)
-    ph_ms, ph_calls = prof.get(W.phase, (0.0, 0))
+    # the dominant kernel: the workload's, or the phase with the largest share of the step
+    phase = W.phase if W.kernel else max(prof, key=lambda k: prof[k][0])
+    kernel = W.kernel or PHASE_KERNELS.get(phase, phase)
+    ph_ms, ph_calls = prof.get(phase, (0.0, 0))
     if ph_calls == 0:  # a strategy without this phase: time the whole step
         ph_ms, ph_calls = ms, args.steps
     per_launch_ms = ph_ms / max(1, ph_calls)
@@ -500,12 +727,18 @@ def run_ours(args):
     e2e_s = max_over_ranks(time.perf_counter() - a, world)
     h2d, d2h = W.e2e_bytes()
     e2e_value = world * h2d * e2e_steps / e2e_s / 1e9
+    strategy = agg.STRATEGY_NAMES.get(getattr(W, "last_strategy", -1), None)
+    W.release()
+    torch.cuda.empty_cache()
+    link = host_link_peak()
 
     extra = {}
-    if rank == 0 and world == 1 and not args.no_extra and W.name == "groupby":
+    if rank == 0 and world == 1 and not args.no_extra and W.name == "table2p30":
+        extra["groupby_2p26"] = extra_groupby_2p26(200, peaks)
         extra["scan"] = extra_scan(200, peaks)
         extra["zipf"] = extra_zipf(5)
         extra["batched"] = extra_batched(5)
+        extra["table2p30_grid"] = extra_table_grid(link)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rows, t, sample = W.cpu_sample(args.cpu_budget)
@@ -518,10 +751,14 @@ def run_ours(args):
             "config": W.config(),
             "rows_per_s": world * W.n * args.steps / (ms * 1e-3),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": kernel_traffic(W.kernel, W.name),
-                         "kernel": W.kernel, "peak_source": peaks["source"] + " (hbm_gbs, burst copy)"},
+                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": kernel_traffic(kernel, W.name),
+                         "kernel": kernel, "phase": phase, "strategy": strategy,
+                         "ms_per_launch": round(per_launch_ms, 4),
+                         "achieved_how": "input bytes of the step / mean CUDA-event time of the phase per launch",
+                         "peak_source": peaks["source"] + " (hbm_gbs, burst copy)"},
             "e2e": {"value": round(e2e_value, 2), "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "steps": e2e_steps},
+                    "steps": e2e_steps, "link_peak_GB/s": link["GB/s"],
+                    "frac_of_link": round(e2e_value / world / link["GB/s"], 4), "link_how": link["how"]},
             "gpu_launches": launches,
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
             "extra": extra,
@@ -565,7 +802,7 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=5)
-    ap.add_argument("--workload", default="groupby", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="table2p30", choices=sorted(WORKLOADS))
     ap.add_argument("--no-extra", action="store_true", help="skip the extra scan and Zipf measurements")
     ap.add_argument("--strategy", type=int, default=0, help="GROUP BY strategy (0 auto, 1 smem, 2 global, 3 sort)")
     ap.add_argument("--ops", type=int, default=0, help="override the ops bitmask (diagnostics)")

@@ -77,6 +77,14 @@ typedef enum {
  * min_f / max_f. sum_f of an integer column is (double)sum_i. Fields of
  * functions not requested in `ops` are unspecified, except count, which is
  * always n.
+ * err_bound: for a float column with SUM or AVG requested, a bound computed on
+ * the device, alongside the sum, on |sum_f - S| where S is the exact real sum
+ * of the column rounded once to float64 (the value of the FP64 reference):
+ * it adds up every rounding the scan can make (the compensation words of the
+ * float32 pairs, the truncations of the float64 fixed-point sums, the merges
+ * of block partials, the final rounding) and S's own rounding. It is +inf
+ * when the column holds an infinity or a NaN, and 0 for integer columns
+ * (their sums are exact). It bounds SUM only, not AVG.
  */
 typedef struct agg_scalar {
   int64_t count;
@@ -89,7 +97,7 @@ typedef struct agg_scalar {
   double max_f;
   uint32_t dtype;
   uint32_t ops;
-  int64_t reserved;
+  double err_bound;
 } agg_scalar;
 
 /*
@@ -172,6 +180,18 @@ typedef struct agg_options {
 #define AGG_FLAG_EXACT_SUM 1
 
 /*
+ * AGG_FLAG_SUM_ERROR -- float columns: report, for every group, the error of
+ * its SUM against the FP64 reference. sum_err[i] = |sum[i] - S_i| where S_i is
+ * the exact real sum of the group's rows rounded once to float64 (the value
+ * the FP64 oracle defines). S_i is computed as for AGG_FLAG_EXACT_SUM (one
+ * more pass over the column), but the strategy's own sums are kept; with both
+ * flags the sums are exact and every sum_err is 0. AGG_ERR_INVALID for a
+ * column holding an infinity or a NaN, and from agg_groupby_host. Integer
+ * columns ignore the flag (their sums are exact; sum_err stays NULL).
+ */
+#define AGG_FLAG_SUM_ERROR 2
+
+/*
  * GROUP BY result, owned by the library (free with agg_groups_free).
  * Rows are in ascending key order, one per distinct key present. Arrays are
  * device memory of num_groups elements each:
@@ -197,6 +217,7 @@ typedef struct agg_groups {
   void* min;
   void* max;
   double* avg;
+  double* sum_err;         /* |sum - exactly rounded sum| per group with AGG_FLAG_SUM_ERROR, else NULL */
   float features[16];      /* key sketch used for the choice (zeros if none) */
   void* priv;
 } agg_groups;
@@ -236,9 +257,10 @@ agg_status agg_groupby(const uint32_t* keys_dev, const void* vals_dev, int64_t n
 agg_status agg_groupby_host(const uint32_t* keys_host, const void* vals_host, int64_t n, agg_dtype vdtype,
                             uint32_t ops, const agg_options* opt, agg_groups** out, void* stream);
 
-/* Copy a result's arrays to host buffers of num_groups elements (any may be NULL). Synchronous. */
+/* Copy a result's arrays to host buffers of num_groups elements (any may be
+   NULL; sum_err is copied only when the result has one). Synchronous. */
 agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* count, void* sum, void* min,
-                              void* max, double* avg);
+                              void* max, double* avg, double* sum_err);
 
 /*
  * Release a result (NULL is allowed). The result's device memory is returned
@@ -387,8 +409,8 @@ int agg_rule_strategy(const float* features_host, uint32_t ops);
  * that cudaMalloc and cudaFree can imply. Arguments, results and errors are
  * those of agg_reduce; the caller still provides the column and out_dev.
  *
- * Scratch: a static device array of 82,176 bytes (the ticket plus 2048 block
- * partials) that every GPU loading the library holds until the process exits.
+ * Scratch: a static device array of 98,560 bytes (the ticket plus 2048 block
+ * partials of 48 bytes) that every GPU loading the library holds until the process exits.
  * A launch that would need more blocks than that returns AGG_ERR_INVALID with
  * a message; no call allocates (no cudaMalloc, cudaFree or allocating library
  * routine). The first call on a device looks up the array's device address

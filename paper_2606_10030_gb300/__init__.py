@@ -21,6 +21,7 @@ AGG_I32, AGG_I64, AGG_U32, AGG_F32, AGG_F64 = range(5)
 AGG_SUM, AGG_MIN, AGG_MAX, AGG_COUNT, AGG_AVG = 1, 2, 4, 8, 16
 AGG_ALL = 31
 AGG_FLAG_EXACT_SUM = 1  # options(flags=...): exactly rounded float sums, identical across strategies
+AGG_FLAG_SUM_ERROR = 2  # options(flags=...): per-group |sum - exactly rounded sum| in Groups.to_host()["sum_err"]
 AGG_OK, AGG_ERR_INVALID, AGG_ERR_OOM, AGG_ERR_CUDA, AGG_ERR_TABLE_FULL, AGG_ERR_TIMEOUT = 0, -1, -2, -3, -4, -5
 
 DTYPE_NAMES = {AGG_I32: "i32", AGG_I64: "i64", AGG_U32: "u32", AGG_F32: "f32", AGG_F64: "f64"}
@@ -47,7 +48,7 @@ class AggScalar(ctypes.Structure):
         ("max_f", ctypes.c_double),
         ("dtype", ctypes.c_uint32),
         ("ops", ctypes.c_uint32),
-        ("reserved", ctypes.c_int64),
+        ("err_bound", ctypes.c_double),
     ]
 
     def as_dict(self) -> dict:
@@ -132,6 +133,7 @@ class AggGroups(ctypes.Structure):
         ("min", ctypes.c_void_p),
         ("max", ctypes.c_void_p),
         ("avg", ctypes.c_void_p),
+        ("sum_err", ctypes.c_void_p),
         ("features", ctypes.c_float * 16),
         ("priv", ctypes.c_void_p),
     ]
@@ -146,7 +148,7 @@ SIGNATURES = {
     "agg_reduce_noalloc": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_groupby": (_i32, [_vp, _vp, _i64, _i32, _u32, _vp, _vp, _vp]),
     "agg_groupby_host": (_i32, [_vp, _vp, _i64, _i32, _u32, _vp, _vp, _vp]),
-    "agg_groups_to_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp]),
+    "agg_groups_to_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "agg_groups_free": (None, [_vp]),
     "agg_sketch": (_i32, [_vp, _i64, _i32, _u32, ctypes.c_uint64, _vp, _vp]),
     "agg_autotune": (_i32, [_vp, _vp, _i64, _i32, _u32, _i32, _vp, _vp]),
@@ -294,6 +296,7 @@ class Groups:
         self.retries = int(g.retries)
         self.table_slots = int(g.table_slots)
         self.smem_slots = int(g.smem_slots)
+        self.has_sum_err = bool(g.sum_err)
         self.features = np.array(list(g.features), dtype=np.float32)
 
     def to_host(self) -> dict:
@@ -305,9 +308,13 @@ class Groups:
         mn = np.empty(d, np.float64 if fp else np.int64)
         mx = np.empty(d, np.float64 if fp else np.int64)
         avg = np.empty(d, np.float64)
-        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
-        check(lib().agg_groups_to_host(self._ptr, p(keys), p(count), p(s), p(mn), p(mx), p(avg)))
-        return {"keys": keys, "count": count, "sum": s, "min": mn, "max": mx, "avg": avg}
+        err = np.empty(d, np.float64) if self.has_sum_err else None
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p) if a is not None else None  # noqa: E731
+        check(lib().agg_groups_to_host(self._ptr, p(keys), p(count), p(s), p(mn), p(mx), p(avg), p(err)))
+        out = {"keys": keys, "count": count, "sum": s, "min": mn, "max": mx, "avg": avg}
+        if err is not None:
+            out["sum_err"] = err
+        return out
 
     def free(self):
         if self._ptr:

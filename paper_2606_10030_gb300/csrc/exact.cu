@@ -1,4 +1,5 @@
-// Exactly rounded float GROUP BY sums (AGG_FLAG_EXACT_SUM).
+// Exactly rounded float GROUP BY sums (AGG_FLAG_EXACT_SUM), and the error of
+// the strategy's sums against them (AGG_FLAG_SUM_ERROR).
 //
 // Float sums built with atomics depend on the order in which rows arrive.
 // With this flag every group's SUM is the exact real sum of its rows rounded
@@ -17,8 +18,8 @@
 // for the row count), so a column of similar magnitudes needs a handful.
 #include <climits>
 
-#include "common.cuh"
 #include "exact.cuh"
+#include "groupby.cuh"
 
 namespace agg {
 
@@ -87,26 +88,41 @@ __global__ void __launch_bounds__(kExactThreads) exact_add(const uint32_t* __res
   }
 }
 
+// replace: write the exact sum (and avg) over the result's; err (nullable):
+// the distance of the sum the result keeps from the exact one.
 __global__ void __launch_bounds__(kExactThreads) exact_round_groups(const unsigned long long* __restrict__ acc,
                                                                     int64_t d, int D, int base,
                                                                     const int64_t* __restrict__ count,
                                                                     double* __restrict__ sum,
-                                                                    double* __restrict__ avg) {
+                                                                    double* __restrict__ avg, bool replace,
+                                                                    double* __restrict__ err) {
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= d) return;
   int64_t a[kMaxDigits];
   for (int k = 0; k < D; ++k) a[k] = (int64_t)acc[(size_t)g * D + k];
   const double s = exact_round(a, D, base);
+  if (err) err[g] = replace ? 0.0 : fabs(sum[g] - s);
+  if (!replace) return;
   sum[g] = s;
   if (avg) avg[g] = count[g] ? s / (double)count[g] : __longlong_as_double(0x7ff8000000000000ll);
 }
 
-// Replaces the sums (and averages) of a finished float GROUP BY result with
-// exactly rounded ones. keys/vals: the query's device columns.
+// Exactly rounded sums of a finished float GROUP BY result: with replace, they
+// replace the result's sums (and averages); with report, g->sum_err receives
+// |kept sum - exact sum| per group. keys/vals: the query's device columns.
 agg_status exact_fp_sums(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                         agg_groups* g, cudaStream_t s) {
+                         agg_groups* g, cudaStream_t s, bool replace, bool report) {
   const int64_t d = g->num_groups;
   if (d == 0 || n == 0) return AGG_OK;
+  double* err = nullptr;
+  if (report) {
+    if (dev_malloc_async((void**)&err, (size_t)d * 8, s) != cudaSuccess) {
+      set_error("sum errors: cannot allocate %lld bytes", (long long)d * 8);
+      return AGG_ERR_OOM;
+    }
+    ((GroupsPriv*)g->priv)->extra = err;  // freed with the result from here on
+    g->sum_err = err;
+  }
   const DeviceInfo& di = device_info();
   const int grid = di.sm_count * 8;
   PhaseTimer pt(AGG_PHASE_FINALIZE, s);
@@ -153,7 +169,8 @@ agg_status exact_fp_sums(const uint32_t* keys, const void* vals, int64_t n, int 
   if (e == cudaSuccess) {
     const int rgrid = (int)((d + kExactThreads - 1) / kExactThreads);
     exact_round_groups<<<rgrid, kExactThreads, 0, s>>>((const unsigned long long*)acc, d, D, base, g->count,
-                                                       (double*)g->sum, (ops & AGG_AVG) ? g->avg : nullptr);
+                                                       (double*)g->sum, (ops & AGG_AVG) ? g->avg : nullptr,
+                                                       replace, err);
     note_launch();
     e = cudaGetLastError();
   }

@@ -703,7 +703,7 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
 
 namespace agg {
 agg_status exact_fp_sums(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                         agg_groups* g, cudaStream_t s);
+                         agg_groups* g, cudaStream_t s, bool replace, bool report);
 }
 
 static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
@@ -711,8 +711,9 @@ static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n
   agg_options o{};
   if (opt) o = *opt;
   agg_status st = groupby_with(keys, vals, n, vdt, ops, o, s, out, nullptr);
-  if (st == AGG_OK && (o.flags & AGG_FLAG_EXACT_SUM) && dtype_is_fp(vdt) && (ops & (AGG_SUM | AGG_AVG))) {
-    st = exact_fp_sums(keys, vals, n, vdt, ops, *out, s);
+  const bool exact = o.flags & AGG_FLAG_EXACT_SUM, report = o.flags & AGG_FLAG_SUM_ERROR;
+  if (st == AGG_OK && (exact || report) && dtype_is_fp(vdt) && (ops & (AGG_SUM | AGG_AVG))) {
+    st = exact_fp_sums(keys, vals, n, vdt, ops, *out, s, exact, report);
     if (st != AGG_OK) {
       agg_groups_free(*out);
       *out = nullptr;
@@ -939,7 +940,8 @@ static agg_status check_groupby_args(const uint32_t* keys, const void* vals, int
                                                opt->block_threads % 32 == 0),
                   "block_threads must be 0 or a multiple of 32 in [64, 1024]");
     AGG_CHECK_ARG(opt->blocks_per_sm >= 0, "blocks_per_sm must be >= 0");
-    AGG_CHECK_ARG((opt->flags & ~AGG_FLAG_EXACT_SUM) == 0, "unknown flags 0x%x", (unsigned)opt->flags);
+    AGG_CHECK_ARG((opt->flags & ~(AGG_FLAG_EXACT_SUM | AGG_FLAG_SUM_ERROR)) == 0, "unknown flags 0x%x",
+                  (unsigned)opt->flags);
   }
   return AGG_OK;
 }
@@ -954,7 +956,7 @@ extern "C" agg_status agg_groupby(const uint32_t* keys_dev, const void* vals_dev
 }
 
 extern "C" agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* count, void* sum, void* min,
-                                         void* max, double* avg) {
+                                         void* max, double* avg, double* sum_err) {
   clear_error();
   AGG_CHECK_ARG(g != nullptr, "null result");
   const int64_t d = g->num_groups;
@@ -965,6 +967,7 @@ extern "C" agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, in
   if (min) AGG_CUDA_TRY(cudaMemcpy(min, g->min, (size_t)d * 8, cudaMemcpyDeviceToHost));
   if (max) AGG_CUDA_TRY(cudaMemcpy(max, g->max, (size_t)d * 8, cudaMemcpyDeviceToHost));
   if (avg) AGG_CUDA_TRY(cudaMemcpy(avg, g->avg, (size_t)d * 8, cudaMemcpyDeviceToHost));
+  if (sum_err && g->sum_err) AGG_CUDA_TRY(cudaMemcpy(sum_err, g->sum_err, (size_t)d * 8, cudaMemcpyDeviceToHost));
   return AGG_OK;
 }
 
@@ -983,6 +986,7 @@ extern "C" void agg_groups_free(agg_groups* g) {
     // stream-ordered: work queued on the producing stream finishes first, and
     // no other stream or the host has to wait
     cudaFreeAsync(p->block, p->stream);
+    if (p->extra) cudaFreeAsync(p->extra, p->stream);
     if (cur != p->device) cudaSetDevice(cur);
     delete p;
   }
@@ -994,8 +998,8 @@ extern "C" agg_status agg_groupby_host(const uint32_t* keys_host, const void* va
   clear_error();
   agg_status st = check_groupby_args(keys_host, vals_host, n, vdtype, ops, opt, out);
   if (st != AGG_OK) return st;
-  AGG_CHECK_ARG(!opt || !(opt->flags & AGG_FLAG_EXACT_SUM),
-                "AGG_FLAG_EXACT_SUM needs device columns (agg_groupby)");
+  AGG_CHECK_ARG(!opt || !(opt->flags & (AGG_FLAG_EXACT_SUM | AGG_FLAG_SUM_ERROR)),
+                "AGG_FLAG_EXACT_SUM and AGG_FLAG_SUM_ERROR need device columns (agg_groupby)");
   *out = nullptr;
   return groupby_host_impl(keys_host, vals_host, n, vdtype, ops, opt, (cudaStream_t)stream, out);
 }

@@ -59,6 +59,7 @@ struct GroupsPriv {
   SharedBlock* shared = nullptr;  // or a reference to a batch's output block
   int device = 0;
   cudaStream_t stream = nullptr;  // stream the result was produced on (block freed there)
+  void* extra = nullptr;          // sum_err array (AGG_FLAG_SUM_ERROR), freed with the result
 };
 
 // Allocate a result with capacity for `cap` rows of every output array.

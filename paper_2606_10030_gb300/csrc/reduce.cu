@@ -20,6 +20,16 @@
 // Block partials carry the sum as a float64 pair (hi, lo); the final merge is
 // a float64 double-double sum in a fixed order, so the result is
 // deterministic for a given grid.
+//
+// Error bound of a float SUM. Every partial also carries eb, a bound on
+// |hi + lo - (exact sum of its rows)|, built from the roundings that can
+// occur: per thread, those of the compensation word of a float32 pair (each
+// at most 2^-24 of the word's new value, tracked as the word's largest
+// magnitude) or the truncations of the float64 fixed-point sum (less than one
+// unit each, at most two per row); per merge, the two float64 roundings of
+// the low words. The result's err_bound adds the final rounding of hi + lo
+// and the oracle's own rounding of the exact sum, so that
+// |sum_f - (exact sum rounded to float64)| <= err_bound.
 #include <cfloat>
 #include <climits>
 #include <cmath>
@@ -34,6 +44,7 @@ struct Partial {  // one block's partial aggregate
   int64_t si;     // integer sum
   double hi, lo;  // float sum, unevaluated hi + lo
   uint64_t mn, mx;  // order-preserving images of min / max
+  double eb;      // bound on |hi + lo - exact sum of the rows| (float columns)
 };
 
 template <int DT> struct Traits;
@@ -72,12 +83,13 @@ struct Acc<DT, SUM, MM, false> {
       fold((T)(((uint64_t)r.w << 32) | r.z));
     }
   }
-  __device__ void to_partial(Partial& p) const {
+  __device__ void to_partial(Partial& p, uint32_t) const {
     p.si = s;
     p.hi = 0.0;
     p.lo = 0.0;
     p.mn = img_i64((int64_t)mn);
     p.mx = img_i64((int64_t)mx);
+    p.eb = 0.0;
   }
 };
 
@@ -180,6 +192,15 @@ struct Fix128 {
     h = ldexp(t, sc) + special;
     l = special == 0.0 ? ldexp(f, sc) : 0.0;
   }
+  // Bound on |h + l - exact sum| after `rows` adds: each add loses less than
+  // one unit 2^(E - 1075 - kFixGuard) (a row far below E), each rescale less
+  // than one unit of the new scale; to_pair rounds e1 + e2 (under 2^-104 of
+  // the sum) and may round h and l into the subnormal range.
+  __device__ double error_bound(uint32_t rows, double h, double l) const {
+    if (special != 0.0) return __longlong_as_double(0x7ff0000000000000ll);
+    if (E == 0) return 0.0;
+    return ldexp(2.0 * (double)rows, E - 1075 - kFixGuard) + (fabs(h) + fabs(l)) * 0x1p-100 + 0x1p-1072;
+  }
 };
 
 template <int DT, bool SUM, bool MM>
@@ -188,10 +209,11 @@ struct Acc<DT, SUM, MM, true> {
   using U = typename FpImg<T>::U;
   static constexpr bool F64 = sizeof(T) == 8;
   T s, c;       // float32: TwoSum-compensated pair
+  T cmax;       // float32: largest |c| so far (bounds the roundings of c)
   Fix128 fx;    // float64
   U mn, mx;
   __device__ void init() {
-    s = 0; c = 0;
+    s = 0; c = 0; cmax = 0;
     if (F64) fx.init();
     mn = (U)~(U)0; mx = 0;
   }
@@ -204,6 +226,7 @@ struct Acc<DT, SUM, MM, true> {
         two_sum(s, v, t, e);
         s = t;
         c += e;
+        cmax = fmaxf(cmax, fabsf(c));
       }
     }
     if (MM) {
@@ -221,13 +244,23 @@ struct Acc<DT, SUM, MM, true> {
       fold(__longlong_as_double((long long)(((uint64_t)r.w << 32) | r.z)));
     }
   }
-  __device__ void to_partial(Partial& p) const {
+  // rows: the number of values this thread folded.
+  __device__ void to_partial(Partial& p, uint32_t rows) const {
     p.si = 0;
+    p.eb = 0.0;
     if (F64 && SUM) {
       fx.to_pair(p.hi, p.lo);
+      p.eb = fx.error_bound(rows, p.hi, p.lo);
     } else {
       p.hi = (double)s;
       p.lo = (double)c;
+      // TwoSum leaves s + c short only by the roundings of c: each at most
+      // 2^-24 of |c| after the add (2^-150 when c is subnormal)
+      if (SUM && !F64) {
+        p.eb = (isfinite(p.hi) && isfinite(p.lo))
+                   ? (double)rows * ((double)cmax * (0x1p-24 * (1.0 + 0x1p-23)) + 0x1p-150)
+                   : __longlong_as_double(0x7ff0000000000000ll);
+      }
     }
     p.mn = FpImg<T>::widen(mn);
     p.mx = FpImg<T>::widen(mx);
@@ -242,7 +275,9 @@ __device__ __forceinline__ void combine(Partial& a, const Partial& b) {
   double s, e;
   two_sum(a.hi, b.hi, s, e);
   a.hi = s;
-  a.lo += e + b.lo;
+  const double r1 = e + b.lo;  // rounded: at most 2^-53 |r1| (+ 2^-1075)
+  a.lo += r1;                  // rounded: at most 2^-53 |a.lo| (+ 2^-1075)
+  a.eb = a.eb + b.eb + (fabs(r1) + fabs(a.lo)) * 0x1p-53 + 0x1p-1074;
   a.mn = min(a.mn, b.mn);
   a.mx = max(a.mx, b.mx);
 }
@@ -254,6 +289,7 @@ __device__ __forceinline__ Partial shfl_xor(const Partial& p, int m) {
   q.lo = __shfl_xor_sync(0xffffffffu, p.lo, m);
   q.mn = __shfl_xor_sync(0xffffffffu, p.mn, m);
   q.mx = __shfl_xor_sync(0xffffffffu, p.mx, m);
+  q.eb = __shfl_xor_sync(0xffffffffu, p.eb, m);
   return q;
 }
 
@@ -268,7 +304,7 @@ __device__ Partial block_reduce(Partial p) {
   __syncthreads();
   if (w == 0) {
     if (l < BLOCK / 32) p = sm[l];
-    else p = Partial{0, 0.0, 0.0, ~0ull, 0ull};
+    else p = Partial{0, 0.0, 0.0, ~0ull, 0ull, 0.0};
 #pragma unroll
     for (int m = 16; m >= 1; m >>= 1) combine(p, shfl_xor(p, m));
   }
@@ -280,7 +316,7 @@ __device__ Partial block_reduce(Partial p) {
 template <int DT, int BLOCK>
 __device__ void merge_partials(const Partial* parts, int np, agg_scalar* out, uint32_t ops,
                                int64_t count) {
-  Partial acc{0, 0.0, 0.0, ~0ull, 0ull};
+  Partial acc{0, 0.0, 0.0, ~0ull, 0ull, 0.0};
   for (int i = threadIdx.x; i < np; i += BLOCK) {
     Partial q;
     q.si = __ldcg(&parts[i].si);
@@ -288,6 +324,7 @@ __device__ void merge_partials(const Partial* parts, int np, agg_scalar* out, ui
     q.lo = __ldcg(&parts[i].lo);
     q.mn = __ldcg(&parts[i].mn);
     q.mx = __ldcg(&parts[i].mx);
+    q.eb = __ldcg(&parts[i].eb);
     combine(acc, q);
   }
   __syncthreads();
@@ -297,12 +334,17 @@ __device__ void merge_partials(const Partial* parts, int np, agg_scalar* out, ui
   r.count = count;
   r.dtype = DT;
   r.ops = ops;
-  r.reserved = 0;
+  r.err_bound = 0.0;
   const double nan = __longlong_as_double(0x7ff8000000000000ll);
   if (Traits<DT>::FP) {
     double s = acc.hi + acc.lo;
     r.sum_i = 0;
     r.sum_f = s;
+    // the partials' bound, plus the rounding of hi + lo and the oracle's own
+    // rounding of the exact sum (each at most 2^-53 of the value), plus a
+    // margin for the roundings of the bound's own sums
+    if (ops & (AGG_SUM | AGG_AVG))
+      r.err_bound = (acc.eb + fabs(s) * 0x1p-52 + 0x1p-1073) * (1.0 + 0x1p-40);
     r.avg = count ? s / (double)count : nan;
     r.min_f = count ? f64_of_img(acc.mn) : __longlong_as_double(0x7ff0000000000000ll);
     r.max_f = count ? f64_of_img(acc.mx) : __longlong_as_double((long long)0xfff0000000000000ull);
@@ -334,12 +376,13 @@ __global__ void __launch_bounds__(kBlock) reduce_scan(const typename Traits<DT>:
   constexpr int EPV = 16 / sizeof(T);
   Acc<DT, SUM, MM> a;
   a.init();
+  uint32_t rows = 0;  // values this thread folds
   if (SUM || MM) {
     const int64_t nv = (n - head) / EPV;
     const int64_t tail0 = head + nv * EPV;
     const int64_t g = (int64_t)blockIdx.x * kBlock + threadIdx.x;
-    if (g < head) a.fold(col[g]);
-    if (g < n - tail0) a.fold(col[tail0 + g]);
+    if (g < head) { a.fold(col[g]); ++rows; }
+    if (g < n - tail0) { a.fold(col[tail0 + g]); ++rows; }
     const uint4* v = reinterpret_cast<const uint4*>(col + head);
     const int64_t stride = (int64_t)gridDim.x * kBlock * kUnroll;
     for (int64_t base = (int64_t)blockIdx.x * kBlock * kUnroll + threadIdx.x; base < nv; base += stride) {
@@ -351,12 +394,15 @@ __global__ void __launch_bounds__(kBlock) reduce_scan(const typename Traits<DT>:
       }
 #pragma unroll
       for (int u = 0; u < kUnroll; ++u) {
-        if (base + (int64_t)u * kBlock < nv) a.fold_vec(r[u]);
+        if (base + (int64_t)u * kBlock < nv) {
+          a.fold_vec(r[u]);
+          rows += EPV;
+        }
       }
     }
   }
   Partial p;
-  a.to_partial(p);
+  a.to_partial(p, rows);
   p = block_reduce<kBlock>(p);
   __shared__ int s_last;
   if (threadIdx.x == 0) {

@@ -275,4 +275,4 @@ extern "C" agg_status agg_profile_read(double* ms, int64_t* calls) {
 
 extern "C" const char* agg_last_error(void) { return agg::g_last_error.c_str(); }
 
-extern "C" int agg_version(void) { return 100; }
+extern "C" int agg_version(void) { return 101; }

@@ -186,6 +186,7 @@ def evaluate_large(log2_rows: int = 30, log2_keys=range(4, 27, 2), skews=(0.0, 0
             row = {"log2_keys": lk, "zipf_s": sk, "ms": T.round(3).tolist(), "best": int(T.argmin()),
                    "learned": learned, "rule": rule, "learned_regret": float(T[learned] / T.min() - 1),
                    "rule_regret": float(T[rule] / T.min() - 1),
+                   "learned_GBps": float(n * 12 / (T[learned] * 1e-3) / 1e9),
                    "best_GBps": float(n * 12 / (T.min() * 1e-3) / 1e9)}
             if e2e_done < e2e_tables and lk in (4, 12, 20, 26) and sk == 1.0:
                 hk, hv = k.cpu().pin_memory(), v.cpu().pin_memory()
@@ -205,9 +206,13 @@ def evaluate_large(log2_rows: int = 30, log2_keys=range(4, 27, 2), skews=(0.0, 0
             log(row)
     lr = np.array([r["learned_regret"] for r in rows])
     rr = np.array([r["rule_regret"] for r in rows])
+    total_learned_ms = float(sum(r["ms"][r["learned"]] for r in rows))
     return {"tables": rows, "rows_per_table": n, "learned_mean_regret": float(lr.mean()),
             "learned_p95_regret": float(np.percentile(lr, 95)), "rule_mean_regret": float(rr.mean()),
-            "rule_p95_regret": float(np.percentile(rr, 95))}
+            "rule_p95_regret": float(np.percentile(rr, 95)),
+            "learned_classes": np.bincount([r["learned"] for r in rows], minlength=3).tolist(),
+            "best_classes": np.bincount([r["best"] for r in rows], minlength=3).tolist(),
+            "learned_GBps_all_tables": float(len(rows) * n * 12 / (total_learned_ms * 1e-3) / 1e9)}
 
 
 def main():

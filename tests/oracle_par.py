@@ -27,7 +27,8 @@ CHUNK = 1 << 24  # rows a worker reads at a time
 
 
 def cache_dir() -> str:
-    d = os.environ.get("AGG_ORACLE_CACHE") or os.path.join(tempfile.gettempdir(), "agg_oracle_cache")
+    base = "/dev/shm" if os.path.isdir("/dev/shm") and os.access("/dev/shm", os.W_OK) else tempfile.gettempdir()
+    d = os.environ.get("AGG_ORACLE_CACHE") or os.path.join(base, "agg_oracle_cache")
     os.makedirs(d, exist_ok=True)
     return d
 
@@ -149,32 +150,43 @@ def _table_rows(spec, a: int, b: int, thresholds):
 def _table_worker(args):
     spec, a, b, tpath, sel = args
     import oracle
-    thresholds = np.load(tpath, mmap_mode="r") if tpath else None
-    keys, vals = _table_rows(spec, a, b, thresholds)
+    if isinstance(spec, tuple) and len(spec) == 2:  # row ranges of stored columns
+        keys = np.asarray(np.load(spec[0], mmap_mode="r")[a:b])
+        vals = np.asarray(np.load(spec[1], mmap_mode="r")[a:b])
+    else:
+        thresholds = np.load(tpath, mmap_mode="r") if tpath else None
+        keys, vals = _table_rows(spec, a, b, thresholds)
     g = oracle.groupby_selected(keys, vals, sel)
     r = oracle.reduce(vals)
     return (g.keys, g.count, g.sum, g.min, g.max), (r["count"], r["sum"], r["min"], r["max"])
 
 
 def table_check(n: int, n_keys: int, s: float, dtype: str, seed: int, sel: np.ndarray, rows_per_job: int = CHUNK,
-                workers: int | None = None) -> dict:
-    """Oracle results for a seeded integer table too large to hold on the host.
+                workers: int | None = None, columns=None) -> dict:
+    """Oracle results for a seeded integer table of up to billions of rows.
 
-    Each job regenerates its row range with the seeded generators (the same
-    draws the GPU generator makes) and runs ``oracle.groupby_selected`` and
-    ``oracle.reduce`` on it; the ranges' integer results are merged as in
-    ``groupby_selected_int``. Returns the selected groups and the ungrouped
-    count, sum (mod 2^64), min and max of the whole column.
+    Each job takes a row range, regenerated with the seeded generators (the
+    same draws the GPU generator makes; uniform keys are cheap to redraw) or,
+    when ``columns`` = (keys, vals) is given, read from a copy of them, and
+    runs ``oracle.groupby_selected`` and ``oracle.reduce`` on it; the ranges'
+    integer results are merged as in ``groupby_selected_int``. Returns the
+    selected groups and the ungrouped count, sum (mod 2^64), min and max of
+    the whole column.
     """
     import datagen as dg
     assert dtype in ("i32", "i64", "u32")
     sel = np.unique(np.asarray(sel, dtype=np.uint32))
     with tempfile.TemporaryDirectory(dir=cache_dir()) as tmp:
         tpath = None
-        if s > 0:
+        if columns is not None:
+            spec = (os.path.join(tmp, "k.npy"), os.path.join(tmp, "v.npy"))
+            np.save(spec[0], np.ascontiguousarray(columns[0], dtype=np.uint32))
+            np.save(spec[1], np.ascontiguousarray(columns[1]))
+        elif s > 0:
             tpath = os.path.join(tmp, "thresholds.npy")
             np.save(tpath, dg.zipf_thresholds(n_keys, s))
-        spec = (n_keys, s, dtype, seed)
+        if columns is None:
+            spec = (n_keys, s, dtype, seed)
         jobs = [(spec, a, min(n, a + rows_per_job), tpath, sel) for a in range(0, n, rows_per_job)]
         workers = workers or (os.cpu_count() or 1)
         with mp.get_context("spawn").Pool(min(workers, len(jobs))) as pool:

@@ -38,7 +38,7 @@ def test_every_declared_symbol_is_exported(L):
 
 
 def test_version(L):
-    assert L.agg_version() == 100
+    assert L.agg_version() == 101
 
 
 def test_reduce_rejects_bad_arguments_without_launching(L):
@@ -79,19 +79,20 @@ def test_groupby_batch_and_network_reject_bad_arguments_without_launching(L):
         o = agg.options(**bad) if "strategy" not in bad else agg.options(bad["strategy"])
         assert L.agg_groupby(k, v, 10, agg.AGG_I32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
                              None) == agg.AGG_ERR_INVALID, bad
-    o = agg.options(flags=2)
+    o = agg.options(flags=4)
     assert L.agg_groupby(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
                          None) == agg.AGG_ERR_INVALID
     assert "flags" in agg.last_error()
-    o = agg.options(flags=agg.AGG_FLAG_EXACT_SUM)  # the exact float sums read device columns
-    assert L.agg_groupby_host(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
-                              None) == agg.AGG_ERR_INVALID
+    for f in (agg.AGG_FLAG_EXACT_SUM, agg.AGG_FLAG_SUM_ERROR):  # the exact float sums read device columns
+        o = agg.options(flags=f)
+        assert L.agg_groupby_host(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
+                                  None) == agg.AGG_ERR_INVALID
     assert L.agg_groupby_host(k, v, 10, 9, agg.AGG_SUM, None, ctypes.byref(out), None) == agg.AGG_ERR_INVALID
     assert L.agg_sketch(k, 10, 9, agg.AGG_SUM, 0, v, None) == agg.AGG_ERR_INVALID
     assert L.agg_sketch(k, 10, agg.AGG_I32, agg.AGG_SUM, 0, None, None) == agg.AGG_ERR_INVALID
     r = agg.AggTuneResult()
     assert L.agg_autotune(k, v, 0, agg.AGG_I32, agg.AGG_SUM, 1, ctypes.byref(r), None) == agg.AGG_ERR_INVALID
-    assert L.agg_groups_to_host(None, None, None, None, None, None, None) == agg.AGG_ERR_INVALID
+    assert L.agg_groups_to_host(None, None, None, None, None, None, None, None) == agg.AGG_ERR_INVALID
     # batches
     q = (agg.AggQuery * 2)()
     q[0].keys, q[0].vals, q[0].n, q[0].dtype, q[0].ops = 0x1000, 0x2000, 10, agg.AGG_I32, agg.AGG_SUM

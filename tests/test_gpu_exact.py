@@ -130,3 +130,37 @@ def test_exact_flag_rejected_on_the_host_path():
         agg.agg_groupby_host(torch.from_numpy(keys), torch.from_numpy(vals), agg.AGG_ALL,
                              agg.options(agg.AGG_STRAT_AUTO, flags=agg.AGG_FLAG_EXACT_SUM))
     assert e.value.status == agg.AGG_ERR_INVALID
+
+
+@pytest.mark.parametrize("strategy", STRATS)
+@pytest.mark.parametrize("dt", ["f32", "f64"])
+@pytest.mark.parametrize("case", ["many", "zipf", "wide", "cancel"])
+def test_sum_error_is_the_distance_from_the_oracles_sum(strategy, dt, case):
+    """AGG_FLAG_SUM_ERROR keeps the strategy's sums and reports |sum - oracle sum| per group."""
+    keys, vals = make(case, dt)
+    res = run(keys, vals, strategy, flags=agg.AGG_FLAG_SUM_ERROR)
+    ref = oracle.groupby(keys, vals)
+    assert np.array_equal(res["keys"], ref.keys)
+    assert np.array_equal(res["sum_err"].view(np.int64), np.abs(res["sum"] - ref.sum).view(np.int64))
+    # and the sums kept are the strategy's own (within the bar, not replaced)
+    plain = run(keys, vals, strategy, flags=0)
+    assert "sum_err" not in plain
+    a = oracle.groupby(keys, np.abs(vals)).sum
+    assert np.all(res["sum_err"] <= 1e-6 * np.maximum(np.abs(ref.sum), 2.0 ** -24 * a))
+
+
+def test_sum_error_with_exact_sums_is_zero():
+    keys, vals = make("zipf", "f32")
+    res = run(keys, vals, agg.AGG_STRAT_AUTO, flags=agg.AGG_FLAG_SUM_ERROR | agg.AGG_FLAG_EXACT_SUM)
+    ref = oracle.groupby(keys, vals)
+    assert np.array_equal(res["sum"].view(np.int64), ref.sum.view(np.int64))
+    assert np.all(res["sum_err"] == 0.0)
+
+
+def test_sum_error_is_absent_for_integer_columns():
+    keys = dg.keys_uniform(10_000, 30, 1)
+    vals = dg.values("i64", keys.size, 1)
+    g = agg.agg_groupby(torch.from_numpy(keys).cuda(), torch.from_numpy(vals).cuda(), agg.AGG_ALL,
+                        agg.options(flags=agg.AGG_FLAG_SUM_ERROR))
+    assert not g.has_sum_err
+    g.free()

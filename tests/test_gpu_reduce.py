@@ -201,3 +201,46 @@ def test_gpu_generator_matches_host_generator():
     assert np.allclose(f, dg.values("f64", n, 3), rtol=1e-12, atol=1e-9)
     assert np.array_equal(dgc.keys_uniform(n, 1000, 4).cpu().numpy(), dg.keys_uniform(n, 1000, 4))
     assert np.array_equal(dgc.keys_zipf(n, 5000, 1.0, 4).cpu().numpy(), dg.keys_zipf(n, 5000, 1.0, 4))
+
+
+def _scalar(x: np.ndarray, ops=agg.AGG_ALL, host=False):
+    if host:
+        return agg.agg_reduce_host(torch.from_numpy(x).pin_memory(), ops)
+    return agg.decode_scalar(agg.agg_reduce(torch.from_numpy(x).cuda(), ops))
+
+
+@pytest.mark.parametrize("dt", [np.float32, np.float64])
+@pytest.mark.parametrize("kind", ["normal", "wide", "cancel", "tiny"])
+@pytest.mark.parametrize("n", [1, 33, 65537, 3_000_001])
+def test_float_sum_error_bound_holds(dt, kind, n):
+    """err_bound, computed on the device with the sum, bounds |sum_f - oracle sum|."""
+    rng = np.random.default_rng(n)
+    if kind == "cancel":
+        h = rng.standard_normal(n // 2 + 1) * 1e6
+        x = np.concatenate([h, -h[::-1]])[:n]
+        x[::97] += 1e-3
+    elif kind == "tiny":  # subnormal float32 / float64 magnitudes beside normal ones
+        tiny = np.finfo(dt).smallest_subnormal
+        x = rng.integers(-1000, 1000, n).astype(np.float64) * float(tiny)
+        x[::5] = rng.standard_normal(x[::5].size)
+    else:
+        x = make(dt, n, seed=n, kind=kind)
+    x = np.asarray(x).astype(dt)
+    ref = oracle.reduce(x)["sum"]
+    for host in (False, True):
+        r = _scalar(x, host=host)
+        assert np.isfinite(r.err_bound) and r.err_bound >= 0
+        assert abs(r.sum_f - ref) <= r.err_bound, (host, r.sum_f, ref, r.err_bound)
+        a = float(np.abs(x.astype(np.float64)).sum())
+        # the bound is itself far inside the 1e-6 bar on these columns
+        assert r.err_bound <= 1e-6 * max(abs(ref), 2.0 ** -24 * a) or r.err_bound <= 2.0 ** -1000
+
+
+def test_error_bound_of_integer_and_nonfinite_columns():
+    x = make(np.int64, 100_000, seed=1)
+    assert _scalar(x).err_bound == 0.0
+    y = np.array([1.0, np.inf, 2.0], dtype=np.float32)
+    assert _scalar(y).err_bound == np.inf
+    z = np.arange(1000, dtype=np.float64)
+    r = _scalar(z, agg.AGG_MIN | agg.AGG_MAX)
+    assert r.err_bound == 0.0  # no SUM asked

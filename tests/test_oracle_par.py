@@ -57,3 +57,7 @@ def test_table_check_regenerates_the_seeded_table(tmp_path, monkeypatch):
         assert np.array_equal(got["min"][has], ref.min[has]) and np.array_equal(got["max"][has], ref.max[has])
         r = oracle.reduce(vals)
         assert got["total"] == {"count": r["count"], "sum": r["sum"], "min": r["min"], "max": r["max"]}
+        again = oracle_par.table_check(n, D, s, "i64", 9, sel, rows_per_job=20_000, workers=4, columns=(keys, vals))
+        for f in ("keys", "count", "sum"):
+            assert np.array_equal(again[f], got[f])
+        assert again["total"] == got["total"]
