@@ -50,6 +50,7 @@ if ROOT not in sys.path:
 METRIC = "Input GB/s & % of GB300 HBM peak; batched+learned vs plain per-query kernels"
 UNIT = "GB/s"
 FALLBACK_HBM_GBS = 6800.0
+WEIGHTS = os.path.join(ROOT, "paper_2606_10030_gb300", "selector_weights.npz")
 
 
 def load_peaks() -> dict:
@@ -313,7 +314,7 @@ class Table2p30Workload:
                             "keys, int64 values uniform in [0, 2^32), strategy from the learned selector",
                 "rows": self.n, "distinct_keys_domain": self.D, "zipf_s": self.zipf_s, "key_dtype": "uint32",
                 "value_dtype": "int64", "input_bytes": self.n * self.esize,
-                "strategy": "learned" if self.learned else "auto (no trained weights)",
+                "strategy": "learned selector" if os.path.exists(WEIGHTS) else "auto rule (no trained weights)",
                 "l2": "input (12 GiB) larger than L2 (129 MB); no flush needed"}
 
     def bytes_per_step(self):
