@@ -390,6 +390,28 @@ PHASE_KERNELS = {"scan": "reduce_scan", "sketch": "sketch_gather + sketch_kernel
                  "segreduce": "seg_reduce + seg_finalize", "batch": "batch_build", "mlp": "mlp kernels"}
 
 
+def energy_mj(device: int):
+    """NVML's energy counter of the GPU (mJ, read-only), or None where it cannot be read."""
+    import paper_2606_10030_gb300 as agg
+    try:
+        return agg.agg_energy_counter(device)
+    except agg.AggError:
+        return None
+
+
+def energy_report(e0, e1, e2, e3, steps, e2e_steps, bytes_step, e2e_bytes) -> dict:
+    """Energy per step of the on-device and the end-to-end runs (the paper's Sec. 6 comparison)."""
+    if None in (e0, e1, e2, e3):
+        return {"unavailable": "NVML energy counter not readable"}
+    dev_j = (e1 - e0) / 1e3 / steps
+    e2e_j = (e3 - e2) / 1e3 / e2e_steps
+    return {"J_per_step": round(dev_j, 4), "GB_per_J": round(bytes_step / 1e9 / dev_j, 3) if dev_j > 0 else None,
+            "e2e_J_per_step": round(e2e_j, 4),
+            "e2e_GB_per_J": round(e2e_bytes / 1e9 / e2e_j, 3) if e2e_j > 0 else None,
+            "how": "difference of NVML's total-energy counter around the timed steps (whole GPU, idle draw "
+                   "included)"}
+
+
 def host_link_peak(gib: int = 1, reps: int = 10) -> dict:
     """Pinned host-to-device copy bandwidth (best of reps, CUDA events): the end-to-end roofline."""
     import torch
@@ -690,6 +712,7 @@ def run_ours(args):
     t1 = torch.cuda.Event(enable_timing=True)
     agg.profile_enable(True)
     launches0 = agg.launch_count()
+    e0 = energy_mj(local)
     t0.record(stream)
     launches = 0
     for i in range(args.steps):
@@ -698,6 +721,7 @@ def run_ours(args):
         evs[i][1].record(stream)
     t1.record(stream)
     torch.cuda.synchronize()
+    e1 = energy_mj(local)
     launches = agg.launch_count() - launches0
     prof = agg.profile_read()
     agg.profile_enable(False)
@@ -722,10 +746,13 @@ def run_ours(args):
     W.step_e2e()
     torch.cuda.synchronize()
     barrier(world)
+    e2 = energy_mj(local)
     a = time.perf_counter()
     for _ in range(e2e_steps):
         W.step_e2e()
     e2e_s = max_over_ranks(time.perf_counter() - a, world)
+    torch.cuda.synchronize()
+    e3 = energy_mj(local)
     h2d, d2h = W.e2e_bytes()
     e2e_value = world * h2d * e2e_steps / e2e_s / 1e9
     strategy = agg.STRATEGY_NAMES.get(getattr(W, "last_strategy", -1), None)
@@ -761,6 +788,7 @@ def run_ours(args):
                     "steps": e2e_steps, "link_peak_GB/s": link["GB/s"],
                     "frac_of_link": round(e2e_value / world / link["GB/s"], 4), "link_how": link["how"]},
             "gpu_launches": launches,
+            "energy": energy_report(e0, e1, e2, e3, args.steps, e2e_steps, bytes_step, h2d),
             "phases_ms_per_step": {k: round(v[0] / args.steps, 4) for k, v in prof.items() if v[1]},
             "extra": extra,
             "clocks": clocks,

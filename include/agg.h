@@ -468,6 +468,20 @@ void agg_debug_fail_alloc(int64_t countdown);
 void agg_profile_enable(int on);
 agg_status agg_profile_read(double* ms, int64_t* calls);
 
+/*
+ * agg_energy_counter -- the energy the GPU `device` (a CUDA device ordinal)
+ * has used since its driver was loaded, in millijoules, read from NVML
+ * (nvmlDeviceGetTotalEnergyConsumption; the paper compares the energy of the
+ * aggregation on each device, Sec. 6). Read-only: nothing is set on the GPU.
+ * The energy of a piece of work is the difference of two reads around it,
+ * after the work has finished; the counter covers the whole GPU, so other
+ * work on it is counted too. NVML is loaded on the first call
+ * (libnvidia-ml.so.1, or the library named by the environment variable
+ * AGG_NVML_LIB). Errors: AGG_ERR_INVALID (null pointer, negative device),
+ * AGG_ERR_CUDA (NVML missing, or it has no counter for the device).
+ */
+agg_status agg_energy_counter(int device, uint64_t* millijoules);
+
 /* Message of the last failed call on this thread ("" if none). */
 const char* agg_last_error(void);
 

@@ -178,6 +178,7 @@ SIGNATURES = {
     "agg_debug_fail_alloc": (None, [_i64]),
     "agg_profile_enable": (None, [_i32]),
     "agg_profile_read": (_i32, [_vp, _vp]),
+    "agg_energy_counter": (_i32, [_i32, _vp]),
     "agg_last_error": (ctypes.c_char_p, []),
     "agg_version": (_i32, []),
 }
@@ -376,6 +377,13 @@ PHASES = ["scan", "sketch", "build", "finalize", "sort", "segreduce", "batch", "
 def agg_stream_release(stream) -> None:
     """Free the library's cached scratch of a stream (call before the stream is destroyed)."""
     check(lib().agg_stream_release(_stream_ptr(stream)))
+
+
+def agg_energy_counter(device: int = 0) -> int:
+    """NVML's energy counter of a CUDA device in millijoules (read-only)."""
+    mj = ctypes.c_uint64(0)
+    check(lib().agg_energy_counter(device, ctypes.byref(mj)))
+    return int(mj.value)
 
 
 def launch_count() -> int:

@@ -68,7 +68,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         libdir = _cuda_lib_dir(nvcc)
         tmp = LIB + f".tmp{os.getpid()}"
         run([nvcc, *ARCH, "-shared", "-cudart", "shared", "-o", tmp, *objs,
-             "-Xlinker", f"-rpath,{libdir}", "-L", libdir])
+             "-Xlinker", f"-rpath,{libdir}", "-L", libdir, "-ldl"])
         os.replace(tmp, LIB)
     return LIB
 
