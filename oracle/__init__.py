@@ -76,6 +76,13 @@ def lib():
         L.oracle_groups_fetch.restype = None
         L.oracle_groups_free.argtypes = [vp]
         L.oracle_groups_free.restype = None
+        L.oracle_groupby_multi.argtypes = [vp, vp, i64, vp, vp, i32, vp, i32, i64, i64, ctypes.c_double,
+                                           ctypes.c_double, ctypes.POINTER(i64)]
+        L.oracle_groupby_multi.restype = vp
+        L.oracle_multi_fetch.argtypes = [vp, vp, vp]
+        L.oracle_multi_fetch.restype = None
+        L.oracle_multi_free.argtypes = [vp]
+        L.oracle_multi_free.restype = None
         _lib = L
     return _lib
 
@@ -173,3 +180,51 @@ def groupby_selected(keys: np.ndarray, vals: np.ndarray, sel: np.ndarray) -> Gro
     if not h:
         raise ValueError("oracle_groupby_selected rejected its arguments")
     return _fetch(h, d.value, dt)
+
+
+def groupby_multi(key_lo: np.ndarray, key_hi: np.ndarray | None, cols: list, filt=None) -> dict:
+    """GROUP BY the 64-bit key (key_hi << 32) | key_lo over several value columns,
+    counting only rows with lo <= f <= hi when filt = (f, lo, hi) is given.
+
+    Returns {"keys": uint64[d] ascending, "count": int64[d], "cols": [{"sum", "min",
+    "max", "avg"} per value column]}.
+    """
+    key_lo = np.ascontiguousarray(key_lo, dtype=np.uint32)
+    n = key_lo.size
+    if key_hi is not None:
+        key_hi = np.ascontiguousarray(key_hi, dtype=np.uint32)
+        assert key_hi.size == n
+    cols = [np.ascontiguousarray(c) for c in cols]
+    assert all(c.size == n for c in cols)
+    dts = np.array([DT[dtype_name(c)] for c in cols], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * len(cols))(*[c.ctypes.data for c in cols])
+    fp, fdt, lo_i, hi_i, lo_f, hi_f = None, 0, 0, 0, 0.0, 0.0
+    if filt is not None:
+        f, lo, hi = filt
+        f = np.ascontiguousarray(f)
+        assert f.size == n
+        fdt = DT[dtype_name(f)]
+        if f.dtype.kind == "f":
+            lo_f, hi_f = float(lo), float(hi)
+        else:
+            lo_i, hi_i = int(lo), int(hi)
+        fp = f
+    d = ctypes.c_int64(0)
+    h = lib().oracle_groupby_multi(_ptr(key_lo), _ptr(key_hi) if key_hi is not None else None, n, ptrs,
+                                   _ptr(dts), len(cols), _ptr(fp) if fp is not None else None, fdt, lo_i, hi_i,
+                                   lo_f, hi_f, ctypes.byref(d))
+    if not h:
+        raise ValueError("oracle_groupby_multi rejected its arguments")
+    keys = np.empty(d.value, dtype=np.uint64)
+    rows = np.empty(d.value * len(cols), dtype=SCALAR_DTYPE)
+    lib().oracle_multi_fetch(h, _ptr(keys), _ptr(rows))
+    lib().oracle_multi_free(h)
+    rows = rows.reshape(d.value, len(cols)) if len(cols) else rows
+    out = {"keys": keys, "count": rows[:, 0]["count"].copy() if d.value else np.zeros(0, np.int64), "cols": []}
+    for c, col in enumerate(cols):
+        fpc = col.dtype.kind == "f"
+        r = rows[:, c]
+        out["cols"].append({"sum": (r["sum_f"] if fpc else r["sum_i"]).copy(),
+                            "min": (r["min_f"] if fpc else r["min_i"]).copy(),
+                            "max": (r["max_f"] if fpc else r["max_i"]).copy(), "avg": r["avg"].copy()})
+    return out

@@ -318,6 +318,83 @@ void* oracle_groupby_selected(const uint32_t* keys, const void* vals, int64_t n,
   return g;
 }
 
+// ---------------------------------------------------------------------------
+// GROUP BY over a composite key with several value columns and a range filter
+// (the operator fusion the paper names as future work, Sec. 8: a selection
+// feeding an aggregation). A row takes part iff flo <= f[i] <= fhi in the
+// filter column's own type (integers compared as int64, uint32 zero-extended;
+// floats as float64, float32 widened exactly); with no filter column every row
+// does. Its group is the 64-bit key (key_hi[i] << 32) | key_lo[i] (key_hi[i] = 0
+// when there is no second key column). Each value column is folded per group
+// exactly as in oracle_groupby; COUNT is the number of rows that took part.
+// Groups come out in ascending 64-bit key order; a group exists iff at least
+// one of its rows passed the filter.
+// ---------------------------------------------------------------------------
+struct MultiState {
+  State<ExactF32> f32;
+  State<ExactF64> f64;
+  State<Dummy> i;
+};
+
+struct MultiGroups {
+  int ncols;
+  std::vector<int> dts;
+  std::map<uint64_t, std::vector<MultiState>> m;
+};
+
+static bool passes(const void* f, int fdt, int64_t i, int64_t lo_i, int64_t hi_i, double lo_f, double hi_f) {
+  if (!f) return true;
+  if (fdt == D_F32 || fdt == D_F64) {
+    const double x = fdt == D_F32 ? (double)((const float*)f)[i] : ((const double*)f)[i];
+    return lo_f <= x && x <= hi_f;
+  }
+  const int64_t x = int_at(f, fdt, i);
+  return lo_i <= x && x <= hi_i;
+}
+
+void* oracle_groupby_multi(const uint32_t* key_lo, const uint32_t* key_hi, int64_t n, const void* const* cols,
+                           const int* dts, int ncols, const void* fcol, int fdt, int64_t flo_i, int64_t fhi_i,
+                           double flo_f, double fhi_f, int64_t* d) {
+  if (n < 0 || ncols < 1 || (n > 0 && !key_lo)) return nullptr;
+  for (int c = 0; c < ncols; ++c)
+    if (dts[c] < 0 || dts[c] > 4 || (n > 0 && !cols[c])) return nullptr;
+  if (fcol && (fdt < 0 || fdt > 4)) return nullptr;
+  auto* g = new MultiGroups();
+  g->ncols = ncols;
+  g->dts.assign(dts, dts + ncols);
+  for (int64_t i = 0; i < n; ++i) {
+    if (!passes(fcol, fdt, i, flo_i, fhi_i, flo_f, fhi_f)) continue;
+    const uint64_t key = ((uint64_t)(key_hi ? key_hi[i] : 0u) << 32) | key_lo[i];
+    std::vector<MultiState>& st = g->m[key];
+    if (st.empty()) st.resize(ncols);
+    for (int c = 0; c < ncols; ++c) {
+      if (dts[c] == D_F32) st[c].f32.fold_fp(((const float*)cols[c])[i]);
+      else if (dts[c] == D_F64) st[c].f64.fold_fp(((const double*)cols[c])[i]);
+      else st[c].i.fold_int(int_at(cols[c], dts[c], i));
+    }
+  }
+  if (d) *d = (int64_t)g->m.size();
+  return g;
+}
+
+// keys[d]; rows[d * ncols] (group-major: rows[j * ncols + c]).
+void oracle_multi_fetch(void* h, uint64_t* keys, oracle_scalar* rows) {
+  const MultiGroups* g = static_cast<const MultiGroups*>(h);
+  int64_t j = 0;
+  for (const auto& kv : g->m) {
+    keys[j] = kv.first;
+    for (int c = 0; c < g->ncols; ++c) {
+      oracle_scalar* o = &rows[j * g->ncols + c];
+      if (g->dts[c] == D_F32) emit(kv.second[c].f32, g->dts[c], o);
+      else if (g->dts[c] == D_F64) emit(kv.second[c].f64, g->dts[c], o);
+      else emit(kv.second[c].i, g->dts[c], o);
+    }
+    ++j;
+  }
+}
+
+void oracle_multi_free(void* h) { delete static_cast<MultiGroups*>(h); }
+
 void oracle_groups_fetch(void* h, uint32_t* keys, oracle_scalar* rows) {
   static_cast<GroupsBase*>(h)->fetch(keys, rows);
 }
