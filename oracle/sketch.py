@@ -74,3 +74,61 @@ def sketch(keys: np.ndarray, vbytes: int, nops: int, fp: int, slot_bytes: int, o
     f[14] = math.log2(1.0 + tb / l2_bytes)
     f[15] = math.log2(float(int(s.max()) - int(s.min())) + 1.0)
     return f
+
+
+# ---------------------------------------------------------------------------
+# HyperLogLog distinct-count estimate (Flajolet, Fusy, Gandouet and Meunier,
+# "HyperLogLog: the analysis of a near-optimal cardinality estimation
+# algorithm", AofA 2007), over every key of a column. The GROUP BY planner
+# sizes its tables from it when the sample does not cover a large column.
+# Hash of a key: SplitMix64's output function of (key XOR the golden-ratio
+# increment 0x9E3779B97F4A7C15), 64 bits; the top p = 14 bits pick one of
+# m = 2^14 registers, which keeps the largest rank (position of the first
+# one bit, from 1) of the remaining 50 bits (51 when they are all zero).
+# ---------------------------------------------------------------------------
+HLL_P = 14
+
+
+def _mix64(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.uint64)
+    with np.errstate(over="ignore"):
+        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
+        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
+    return z ^ (z >> np.uint64(31))
+
+
+def hll_registers(keys: np.ndarray, p: int = HLL_P) -> np.ndarray:
+    """The m = 2^p registers after adding every key."""
+    m = 1 << p
+    h = _mix64(np.asarray(keys, dtype=np.uint32).astype(np.uint64) ^ np.uint64(0x9E3779B97F4A7C15))
+    idx = (h >> np.uint64(64 - p)).astype(np.int64)
+    w = h << np.uint64(p)  # the remaining 64 - p bits, at the top
+    rank = np.full(h.size, 64 - p + 1, dtype=np.int64)
+    nz = w != 0
+    # position of the leading one bit of w, from 1: 64 - bit_length(w) + 1
+    bl = np.zeros(h.size, dtype=np.int64)
+    v = w[nz]
+    b = np.zeros(v.size, dtype=np.int64)
+    for s in (32, 16, 8, 4, 2, 1):
+        big = v >= (np.uint64(1) << np.uint64(s))
+        b[big] += s
+        v = np.where(big, v >> np.uint64(s), v)
+    bl[nz] = b + 1
+    rank[nz] = 64 - bl[nz] + 1
+    reg = np.zeros(m, dtype=np.int64)
+    np.maximum.at(reg, idx, rank)
+    return reg
+
+
+def hll_estimate(keys: np.ndarray, p: int = HLL_P) -> float:
+    """alpha_m m^2 / sum 2^-M_j, with linear counting m ln(m / V) below 5m/2 when V registers are zero."""
+    if np.asarray(keys).size == 0:
+        return 0.0
+    m = 1 << p
+    reg = hll_registers(keys, p)
+    alpha = 0.7213 / (1.0 + 1.079 / m)
+    e = alpha * m * m / float(np.sum(np.ldexp(1.0, -reg)))
+    zeros = int(np.count_nonzero(reg == 0))
+    if e <= 2.5 * m and zeros > 0:
+        e = m * math.log(m / zeros)
+    return e

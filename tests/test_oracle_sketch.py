@@ -2,6 +2,7 @@
 import math
 
 import numpy as np
+import pytest
 
 from oracle.sketch import SAMPLE, sample_positions, sketch
 
@@ -96,3 +97,41 @@ def test_table_size_features_on_closed_form_cases():
     args = dict(ARGS, slot_bytes=16, smem_bytes=float(2 ** 20), l2_bytes=float(2 ** 20) / 3.0)
     f = sketch(np.arange(SAMPLE * 64, dtype=np.uint32), **args)
     assert f[13] == 1.0 and f[14] == 2.0
+
+
+def test_hll_closed_forms():
+    from oracle.sketch import hll_estimate, hll_registers
+    assert hll_estimate(np.array([], dtype=np.uint32)) == 0.0
+    one = hll_registers(np.full(1000, 12345, dtype=np.uint32))
+    assert np.count_nonzero(one) == 1 and 1 <= one.max() <= 51
+    # one key: linear counting with V = m - 1 zero registers gives m ln(m / (m - 1)) ~ 1
+    m = 1 << 14
+    assert abs(hll_estimate(np.full(10, 7, dtype=np.uint32)) - m * math.log(m / (m - 1))) < 1e-9
+
+
+def test_hll_ignores_repeats_and_order():
+    from oracle.sketch import hll_estimate
+    rng = np.random.default_rng(4)
+    keys = rng.integers(0, 2 ** 32, 50_000, dtype=np.uint64).astype(np.uint32)
+    rep = np.concatenate([keys, keys[::3], keys[::7]])
+    rng.shuffle(rep)
+    assert hll_estimate(rep) == hll_estimate(np.unique(keys))
+
+
+def test_hll_rank_of_known_hashes():
+    """Register index and rank worked out by hand from the SplitMix64 output of key 0."""
+    from oracle.sketch import _mix64, hll_registers
+    h = int(_mix64(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0])
+    idx = h >> 50
+    w = (h << 14) & ((1 << 64) - 1)
+    rank = 64 - w.bit_length() + 1 if w else 51
+    reg = hll_registers(np.array([0], dtype=np.uint32))
+    assert reg[idx] == rank and np.count_nonzero(reg) == 1
+
+
+@pytest.mark.parametrize("d", [300, 20_000, 200_000, 3_000_000])
+def test_hll_within_its_error_bound(d):
+    """Relative standard error 1.04 / sqrt(m) = 0.81%; allow five of them."""
+    from oracle.sketch import hll_estimate
+    keys = np.arange(d, dtype=np.uint64).astype(np.uint32) * np.uint32(2654435761)
+    assert abs(hll_estimate(keys) / d - 1.0) < 5 * 1.04 / math.sqrt(1 << 14)
