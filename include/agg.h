@@ -273,6 +273,83 @@ agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* coun
 void agg_groups_free(agg_groups* g);
 
 /*
+ * Multi-column GROUP BY over a composite key with a fused range filter (the
+ * paper's future work fuses operators, Sec. 8: here a selection feeding the
+ * aggregation, in one scan).
+ *
+ * agg_column  one value column: device pointer to n values of dtype, and the
+ *             functions to compute on it (COUNT is per group, shared).
+ * agg_range   a predicate lo <= f[i] <= hi on a device column of n values of
+ *             dtype: integer columns compare with lo_i / hi_i (uint32 values
+ *             zero-extended), float columns with lo_f / hi_f (float32 widened
+ *             exactly); both bounds inclusive. A row that fails it takes no part.
+ * agg_multi   result, owned by the library (agg_multi_free): num_groups rows in
+ *             ascending order of the 64-bit key (key_hi << 32) | key_lo, each
+ *             with at least one row that passed the filter; count = rows that
+ *             passed; per value column c, sum[c] / min[c] / max[c] / avg[c] as
+ *             in agg_groups (int64 for integer columns, double for float).
+ *             Arrays are device memory; arrays of functions a column did not
+ *             ask for are unspecified.
+ */
+#define AGG_MAX_COLUMNS 4
+typedef struct agg_column {
+  const void* data;
+  int32_t dtype;
+  uint32_t ops;
+} agg_column;
+
+typedef struct agg_range {
+  const void* data;
+  int32_t dtype;
+  int32_t reserved;
+  int64_t lo_i, hi_i;
+  double lo_f, hi_f;
+} agg_range;
+
+typedef struct agg_multi {
+  int64_t num_groups;
+  int32_t ncols;
+  int32_t retries;      /* times the key table was regrown */
+  int64_t table_slots;  /* key table slots used */
+  uint64_t* keys;
+  int64_t* count;
+  void* sum[AGG_MAX_COLUMNS];
+  void* min[AGG_MAX_COLUMNS];
+  void* max[AGG_MAX_COLUMNS];
+  double* avg[AGG_MAX_COLUMNS];
+  void* priv;
+} agg_multi;
+
+/*
+ * agg_groupby_multi -- SUM/MIN/MAX/COUNT/AVG of up to AGG_MAX_COLUMNS value
+ * columns per distinct composite key over the rows that pass `filter`.
+ *
+ *  key_lo_dev  device pointer to n uint32 low key words
+ *  key_hi_dev  device pointer to n uint32 high key words, or NULL (high word 0)
+ *  n           0 <= n < 2^32
+ *  cols/ncols  1 <= ncols <= AGG_MAX_COLUMNS value columns
+ *  filter      NULL (every row) or a range predicate
+ *
+ * One fused scan: the filter column is read first and a failing row reads
+ * nothing else; a passing row finds its key's slot in a hash table of 64-bit
+ * keys (sized from the key columns' sketches, regrown 4x if it fills) and
+ * folds every value column into that slot's accumulators (per-block shared
+ * memory when they fit, else HBM). Synchronous (one read-back). Integer
+ * results, COUNT and MIN/MAX are exact; float sums as in agg_groupby.
+ * Errors: AGG_ERR_INVALID, AGG_ERR_OOM, AGG_ERR_CUDA, AGG_ERR_TABLE_FULL.
+ */
+agg_status agg_groupby_multi(const uint32_t* key_lo_dev, const uint32_t* key_hi_dev, int64_t n,
+                             const agg_column* cols, int ncols, const agg_range* filter, agg_multi** out,
+                             void* stream);
+/* Copy the keys, counts and column col's arrays to host buffers of num_groups
+   elements (any may be NULL). Synchronous. */
+agg_status agg_multi_to_host(const agg_multi* m, uint64_t* keys, int64_t* count, int col, void* sum, void* min,
+                             void* max, double* avg);
+/* Release a result (NULL is allowed); memory is returned in stream order on
+   the stream of the call that produced it. */
+void agg_multi_free(agg_multi* m);
+
+/*
  * agg_sketch -- the 16 features of a sample of keys that the strategy
  * selectors read (written to features_dev[0..16) as float32, asynchronously):
  *   0 log2 n            1 value bytes        2 popcount(ops)      3 float values
@@ -288,6 +365,18 @@ void agg_groups_free(agg_groups* g);
  */
 agg_status agg_sketch(const uint32_t* keys_dev, int64_t n, agg_dtype vdtype, uint32_t ops,
                       uint64_t sample_offset, float* features_dev, void* stream);
+
+/*
+ * agg_distinct_estimate -- HyperLogLog estimate (Flajolet, Fusy, Gandouet and
+ * Meunier 2007) of the number of distinct values among keys_dev[0..n), with
+ * 2^14 registers (relative standard error about 0.8%), in one pass over the
+ * keys; *estimate_host is valid when the call returns (synchronous). GROUP BY
+ * plans its tables from this count when a column of at least 2^22 rows is not
+ * covered by its 4096-key sample (the paper's related work chooses group-by
+ * configurations from a model of the input, Sec. 7). Errors: AGG_ERR_INVALID,
+ * AGG_ERR_OOM, AGG_ERR_CUDA.
+ */
+agg_status agg_distinct_estimate(const uint32_t* keys_dev, int64_t n, double* estimate_host, void* stream);
 
 /*
  * Batched GROUP BY: many independent queries in one persistent

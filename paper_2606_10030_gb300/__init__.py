@@ -138,6 +138,30 @@ class AggGroups(ctypes.Structure):
         ("priv", ctypes.c_void_p),
     ]
 
+AGG_MAX_COLUMNS = 4
+
+
+class AggColumn(ctypes.Structure):
+    """Mirror of ``agg_column``."""
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("ops", ctypes.c_uint32)]
+
+
+class AggRange(ctypes.Structure):
+    """Mirror of ``agg_range``."""
+    _fields_ = [("data", ctypes.c_void_p), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("lo_i", ctypes.c_int64), ("hi_i", ctypes.c_int64), ("lo_f", ctypes.c_double),
+                ("hi_f", ctypes.c_double)]
+
+
+class AggMulti(ctypes.Structure):
+    """Mirror of ``agg_multi``."""
+    _fields_ = [("num_groups", ctypes.c_int64), ("ncols", ctypes.c_int32), ("retries", ctypes.c_int32),
+                ("table_slots", ctypes.c_int64), ("keys", ctypes.c_void_p), ("count", ctypes.c_void_p),
+                ("sum", ctypes.c_void_p * AGG_MAX_COLUMNS), ("min", ctypes.c_void_p * AGG_MAX_COLUMNS),
+                ("max", ctypes.c_void_p * AGG_MAX_COLUMNS), ("avg", ctypes.c_void_p * AGG_MAX_COLUMNS),
+                ("priv", ctypes.c_void_p)]
+
+
 _lib = None
 
 # name -> (restype, argtypes) of every exported entry point
@@ -151,6 +175,10 @@ SIGNATURES = {
     "agg_groups_to_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
     "agg_groups_free": (None, [_vp]),
     "agg_sketch": (_i32, [_vp, _i64, _i32, _u32, ctypes.c_uint64, _vp, _vp]),
+    "agg_groupby_multi": (_i32, [_vp, _vp, _i64, _vp, _i32, _vp, _vp, _vp]),
+    "agg_distinct_estimate": (_i32, [_vp, _i64, _vp, _vp]),
+    "agg_multi_to_host": (_i32, [_vp, _vp, _vp, _i32, _vp, _vp, _vp, _vp]),
+    "agg_multi_free": (None, [_vp]),
     "agg_autotune": (_i32, [_vp, _vp, _i64, _i32, _u32, _i32, _vp, _vp]),
     "agg_autotune_cache_size": (ctypes.c_int64, []),
     "agg_autotune_clear": (None, []),
@@ -359,6 +387,88 @@ def agg_groupby_host(keys, vals, ops: int = AGG_ALL, opts: AggOptions | None = N
                                  ctypes.byref(opts) if opts is not None else None, ctypes.byref(out),
                                  _stream_ptr(stream)))
     return Groups(out.value)
+
+
+class Multi:
+    """A multi-column GROUP BY result owned by the library; ``to_host()`` copies it to NumPy."""
+
+    def __init__(self, ptr, dtypes):
+        self._ptr = ptr
+        m = ctypes.cast(ptr, ctypes.POINTER(AggMulti)).contents
+        self.num_groups = int(m.num_groups)
+        self.ncols = int(m.ncols)
+        self.retries = int(m.retries)
+        self.table_slots = int(m.table_slots)
+        self.dtypes = dtypes
+
+    def to_host(self) -> dict:
+        d = self.num_groups
+        keys = np.empty(d, np.uint64)
+        count = np.empty(d, np.int64)
+        p = lambda a: a.ctypes.data_as(ctypes.c_void_p)  # noqa: E731
+        out = {"keys": keys, "count": count, "cols": []}
+        for c in range(self.ncols):
+            fp = self.dtypes[c] in (AGG_F32, AGG_F64)
+            s = np.empty(d, np.float64 if fp else np.int64)
+            mn = np.empty(d, np.float64 if fp else np.int64)
+            mx = np.empty(d, np.float64 if fp else np.int64)
+            avg = np.empty(d, np.float64)
+            check(lib().agg_multi_to_host(self._ptr, p(keys) if c == 0 else None, p(count) if c == 0 else None, c,
+                                          p(s), p(mn), p(mx), p(avg)))
+            out["cols"].append({"sum": s, "min": mn, "max": mx, "avg": avg})
+        return out
+
+    def free(self):
+        if self._ptr:
+            lib().agg_multi_free(self._ptr)
+            self._ptr = None
+
+    def __del__(self):
+        try:
+            self.free()
+        except Exception:
+            pass
+
+
+def agg_groupby_multi(key_lo, key_hi, cols, filt=None, stream=None) -> Multi:
+    """GROUP BY the 64-bit key (key_hi << 32) | key_lo over device tensors.
+
+    cols: list of (values, ops); filt: None or (column, lo, hi), both bounds inclusive.
+    """
+    n = key_lo.numel()
+    arr = (AggColumn * len(cols))()
+    keep = [key_lo, key_hi]
+    for i, (v, ops) in enumerate(cols):
+        assert v.is_cuda and v.numel() == n and v.is_contiguous()
+        arr[i].data = v.data_ptr() if n else None
+        arr[i].dtype = dtype_code(v)
+        arr[i].ops = ops
+        keep.append(v)
+    rng = None
+    if filt is not None:
+        f, lo, hi = filt
+        assert f.is_cuda and f.numel() == n and f.is_contiguous()
+        rng = AggRange()
+        rng.data = f.data_ptr() if n else None
+        rng.dtype = dtype_code(f)
+        if rng.dtype in (AGG_F32, AGG_F64):
+            rng.lo_f, rng.hi_f = float(lo), float(hi)
+        else:
+            rng.lo_i, rng.hi_i = int(lo), int(hi)
+    out = ctypes.c_void_p()
+    check(lib().agg_groupby_multi(ctypes.c_void_p(key_lo.data_ptr()) if n else None,
+                                  ctypes.c_void_p(key_hi.data_ptr()) if key_hi is not None and n else None, n, arr,
+                                  len(cols), ctypes.byref(rng) if rng is not None else None, ctypes.byref(out),
+                                  _stream_ptr(stream)))
+    return Multi(out.value, [dtype_code(v) for v, _ in cols])
+
+
+def agg_distinct_estimate(keys, stream=None) -> float:
+    """HyperLogLog estimate of the distinct keys of a uint32 device tensor (synchronous)."""
+    est = ctypes.c_double(0.0)
+    check(lib().agg_distinct_estimate(ctypes.c_void_p(keys.data_ptr()) if keys.numel() else None, keys.numel(),
+                                      ctypes.byref(est), _stream_ptr(stream)))
+    return float(est.value)
 
 
 def agg_sketch(keys, vdtype: int, ops: int = AGG_ALL, sample_offset: int = 0, out=None, stream=None):

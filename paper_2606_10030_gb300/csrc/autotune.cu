@@ -33,7 +33,8 @@ Sig signature(int vdt, uint32_t ops, const float* f) {
 }  // namespace
 
 agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                        const agg_options& o, cudaStream_t s, agg_groups** out, const float* known_feat);
+                        const agg_options& o, cudaStream_t s, agg_groups** out, const float* known_feat,
+                        double known_hll);
 
 static int smem_slots_sized(const float* f, bool mm) {
   bool covered = false;
@@ -46,7 +47,7 @@ static int smem_slots_sized(const float* f, bool mm) {
 }
 
 static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                                 const float* feat, int reps, cudaStream_t s, agg_tune_result* r) {
+                                 const float* feat, double hll, int reps, cudaStream_t s, agg_tune_result* r) {
   std::memset(r, 0, sizeof(*r));
   std::memcpy(r->features, feat, sizeof(float) * F_COUNT);
   const bool mm = ops_minmax(ops);
@@ -66,7 +67,7 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
   agg_status st = AGG_OK;
   // every candidate gets the global table size the sketch implies, so that
   // none of them pays for a second sketch of its own
-  const int64_t tslots = table_slots_from_sketch(feat, n);
+  const int64_t tslots = table_slots_for(feat, n, hll);
   for (int i = 0; i < nc && st == AGG_OK; ++i) {
     agg_options o{};
     o.strategy = c[i].strategy;
@@ -77,7 +78,7 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
     for (int rep = 0; rep < std::max(1, reps) && st == AGG_OK; ++rep) {
       agg_groups* g = nullptr;
       cudaEventRecord(a, s);
-      st = groupby_with(keys, vals, n, vdt, ops, o, s, &g, feat);
+      st = groupby_with(keys, vals, n, vdt, ops, o, s, &g, feat, hll);
       cudaEventRecord(b, s);
       if (st != AGG_OK) break;
       cudaEventSynchronize(b);
@@ -106,7 +107,8 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
 }
 
 agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                         const float* feat, cudaStream_t s, int* strategy, int* smem_slots, int64_t* table_slots) {
+                         const float* feat, double hll, cudaStream_t s, int* strategy, int* smem_slots,
+                         int64_t* table_slots) {
   *table_slots = 0;
   {
     std::lock_guard<std::mutex> lk(g_tmu);
@@ -118,7 +120,7 @@ agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int 
     }
   }
   agg_tune_result r;
-  agg_status st = run_candidates(keys, vals, n, vdt, ops, feat, 1, s, &r);
+  agg_status st = run_candidates(keys, vals, n, vdt, ops, feat, hll, 1, s, &r);
   if (st != AGG_OK) return st;
   *strategy = r.strategy[r.best];
   *smem_slots = r.smem_slots[r.best];
@@ -143,7 +145,12 @@ extern "C" agg_status agg_autotune(const uint32_t* keys_dev, const void* vals_de
   float feat[F_COUNT];
   agg_status st = sketch_features(keys_dev, n, vdtype, ops, 0, s, feat);
   if (st != AGG_OK) return st;
-  return run_candidates(keys_dev, vals_dev, n, vdtype, ops, feat, reps, s, out);
+  double hll = 0.0;
+  if (wants_hll(feat, n)) {
+    st = hll_estimate(keys_dev, n, s, &hll);
+    if (st != AGG_OK) return st;
+  }
+  return run_candidates(keys_dev, vals_dev, n, vdtype, ops, feat, hll, reps, s, out);
 }
 
 extern "C" int64_t agg_autotune_cache_size(void) {

@@ -172,12 +172,19 @@ int64_t table_slots_from_sketch(const float* f, int64_t n) {
 //    many more keys than Chao1);
 //  - a skewed sample far from covering the column: SMEM on hash-partitioned
 //    rows from 2^25 rows on, SORT below.
-int rule_strategy(const float* f, uint32_t ops) {
+int rule_strategy(const float* f, uint32_t ops, double hll) {
   const KeyEstimate e = key_estimate(f);
   const int cap = ops_minmax(ops) ? 1536 : 3072;  // 3/4 of the largest shared tables
   const double coverage = 1.0 - (double)f[F_F1];  // F_F1 = f1 / m
   const float log2n = f[F_LOG2N];
   if (coverage >= 0.97) return AGG_STRAT_SMEM;
+  // with the column's HyperLogLog count: a hot head that shared tables absorb
+  // (the rest spilling to a right-sized table), or a flat column of up to 2^23
+  // keys (hash-partitioned shared tables); larger flat columns sort
+  if (hll > 0.0) {
+    if (hot_sample(f, cap) || hll <= cap) return AGG_STRAT_SMEM;
+    if (e.flat) return hll <= 8388608.0 ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
+  }
   if (log2n < 20.0f) return (e.plan <= cap || !e.flat) ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
   const double m = std::min(std::exp2((double)log2n), (double)kSketchSample);
   const double d = (double)f[F_DISTINCT] * m, f1 = (double)f[F_F1] * m, f2 = (double)f[F_F2] * m;
@@ -515,7 +522,8 @@ int select_learned(const float* feat, bool* ok);
 agg_status sketch_and_select(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
                              cudaStream_t s, float* feat, int* strategy);
 agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                         const float* feat, cudaStream_t s, int* strategy, int* smem_slots, int64_t* table_slots);
+                         const float* feat, double hll, cudaStream_t s, int* strategy, int* smem_slots,
+                         int64_t* table_slots);
 
 // Sketch the keys on the device and read the features back (one sync).
 agg_status sketch_features(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
@@ -556,26 +564,49 @@ struct Choice {
   HashPlan plan;
 };
 
+bool wants_hll(const float* f, int64_t n) {
+  return n >= (int64_t(1) << 22) && 1.0 - (double)f[F_F1] < 0.97;
+}
+
+bool hot_sample(const float* f, int cap) {
+  const double m = std::min(std::exp2((double)f[F_LOG2N]), (double)kSketchSample);
+  return 1.0 - (double)f[F_F1] >= 0.9 && (double)f[F_DISTINCT] * m <= (double)cap;
+}
+
+// Global-table slots for a column with about `keys` distinct keys (a
+// HyperLogLog count, relative error about 1%): load at most about 1/2.
+static int64_t slots_for_count(double keys, int64_t n) {
+  const int64_t cap = std::min<int64_t>(int64_t(1) << 31, next_pow2(std::max<int64_t>(2 * n, 1024)));
+  return std::min<int64_t>(cap, std::max<int64_t>(1024, next_pow2((int64_t)std::ceil(2.2 * keys))));
+}
+
+int64_t table_slots_for(const float* feat, int64_t n, double hll) {
+  return hll > 0.0 ? slots_for_count(hll, n) : table_slots_from_sketch(feat, n);
+}
+
 static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                         const agg_options& o, const float* feat, bool have_feat, cudaStream_t s, Choice* c) {
+                         const agg_options& o, const float* feat, bool have_feat, double hll, cudaStream_t s,
+                         Choice* c) {
   bool covered = false;
-  const double est = have_feat ? distinct_estimate(feat, &covered) : 1024.0;
+  double est = have_feat ? distinct_estimate(feat, &covered) : 1024.0;
+  if (hll > 0.0) est = hll;
   int strategy = o.strategy;
   int64_t tslots = o.table_slots;
   int sslots = o.smem_slots;
   if (strategy == AGG_STRAT_LEARNED) {
     bool ok = false;
     strategy = select_learned(feat, &ok);
-    if (!ok) strategy = rule_strategy(feat, ops);
+    if (!ok) strategy = rule_strategy(feat, ops, hll);
   } else if (strategy == AGG_STRAT_AUTOTUNE) {
-    agg_status st = autotune_pick(keys, vals, n, vdt, ops, feat, s, &strategy, &sslots, &tslots);
+    agg_status st = autotune_pick(keys, vals, n, vdt, ops, feat, hll, s, &strategy, &sslots, &tslots);
     if (st != AGG_OK) return st;
   } else if (strategy == AGG_STRAT_AUTO) {
-    strategy = have_feat ? rule_strategy(feat, ops) : AGG_STRAT_GLOBAL;
+    strategy = have_feat ? rule_strategy(feat, ops, hll) : AGG_STRAT_GLOBAL;
   }
   c->strategy = strategy;
   c->plan.strategy = strategy;
-  c->plan.slots = tslots ? tslots : (have_feat ? table_slots_from_sketch(feat, n) : 2048);
+  c->plan.slots = tslots ? tslots
+                         : hll > 0.0 ? slots_for_count(hll, n) : (have_feat ? table_slots_from_sketch(feat, n) : 2048);
   c->plan.smem_slots = sslots ? sslots : smem_slots_for(est, ops_minmax(ops));
   c->plan.threads = o.block_threads ? o.block_threads : (strategy == AGG_STRAT_SMEM ? 512 : 256);
   // frequent keys (a key with >= 3% of the sample, or a handful of keys) make
@@ -586,7 +617,10 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   // distinct keys than a shared table admits) or the global table exceeds
   // half of L2; each partition then has about 1/256 of the keys.
   const double table_bytes = (double)(c->plan.slots + 2) * gslot_bytes(ops_minmax(ops));
-  const bool spills = strategy == AGG_STRAT_SMEM && est > 0.75 * c->plan.smem_slots;
+  // a hot head that the shared tables absorb needs no partitioning: the few
+  // rows of rarer keys spill to the (right-sized) global table
+  const bool hot = hll > 0.0 && hot_sample(feat, (c->plan.smem_slots * 3) / 4);
+  const bool spills = strategy == AGG_STRAT_SMEM && est > 0.75 * c->plan.smem_slots && !hot;
   const bool big_table = table_bytes > 0.5 * device_info().l2_bytes;
   c->plan.partition = o.partition > 0 || (o.partition == 0 && n >= (int64_t(1) << 20) && (spills || big_table));
   // two levels (65536 partitions) when 256 partitions would still spill
@@ -657,23 +691,30 @@ namespace agg {
 // null, is the column's sketch (the autotuner passes it, so that its timed
 // candidates plan partitioning exactly as the untuned call would).
 agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
-                        const agg_options& o, cudaStream_t s, agg_groups** out, const float* known_feat) {
+                        const agg_options& o, cudaStream_t s, agg_groups** out, const float* known_feat,
+                        double known_hll) {
   float feat[F_COUNT] = {0};
   bool have = false;
+  double hll = 0.0;
   agg_status st = AGG_OK;
   if (known_feat && n > 0) {
     std::memcpy(feat, known_feat, sizeof(feat));
     have = true;
+    hll = known_hll;
   } else if (needs_sketch(o) && n > 0) {
     if (o.strategy == AGG_STRAT_LEARNED) {
       int learned = -1;
       st = sketch_and_select(keys, n, vdt, ops, o.sample_offset, s, feat, &learned);
       if (st != AGG_OK) return st;
       have = true;
+      if (wants_hll(feat, n)) {
+        st = hll_estimate(keys, n, s, &hll);
+        if (st != AGG_OK) return st;
+      }
       agg_options o2 = o;
-      o2.strategy = learned >= 0 ? learned : rule_strategy(feat, ops);
+      o2.strategy = learned >= 0 ? learned : rule_strategy(feat, ops, hll);
       Choice c;
-      st = choose(keys, vals, n, vdt, ops, o2, feat, have, s, &c);
+      st = choose(keys, vals, n, vdt, ops, o2, feat, have, hll, s, &c);
       if (st != AGG_OK) return st;
       agg_groups* g = nullptr;
       if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g, feat);
@@ -686,9 +727,13 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
     st = sketch_features(keys, n, vdt, ops, o.sample_offset, s, feat);
     if (st != AGG_OK) return st;
     have = true;
+    if (wants_hll(feat, n)) {
+      st = hll_estimate(keys, n, s, &hll);
+      if (st != AGG_OK) return st;
+    }
   }
   Choice c;
-  st = choose(keys, vals, n, vdt, ops, o, feat, have, s, &c);
+  st = choose(keys, vals, n, vdt, ops, o, feat, have, hll, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
   if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g, have ? feat : nullptr);
@@ -710,7 +755,7 @@ static agg_status groupby_impl(const uint32_t* keys, const void* vals, int64_t n
                                const agg_options* opt, cudaStream_t s, agg_groups** out) {
   agg_options o{};
   if (opt) o = *opt;
-  agg_status st = groupby_with(keys, vals, n, vdt, ops, o, s, out, nullptr);
+  agg_status st = groupby_with(keys, vals, n, vdt, ops, o, s, out, nullptr, 0.0);
   const bool exact = o.flags & AGG_FLAG_EXACT_SUM, report = o.flags & AGG_FLAG_SUM_ERROR;
   if (st == AGG_OK && (exact || report) && dtype_is_fp(vdt) && (ops & (AGG_SUM | AGG_AVG))) {
     st = exact_fp_sums(keys, vals, n, vdt, ops, *out, s, exact, report);
@@ -837,7 +882,7 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
   Choice c;
   // the autotuner times candidates on a device column: give it the first chunk
   cudaStreamWaitEvent(s, pipe->ready[0], 0);
-  st = choose(kbuf(0), vbuf(0), std::min<int64_t>(chunk, n), vdt, ops, o, feat, have, s, &c);
+  st = choose(kbuf(0), vbuf(0), std::min<int64_t>(chunk, n), vdt, ops, o, feat, have, 0.0, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
   // The sort, and hash plans that partition the rows, work on the whole

@@ -33,8 +33,19 @@ agg_status sketch_features(const uint32_t* keys, int64_t n, int vdt, uint32_t op
 inline int gslot_bytes(bool minmax) { return minmax ? 32 : 16; }
 inline bool ops_minmax(uint32_t ops) { return ops & (AGG_MIN | AGG_MAX); }
 
-// Strategy choice without a learned model: a rule on the sketch.
-int rule_strategy(const float* feat, uint32_t ops);
+// Strategy choice without a learned model: a rule on the sketch (and the
+// HyperLogLog count of the column's keys when it was taken, else 0).
+int rule_strategy(const float* feat, uint32_t ops, double hll = 0.0);
+
+// HyperLogLog estimate of the distinct keys of a device key column (one pass
+// over the keys, one read-back).
+agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est);
+// Whether planning a GROUP BY of n rows with this sketch takes a HyperLogLog
+// count first: a large column whose sample does not cover its keys.
+bool wants_hll(const float* feat, int64_t n);
+// The sample's keys hold most of the column and fit a shared table of cap keys
+// (a hot head that per-block tables absorb, the rest spilling).
+bool hot_sample(const float* feat, int cap);
 // Distinct-key estimates from a sketch.
 struct KeyEstimate {
   double chao1, gee;
@@ -48,6 +59,8 @@ KeyEstimate key_estimate(const float* feat);
 double distinct_estimate(const float* feat, bool* covered);
 // Global hash-table slots for a column of n rows from its sketch (power of two).
 int64_t table_slots_from_sketch(const float* feat, int64_t n);
+// The same from the HyperLogLog count when one was taken (hll > 0).
+int64_t table_slots_for(const float* feat, int64_t n, double hll);
 
 // Output block shared by the results of one batch (reference counted).
 struct SharedBlock;

@@ -15,10 +15,10 @@
 // 0xFFFFFFFF has its own side slot after the main slots. All global
 // accumulators start at zero: count and sum add, MIN is kept as the
 // complement of an order-preserving image and MAX as the image, both updated
-// with atomicMax. Float sums in the global table: a float32 column keeps a
-// TwoSum-compensated float32 pair (s, c) in the slot's 8-byte sum word (the
-// adder recovers the exact rounding error of its own atomic add of s from the
-// value the atomic returns and adds it to c); a float64 column adds float64.
+// with atomicMax; float sums in the global table are float64 (L2 atomic adds:
+// a per-block or per-warp compensated float32 partial, or a single row, is
+// merged into a float64 accumulator; the float64 additions run in the L2's
+// atomic units, not on the SM's narrow float64 pipe).
 #pragma once
 
 #include <cstring>
@@ -109,25 +109,11 @@ __device__ __forceinline__ int64_t g_slot(GSlot<MM>* tab, uint32_t mask, int shi
   return -1;
 }
 
-// Add a compensated float32 pair (ps, pc) to the pair (s, c) at w[0], w[1]:
-// the atomic add of ps into s rounds; TwoSum of the value it replaced and ps
-// recovers that rounding exactly, and it goes to c with pc.
-__device__ __forceinline__ void g_add_f32_pair(unsigned long long* word, float ps, float pc) {
-  float* w = (float*)word;
-  const float old = atomicAdd(&w[0], ps);
-  float t, e;
-  two_sum(old, ps, t, e);
-  const float c = e + pc;
-  if (c != 0.f) atomicAdd(&w[1], c);
-}
-
 // Fold one row (or a merged partial) into a global slot.
 template <int DT, bool MM>
 __device__ __forceinline__ void g_add_row(GSlot<MM>& s, typename GV<DT>::T v) {
   atomicAdd(&s.cnt, 1u);
-  if (DT == AGG_F32) {
-    g_add_f32_pair(&s.sum, (float)v, 0.f);
-  } else if (DT == AGG_F64) {
+  if (DT == AGG_F32 || DT == AGG_F64) {
     atomicAdd((double*)&s.sum, (double)v);
   } else {
     atomicAdd(&s.sum, (unsigned long long)(int64_t)v);
@@ -299,9 +285,7 @@ __device__ __noinline__ int s_lookup(const STab<DT, MM>& t, int S, int cap, uint
 template <int DT, bool MM>
 __device__ __forceinline__ void g_add_row_cached(GSlot<MM>& s, typename GV<DT>::T v) {
   atomicAdd(&s.cnt, 1u);
-  if (DT == AGG_F32) {
-    g_add_f32_pair(&s.sum, (float)v, 0.f);
-  } else if (DT == AGG_F64) {
+  if (DT == AGG_F32 || DT == AGG_F64) {
     atomicAdd((double*)&s.sum, (double)v);
   } else {
     atomicAdd(&s.sum, (unsigned long long)(int64_t)v);
@@ -530,7 +514,7 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
   }
   GSlot<MM>& gs = tab[g];
   atomicAdd(&gs.cnt, p.cnt);
-  if (DT == AGG_F32) g_add_f32_pair(&gs.sum, p.fs, p.fc);
+  if (DT == AGG_F32) atomicAdd((double*)&gs.sum, (double)p.fs + (double)p.fc);
   else if (DT == AGG_F64) atomicAdd((double*)&gs.sum, p.ds);
   else atomicAdd(&gs.sum, p.isum);
   if (MM) {
@@ -722,7 +706,8 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     atomicAdd(&gs.cnt, c);
     const unsigned long long sv = st.sum[j];
     if (DT == AGG_F32) {
-      g_add_f32_pair(&gs.sum, __uint_as_float((uint32_t)sv), __uint_as_float((uint32_t)(sv >> 32)));
+      const double d = (double)__uint_as_float((uint32_t)sv) + (double)__uint_as_float((uint32_t)(sv >> 32));
+      atomicAdd((double*)&gs.sum, d);
     } else if (DT == AGG_F64) {
       atomicAdd((double*)&gs.sum, __longlong_as_double((long long)sv));
     } else {
@@ -819,17 +804,11 @@ __device__ __forceinline__ void write_group(const OutArrays& o, int64_t i, uint3
   const uint32_t c = s.cnt;
   o.keys[i] = key;
   o.count[i] = c;
-  unsigned long long sv = s.sum;
-  double fsum;
-  if (DT == AGG_F32) {  // the compensated pair, merged in float64
-    fsum = (double)__uint_as_float((uint32_t)sv) + (double)__uint_as_float((uint32_t)(sv >> 32));
-    sv = (unsigned long long)__double_as_longlong(fsum);
-  } else if (DT == AGG_F64) {
-    fsum = __longlong_as_double((long long)sv);
-  } else {
-    fsum = (double)(long long)sv;
-  }
+  const unsigned long long sv = s.sum;
   o.sum[i] = sv;
+  double fsum;
+  if (DT == AGG_F32 || DT == AGG_F64) fsum = __longlong_as_double((long long)sv);
+  else fsum = (double)(long long)sv;
   o.avg[i] = fsum / (double)c;
   if (MM) {
     const GSlot<true>& w = (const GSlot<true>&)s;

@@ -1,0 +1,165 @@
+// HyperLogLog estimate of the distinct keys of a column (Flajolet, Fusy,
+// Gandouet and Meunier, AofA 2007), one pass over every key. The GROUP BY
+// planner sizes its hash tables from it when the 4096-key sample does not
+// cover a large column (a long tail of rare keys the sample cannot see).
+//
+// A key's 64-bit hash is SplitMix64's output function of (key XOR the
+// golden-ratio increment); its top 14 bits pick one of m = 2^14 registers,
+// which keeps the largest rank (position of the first one bit, from 1) of the
+// remaining 50 bits. Each block keeps its registers in shared memory (a rank
+// is written only when it exceeds the register, so repeated keys cost a
+// shared-memory read), merges them into the column's registers with atomicMax,
+// and the last block to finish (fence plus ticket, no waiting) forms the
+// estimate alpha_m m^2 / sum 2^-M_j (linear counting m ln(m / V) below 5m/2
+// when V registers are zero). The registers and the ticket live in the
+// stream's scratch and are cleared before every launch.
+#include <cmath>
+
+#include "groupby.cuh"
+
+namespace agg {
+
+constexpr int kHllP = 14;
+constexpr int kHllM = 1 << kHllP;
+constexpr int kHllThreads = 512;
+constexpr size_t kHllScratchOff = 8192;  // in the stream scratch, past the scan ticket
+constexpr size_t kHllScratchBytes = kHllScratchOff + (size_t)kHllM * 4 + 256;
+
+__device__ __forceinline__ void hll_add(uint32_t* sreg, uint32_t key) {
+  uint64_t z = (uint64_t)key ^ 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  const uint32_t idx = (uint32_t)(z >> (64 - kHllP));
+  const uint32_t rank = (uint32_t)__clzll((long long)((z << kHllP) | (1ull << (kHllP - 1)))) + 1u;  // 1..51
+  if (rank > *(volatile uint32_t*)&sreg[idx]) atomicMax(&sreg[idx], rank);
+}
+
+// regs[kHllM], then the ticket (+kHllM * 4) and the estimate (+kHllM * 4 + 8, double).
+__global__ void __launch_bounds__(kHllThreads) hll_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t head,
+                                                          uint32_t* __restrict__ regs) {
+  extern __shared__ uint32_t sreg[];
+  __shared__ double red[33];
+  __shared__ int s_last;
+  unsigned* ticket = regs + kHllM;
+  double* est = (double*)(regs + kHllM + 2);
+  for (int i = threadIdx.x; i < kHllM; i += blockDim.x) sreg[i] = 0;
+  __syncthreads();
+  const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
+  const int64_t nq = (n - head) / 4;
+  const int64_t tail0 = head + nq * 4;
+  if (g < head) hll_add(sreg, keys[g]);
+  if (g < n - tail0) hll_add(sreg, keys[tail0 + g]);
+  const uint4* kq = (const uint4*)(keys + head);
+  for (int64_t q = g; q < nq; q += 2 * nthreads) {
+    const uint4 a = ld_stream_v4(kq + q);
+    const bool two = q + nthreads < nq;
+    const uint4 b = two ? ld_stream_v4(kq + q + nthreads) : make_uint4(0, 0, 0, 0);
+    hll_add(sreg, a.x);
+    hll_add(sreg, a.y);
+    hll_add(sreg, a.z);
+    hll_add(sreg, a.w);
+    if (two) {
+      hll_add(sreg, b.x);
+      hll_add(sreg, b.y);
+      hll_add(sreg, b.z);
+      hll_add(sreg, b.w);
+    }
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < kHllM; i += blockDim.x) {
+    const uint32_t r = sreg[i];
+    if (r != 0 && r > __ldcg(&regs[i])) atomicMax(&regs[i], r);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  double sum = 0.0, zeros = 0.0;
+  for (int i = threadIdx.x; i < kHllM; i += blockDim.x) {
+    const uint32_t r = __ldcg(&regs[i]);
+    sum += ldexp(1.0, -(int)r);
+    zeros += r == 0 ? 1.0 : 0.0;
+  }
+  // block sums in a fixed order
+#pragma unroll
+  for (int o = 16; o >= 1; o >>= 1) {
+    sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    zeros += __shfl_xor_sync(0xffffffffu, zeros, o);
+  }
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+  if (l == 0) red[w] = sum;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) t += red[i];
+    red[32] = t;
+  }
+  __syncthreads();
+  const double tot = red[32];
+  __syncthreads();
+  if (l == 0) red[w] = zeros;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double v = 0.0;
+    for (int i = 0; i < (int)(blockDim.x >> 5); ++i) v += red[i];
+    const double m = (double)kHllM;
+    const double alpha = 0.7213 / (1.0 + 1.079 / m);
+    double e = alpha * m * m / tot;
+    if (e <= 2.5 * m && v > 0.0) e = m * log(m / v);
+    *est = e;
+  }
+}
+
+agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est) {
+  *est = 0.0;
+  if (n <= 0) return AGG_OK;
+  agg_status st = AGG_OK;
+  char* scr = (char*)stream_scratch(s, kHllScratchBytes, &st);
+  if (!scr) return st;
+  uint32_t* regs = (uint32_t*)(scr + kHllScratchOff);
+  static bool attr_set[64] = {};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 64 && !attr_set[dev]) {
+    AGG_CUDA_TRY(cudaFuncSetAttribute(hll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kHllM * 4));
+    attr_set[dev] = true;
+  }
+  int64_t head = (int64_t)(((16 - ((uintptr_t)keys & 15)) & 15) / 4);
+  if (head > n) head = n;
+  int bps = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, hll_kernel, kHllThreads, kHllM * 4) != cudaSuccess ||
+      bps < 1)
+    bps = 1;
+  int64_t grid = (int64_t)device_info().sm_count * bps;
+  const int64_t need = ((n - head) / 4 + 2 * kHllThreads - 1) / (2 * kHllThreads);
+  if (need < grid) grid = std::max<int64_t>(1, need);
+  AGG_CUDA_TRY(cudaMemsetAsync(regs, 0, (size_t)kHllM * 4 + 8, s));  // registers and ticket
+  {
+    PhaseTimer pt(AGG_PHASE_SKETCH, s);
+    hll_kernel<<<(unsigned)grid, kHllThreads, kHllM * 4, s>>>(keys, n, head, regs);
+    note_launch();
+    AGG_CUDA_TRY(cudaGetLastError());
+  }
+  double* hb = (double*)stream_pinned(s, 256, &st);
+  if (!hb) return st;
+  AGG_CUDA_TRY(cudaMemcpyAsync(hb, regs + kHllM + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AGG_CUDA_TRY(cudaStreamSynchronize(s));
+  *est = hb[0];
+  return AGG_OK;
+}
+
+}  // namespace agg
+
+extern "C" agg_status agg_distinct_estimate(const uint32_t* keys_dev, int64_t n, double* estimate_host, void* stream) {
+  using namespace agg;
+  clear_error();
+  AGG_CHECK_ARG(estimate_host != nullptr, "null output pointer");
+  AGG_CHECK_ARG(n >= 0 && n < (int64_t(1) << 62), "invalid row count %lld", (long long)n);
+  AGG_CHECK_ARG(n == 0 || keys_dev != nullptr, "null key pointer");
+  AGG_CHECK_ARG(((uintptr_t)keys_dev & 3) == 0, "key pointer not 4-byte aligned");
+  return hll_estimate(keys_dev, n, (cudaStream_t)stream, estimate_host);
+}

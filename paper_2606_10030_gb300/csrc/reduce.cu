@@ -343,8 +343,11 @@ __device__ void merge_partials(const Partial* parts, int np, agg_scalar* out, ui
     // the partials' bound, plus the rounding of hi + lo and the oracle's own
     // rounding of the exact sum (each at most 2^-53 of the value), plus a
     // margin for the roundings of the bound's own sums
-    if (ops & (AGG_SUM | AGG_AVG))
+    if (ops & (AGG_SUM | AGG_AVG)) {
       r.err_bound = (acc.eb + fabs(s) * 0x1p-52 + 0x1p-1073) * (1.0 + 0x1p-40);
+      // a column holding an infinity or a NaN has no finite bound
+      if (!isfinite(s) || !isfinite(r.err_bound)) r.err_bound = __longlong_as_double(0x7ff0000000000000ll);
+    }
     r.avg = count ? s / (double)count : nan;
     r.min_f = count ? f64_of_img(acc.mn) : __longlong_as_double(0x7ff0000000000000ll);
     r.max_f = count ? f64_of_img(acc.mx) : __longlong_as_double((long long)0xfff0000000000000ull);

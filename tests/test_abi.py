@@ -157,3 +157,36 @@ def test_rule_strategy_is_a_host_call(L):
     # a sample covering 98 % of the mass of a large column: shared-memory tables
     f[0], f[4], f[5], f[6], f[8] = 28, 2000 / 4096, 80 / 4096, 200 / 4096, 0.01
     assert agg.agg_rule_strategy(f, agg.AGG_SUM) == agg.AGG_STRAT_SMEM
+
+
+def test_multi_rejects_bad_arguments_without_launching(L):
+    k = ctypes.c_void_p(0x1000)
+    cols = (agg.AggColumn * 5)()
+    for c in cols:
+        c.data, c.dtype, c.ops = 0x2000, agg.AGG_I64, agg.AGG_SUM
+    out = ctypes.c_void_p()
+    ok_args = lambda **kw: dict(dict(lo=k, hi=None, n=10, cols=cols, ncols=1, filt=None, out=ctypes.byref(out)), **kw)  # noqa: E731
+
+    def call(**kw):
+        a = ok_args(**kw)
+        return L.agg_groupby_multi(a["lo"], a["hi"], a["n"], a["cols"], a["ncols"], a["filt"], a["out"], None)
+
+    assert call(ncols=0) == agg.AGG_ERR_INVALID
+    assert call(ncols=5) == agg.AGG_ERR_INVALID
+    assert call(n=-1) == agg.AGG_ERR_INVALID
+    assert call(lo=None) == agg.AGG_ERR_INVALID
+    assert call(lo=ctypes.c_void_p(0x1002)) == agg.AGG_ERR_INVALID
+    assert call(out=None) == agg.AGG_ERR_INVALID
+    cols[0].dtype = 9
+    assert call() == agg.AGG_ERR_INVALID and "dtype" in agg.last_error()
+    cols[0].dtype, cols[0].ops = agg.AGG_I64, 0
+    assert call() == agg.AGG_ERR_INVALID and "ops" in agg.last_error()
+    cols[0].ops = agg.AGG_SUM
+    cols[0].data = 0x2004  # not 8-byte aligned for int64
+    assert call() == agg.AGG_ERR_INVALID
+    cols[0].data = 0x2000
+    r = agg.AggRange()
+    r.data, r.dtype = 0x3000, 11
+    assert call(filt=ctypes.byref(r)) == agg.AGG_ERR_INVALID
+    assert L.agg_multi_to_host(None, None, None, 0, None, None, None, None) == agg.AGG_ERR_INVALID
+    L.agg_multi_free(None)
