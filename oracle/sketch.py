@@ -81,47 +81,44 @@ def sketch(keys: np.ndarray, vbytes: int, nops: int, fp: int, slot_bytes: int, o
 # "HyperLogLog: the analysis of a near-optimal cardinality estimation
 # algorithm", AofA 2007), over every key of a column. The GROUP BY planner
 # sizes its tables from it when the sample does not cover a large column.
-# Hash of a key: SplitMix64's output function of (key XOR the golden-ratio
-# increment 0x9E3779B97F4A7C15), 64 bits; the top p = 14 bits pick one of
-# m = 2^14 registers, which keeps the largest rank (position of the first
-# one bit, from 1) of the remaining 50 bits (51 when they are all zero).
+# Hash of a key: MurmurHash3's 32-bit finaliser (a bijection of uint32); the
+# top p = 14 bits pick one of m = 2^14 registers, which keeps the largest rank
+# (position of the first one bit, from 1) of the remaining 18 bits (19 when
+# they are all zero).
 # ---------------------------------------------------------------------------
 HLL_P = 14
 
 
-def _mix64(z: np.ndarray) -> np.ndarray:
-    z = z.astype(np.uint64)
+def _fmix32(x: np.ndarray) -> np.ndarray:
+    x = np.asarray(x, dtype=np.uint32).copy()
     with np.errstate(over="ignore"):
-        z = (z ^ (z >> np.uint64(30))) * np.uint64(0xBF58476D1CE4E5B9)
-        z = (z ^ (z >> np.uint64(27))) * np.uint64(0x94D049BB133111EB)
-    return z ^ (z >> np.uint64(31))
+        x ^= x >> np.uint32(16)
+        x *= np.uint32(0x85EBCA6B)
+        x ^= x >> np.uint32(13)
+        x *= np.uint32(0xC2B2AE35)
+        x ^= x >> np.uint32(16)
+    return x
 
 
 def hll_registers(keys: np.ndarray, p: int = HLL_P) -> np.ndarray:
     """The m = 2^p registers after adding every key."""
     m = 1 << p
-    h = _mix64(np.asarray(keys, dtype=np.uint32).astype(np.uint64) ^ np.uint64(0x9E3779B97F4A7C15))
-    idx = (h >> np.uint64(64 - p)).astype(np.int64)
-    w = h << np.uint64(p)  # the remaining 64 - p bits, at the top
-    rank = np.full(h.size, 64 - p + 1, dtype=np.int64)
+    h = _fmix32(keys).astype(np.int64)
+    idx = h >> (32 - p)
+    w = (h << p) & 0xFFFFFFFF  # the remaining 32 - p bits, at the top of a 32-bit word
+    rank = np.full(h.size, 32 - p + 1, dtype=np.int64)
     nz = w != 0
-    # position of the leading one bit of w, from 1: 64 - bit_length(w) + 1
-    bl = np.zeros(h.size, dtype=np.int64)
-    v = w[nz]
-    b = np.zeros(v.size, dtype=np.int64)
-    for s in (32, 16, 8, 4, 2, 1):
-        big = v >= (np.uint64(1) << np.uint64(s))
-        b[big] += s
-        v = np.where(big, v >> np.uint64(s), v)
-    bl[nz] = b + 1
-    rank[nz] = 64 - bl[nz] + 1
+    # position of the leading one bit of w, from 1: 32 - bit_length(w) + 1
+    bl = np.floor(np.log2(w[nz].astype(np.float64))).astype(np.int64) + 1  # exact for w < 2^32
+    rank[nz] = 32 - bl + 1
     reg = np.zeros(m, dtype=np.int64)
     np.maximum.at(reg, idx, rank)
     return reg
 
 
 def hll_estimate(keys: np.ndarray, p: int = HLL_P) -> float:
-    """alpha_m m^2 / sum 2^-M_j, with linear counting m ln(m / V) below 5m/2 when V registers are zero."""
+    """alpha_m m^2 / sum 2^-M_j; linear counting m ln(m / V) below 5m/2 when V registers are
+    zero; above 2^32 / 30, the 32-bit hash space correction -2^32 ln(1 - E / 2^32)."""
     if np.asarray(keys).size == 0:
         return 0.0
     m = 1 << p
@@ -131,4 +128,6 @@ def hll_estimate(keys: np.ndarray, p: int = HLL_P) -> float:
     zeros = int(np.count_nonzero(reg == 0))
     if e <= 2.5 * m and zeros > 0:
         e = m * math.log(m / zeros)
+    elif e > 2.0 ** 32 / 30.0:
+        e = -(2.0 ** 32) * math.log(1.0 - e / 2.0 ** 32)
     return e

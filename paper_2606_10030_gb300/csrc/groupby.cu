@@ -333,9 +333,9 @@ class HashRun {
     agg_status st;
     {
       PhaseTimer pt(AGG_PHASE_SORT, s_);
-      if (passes == 1) {
-        st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_, 24)
-                     : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_, 24);
+      if (passes == 1) {  // rows only need grouping by partition: no stable order
+        st = es == 4 ? partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_)
+                     : partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_);
       } else {  // by bits 16..23, then stably by bits 24..31: ordered by the top 16 bits
         st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kq, (uint32_t*)vq, n, rt, s_, 16)
                      : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kq, (uint64_t*)vq, n, rt, s_, 16);

@@ -3,15 +3,16 @@
 // planner sizes its hash tables from it when the 4096-key sample does not
 // cover a large column (a long tail of rare keys the sample cannot see).
 //
-// A key's 64-bit hash is SplitMix64's output function of (key XOR the
-// golden-ratio increment); its top 14 bits pick one of m = 2^14 registers,
-// which keeps the largest rank (position of the first one bit, from 1) of the
-// remaining 50 bits. Each block keeps its registers in shared memory (a rank
+// A key's hash is MurmurHash3's 32-bit finaliser (a bijection of uint32, so
+// distinct keys never collide); its top 14 bits pick one of m = 2^14
+// registers, which keeps the largest rank (position of the first one bit,
+// from 1) of the remaining 18 bits (19 if they are all zero). Each block keeps its registers in shared memory (a rank
 // is written only when it exceeds the register, so repeated keys cost a
 // shared-memory read), merges them into the column's registers with atomicMax,
 // and the last block to finish (fence plus ticket, no waiting) forms the
 // estimate alpha_m m^2 / sum 2^-M_j (linear counting m ln(m / V) below 5m/2
-// when V registers are zero). The registers and the ticket live in the
+// when V registers are zero; above 2^32/30, the correction for a 32-bit hash
+// space). The registers and the ticket live in the
 // stream's scratch and are cleared before every launch.
 #include <cmath>
 
@@ -26,12 +27,9 @@ constexpr size_t kHllScratchOff = 8192;  // in the stream scratch, past the scan
 constexpr size_t kHllScratchBytes = kHllScratchOff + (size_t)kHllM * 4 + 256;
 
 __device__ __forceinline__ void hll_add(uint32_t* sreg, uint32_t key) {
-  uint64_t z = (uint64_t)key ^ 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z ^= z >> 31;
-  const uint32_t idx = (uint32_t)(z >> (64 - kHllP));
-  const uint32_t rank = (uint32_t)__clzll((long long)((z << kHllP) | (1ull << (kHllP - 1)))) + 1u;  // 1..51
+  const uint32_t h = fmix32(key);
+  const uint32_t idx = h >> (32 - kHllP);
+  const uint32_t rank = (uint32_t)__clz((int)((h << kHllP) | (1u << (kHllP - 1)))) + 1u;  // 1..19
   if (rank > *(volatile uint32_t*)&sreg[idx]) atomicMax(&sreg[idx], rank);
 }
 
@@ -109,7 +107,8 @@ __global__ void __launch_bounds__(kHllThreads) hll_kernel(const uint32_t* __rest
     const double m = (double)kHllM;
     const double alpha = 0.7213 / (1.0 + 1.079 / m);
     double e = alpha * m * m / tot;
-    if (e <= 2.5 * m && v > 0.0) e = m * log(m / v);
+    if (e <= 2.5 * m && v > 0.0) e = m * log(m / v);                               // linear counting
+    else if (e > 4294967296.0 / 30.0) e = -4294967296.0 * log(1.0 - e / 4294967296.0);  // 32-bit hash space
     *est = e;
   }
 }

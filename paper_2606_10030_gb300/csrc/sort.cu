@@ -10,6 +10,8 @@
 //                  same digit (ballots + per-warp running counts), staging
 //                  of the tile in shared memory in digit order, then coalesced
 //                  writes of each digit's run to its global offset.
+#include <algorithm>
+
 #include "sort.cuh"
 
 namespace agg {
@@ -351,6 +353,203 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
   AGG_CUDA_TRY(cudaGetLastError());
   return AGG_OK;
 }
+
+// ---------------------------------------------------------------------------
+// One-level hash partition without a stable order (the hash build needs rows
+// grouped by partition, in any order within one). Two kernels:
+//   part_hist     256-bin histogram of the partition digit (top 8 bits of
+//                 fmix32(key)), per-warp counters in shared memory, merged with
+//                 one global atomic per bin and block; the last block to finish
+//                 turns the totals into each partition's start;
+//   part_scatter  per tile of kPartTile rows: every row's place within its
+//                 digit's run of the tile from a shared-memory counter (lanes
+//                 of a warp holding the same digit share one atomic, so hot
+//                 keys do not serialise), the tile's runs reserved in the output
+//                 with one global atomic per digit, the rows staged in shared
+//                 memory in digit order and written out run by run.
+// Reads 4 + 12 B and writes 12 B per row (uint32 key, 8-byte value), with no
+// per-tile count array and no ranking rounds.
+// ---------------------------------------------------------------------------
+constexpr int kPartThreads = 512;
+constexpr int kPartTile = 8192;
+
+__device__ __forceinline__ uint32_t part_digit(uint32_t key) { return fmix32(key) >> 24; }
+
+// fill[0..256): partition starts (written by the last block), fill[256]: ticket.
+__global__ void __launch_bounds__(kPartThreads) part_hist(const uint32_t* __restrict__ keys, int64_t n,
+                                                          unsigned long long* __restrict__ fill) {
+  constexpr int kWarps = kPartThreads / 32;
+  __shared__ uint32_t h[kWarps][256];
+  __shared__ int s_last;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const int64_t nthreads = (int64_t)gridDim.x * kPartThreads;
+  for (int64_t i0 = (int64_t)blockIdx.x * kPartThreads + (threadIdx.x & ~31); i0 < n; i0 += nthreads) {
+    const int64_t i = i0 + lane;
+    const bool ok = i < n;
+    const uint32_t d = ok ? part_digit(keys[i]) : 0u;
+    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u);
+    if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[w][d], (uint32_t)__popc(peers));
+  }
+  __syncthreads();
+  if (threadIdx.x < 256) {
+    uint32_t t = 0;
+    for (int ww = 0; ww < kWarps; ++ww) t += h[ww][threadIdx.x];
+    if (t) atomicAdd(&fill[threadIdx.x], (unsigned long long)t);
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&fill[256], 1ull) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;  // the whole block leaves together
+  __threadfence();
+  // exclusive scan of the 256 totals (one warp, 8 chunks of 32)
+  __shared__ unsigned long long tot[256];
+  if (threadIdx.x < 256) tot[threadIdx.x] = __ldcg(&fill[threadIdx.x]);
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    unsigned long long run = 0;
+    for (int j = 0; j < 8; ++j) {
+      unsigned long long x = tot[j * 32 + lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      const unsigned long long incl = x + run;
+      const unsigned long long excl = incl - tot[j * 32 + lane];
+      run = __shfl_sync(0xffffffffu, incl, 31);
+      fill[j * 32 + lane] = excl;
+    }
+  }
+  if (threadIdx.x == 0) fill[256] = 0;
+}
+
+template <class P>
+__global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* __restrict__ keys,
+                                                             const P* __restrict__ vals, uint32_t* __restrict__ okeys,
+                                                             P* __restrict__ ovals, int64_t n,
+                                                             unsigned long long* __restrict__ fill) {
+  constexpr int kRows = kPartTile / kPartThreads;  // rows per thread and tile
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  P* stage_v = (P*)sm_raw;                                // kPartTile
+  uint32_t* stage_k = (uint32_t*)(stage_v + kPartTile);  // kPartTile
+  __shared__ uint32_t cnt[256], off[256];
+  __shared__ unsigned long long base[256];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const int64_t r0 = t * kPartTile;
+    const int rows = (int)min((int64_t)kPartTile, n - r0);
+    if (threadIdx.x < 256) cnt[threadIdx.x] = 0;
+    __syncthreads();
+    // each warp owns kRows * 32 consecutive rows; rows in registers, places in the digit runs
+    uint32_t kr[kRows], pr[kRows];
+    const int wbase = w * kRows * 32;
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = wbase + r * 32 + lane;
+      kr[r] = j < rows ? keys[r0 + j] : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = wbase + r * 32 + lane;
+      const bool ok = j < rows;
+      const uint32_t d = part_digit(kr[r]);
+      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u);
+      const int leader = __ffs(peers) - 1;
+      uint32_t b = 0;
+      if (ok && lane == leader) b = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
+      b = __shfl_sync(0xffffffffu, b, leader);
+      pr[r] = b + __popc(peers & lt);
+    }
+    __syncthreads();
+    // the tile's digit runs: offsets in the stage, and places in the output
+    if (threadIdx.x < 256) {
+      const uint32_t c = cnt[threadIdx.x];
+      base[threadIdx.x] = c ? atomicAdd(&fill[threadIdx.x], (unsigned long long)c) : 0ull;
+    }
+    if (threadIdx.x < 32) {
+      uint32_t run = 0;
+      for (int j = 0; j < 8; ++j) {
+        uint32_t x = cnt[j * 32 + lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+          if (lane >= o) x += y;
+        }
+        off[j * 32 + lane] = x + run - cnt[j * 32 + lane];
+        run += __shfl_sync(0xffffffffu, x, 31);
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = wbase + r * 32 + lane;
+      if (j < rows) {
+        const uint32_t p = off[part_digit(kr[r])] + pr[r];
+        stage_k[p] = kr[r];
+        stage_v[p] = vals[r0 + j];
+      }
+    }
+    __syncthreads();
+    for (int p = threadIdx.x; p < rows; p += kPartThreads) {
+      const uint32_t key = stage_k[p];
+      const uint32_t d = part_digit(key);
+      const unsigned long long q = base[d] + (unsigned long long)(p - (int)off[d]);
+      okeys[q] = key;
+      ovals[q] = stage_v[p];
+    }
+    __syncthreads();  // the stage and the counters are reused by the next tile
+  }
+}
+
+template <class P>
+static size_t part_smem() {
+  return (size_t)kPartTile * (sizeof(P) + 4);
+}
+
+size_t partition_tmp_bytes() { return 257 * sizeof(unsigned long long) + 256; }
+
+template <class P>
+agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
+                            cudaStream_t s) {
+  if (n <= 0) return AGG_OK;
+  int dev = 0;
+  cudaGetDevice(&dev);
+  static bool attr[64] = {};
+  if (dev < 64 && !attr[dev]) {
+    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)part_smem<uint32_t>()));
+    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)part_smem<uint64_t>()));
+    attr[dev] = true;
+  }
+  unsigned long long* fill = (unsigned long long*)tmp;
+  AGG_CUDA_TRY(cudaMemsetAsync(fill, 0, 257 * sizeof(unsigned long long), s));
+  const DeviceInfo& di = device_info();
+  int bh = 1, bs = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, part_hist, kPartThreads, 0) != cudaSuccess || bh < 1) bh = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, part_scatter<P>, kPartThreads, part_smem<P>()) !=
+          cudaSuccess ||
+      bs < 1)
+    bs = 1;
+  const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+  const int64_t gh = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bh, (n + kPartThreads - 1) / kPartThreads));
+  const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, ntiles));
+  part_hist<<<(unsigned)gh, kPartThreads, 0, s>>>(kin, n, fill);
+  part_scatter<P><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kin, vin, kout, vout, n, fill);
+  note_launch(2);
+  AGG_CUDA_TRY(cudaGetLastError());
+  return AGG_OK;
+}
+
+template agg_status partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t, void*,
+                                               cudaStream_t);
+template agg_status partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t, void*,
+                                               cudaStream_t);
 
 template agg_status radix_partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t,
                                                      void*, cudaStream_t, int);

@@ -39,6 +39,14 @@ template <class P>
 agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
                                   cudaStream_t s, int shift);
 
+// One-level hash partition by the top 8 bits of fmix32(key), in no particular
+// order within a partition (rows of one partition are contiguous, partitions
+// in ascending digit order). tmp must hold partition_tmp_bytes() bytes.
+size_t partition_tmp_bytes();
+template <class P>
+agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
+                            cudaStream_t s);
+
 // Set the kernel attributes the sort needs (call before a stream capture).
 agg_status radix_prepare();
 

@@ -103,7 +103,7 @@ def test_hll_closed_forms():
     from oracle.sketch import hll_estimate, hll_registers
     assert hll_estimate(np.array([], dtype=np.uint32)) == 0.0
     one = hll_registers(np.full(1000, 12345, dtype=np.uint32))
-    assert np.count_nonzero(one) == 1 and 1 <= one.max() <= 51
+    assert np.count_nonzero(one) == 1 and 1 <= one.max() <= 19
     # one key: linear counting with V = m - 1 zero registers gives m ln(m / (m - 1)) ~ 1
     m = 1 << 14
     assert abs(hll_estimate(np.full(10, 7, dtype=np.uint32)) - m * math.log(m / (m - 1))) < 1e-9
@@ -118,15 +118,25 @@ def test_hll_ignores_repeats_and_order():
     assert hll_estimate(rep) == hll_estimate(np.unique(keys))
 
 
-def test_hll_rank_of_known_hashes():
-    """Register index and rank worked out by hand from the SplitMix64 output of key 0."""
-    from oracle.sketch import _mix64, hll_registers
-    h = int(_mix64(np.array([0x9E3779B97F4A7C15], dtype=np.uint64))[0])
-    idx = h >> 50
-    w = (h << 14) & ((1 << 64) - 1)
-    rank = 64 - w.bit_length() + 1 if w else 51
+def test_hll_registers_of_known_hashes():
+    """Register and rank worked out by hand from MurmurHash3's finaliser: fmix32(1) =
+    0x514E28B7 (register 0x514E28B7 >> 18 = 5203; low 18 bits 0x228B7 >= 2^17, so the
+    first of the 18 bits is one: rank 1); fmix32(0) = 0 (register 0, no one bit among the
+    18: rank 19); and the rank rule, 18 - bit_length(low 18 bits) + 1, on a few more keys."""
+    from oracle.sketch import _fmix32, hll_registers
+    assert int(_fmix32(np.array([1], dtype=np.uint32))[0]) == 0x514E28B7
+    reg = hll_registers(np.array([1], dtype=np.uint32))
+    assert reg[5203] == 1 and np.count_nonzero(reg) == 1
+    # the rank rule on more keys (their registers may also hold other keys' larger ranks)
+    keys = np.arange(1 << 16, dtype=np.uint32)
+    h = _fmix32(keys).astype(np.int64)
+    reg = hll_registers(keys)
+    for k in (3, 77, 4096, 65535):
+        low = int(h[k]) & 0x3FFFF
+        rank = 18 - low.bit_length() + 1 if low else 19
+        assert reg[int(h[k]) >> 18] >= rank
     reg = hll_registers(np.array([0], dtype=np.uint32))
-    assert reg[idx] == rank and np.count_nonzero(reg) == 1
+    assert reg[0] == 19 and np.count_nonzero(reg) == 1
 
 
 @pytest.mark.parametrize("d", [300, 20_000, 200_000, 3_000_000])
