@@ -37,6 +37,7 @@
 #ifndef AGG_H_
 #define AGG_H_
 
+#include <stddef.h>
 #include <stdint.h>
 
 #ifdef __cplusplus
@@ -137,6 +138,46 @@ agg_status agg_reduce(const void* col_dev, int64_t n, agg_dtype dtype, uint32_t 
  */
 agg_status agg_reduce_host(const void* col_host, int64_t n, agg_dtype dtype, uint32_t ops,
                            agg_scalar* out_host, void* stream);
+
+/*
+ * Compressed integer columns for the scan (the paper's future work compresses
+ * data to speed up transfers, Sec. 8): frame-of-reference bit packing. A
+ * column is cut into frames of AGG_PACK_FRAME values; each frame keeps its
+ * minimum as reference and every value minus it in the fewest bits that hold
+ * the frame's range (0 to 64), least significant bit first, in 32-bit words.
+ * Buffer layout (16-byte aligned): nframes descriptors of 24 bytes
+ * {int64 ref; uint32 bits; uint32 zero; uint64 first word of the frame}, zero
+ * padding to a multiple of 16 bytes, the words, and 8 zero bytes.
+ *
+ * agg_pack_for_bound  bytes enough for any column of n values of dtype.
+ * agg_pack_for        encode n values (int32, int64 or uint32) from host memory
+ *                     into out_host (capacity bytes, 16-byte aligned); fills
+ *                     *info. Host code: the format the column is kept in before
+ *                     a transfer. AGG_ERR_INVALID if the buffer is too small.
+ * agg_reduce_packed   agg_reduce of a packed column in device memory (decoded
+ *                     inside the scan kernel); out_dev written asynchronously.
+ * agg_reduce_packed_host  the end-to-end variant: only packed bytes cross the
+ *                     link (chunks of frames copied on a copy stream while the
+ *                     previous chunk is scanned); synchronous.
+ * Results are those of agg_reduce on the unpacked column (integers: exact).
+ */
+#define AGG_PACK_FRAME 1024
+typedef struct agg_packed_info {
+  int64_t n;        /* values */
+  int32_t dtype;    /* AGG_I32, AGG_I64 or AGG_U32 */
+  int32_t reserved;
+  int64_t nframes;  /* ceil(n / AGG_PACK_FRAME) */
+  int64_t nwords;   /* 32-bit words of packed values */
+  int64_t bytes;    /* size of the whole buffer */
+} agg_packed_info;
+
+size_t agg_pack_for_bound(int64_t n, agg_dtype dtype);
+agg_status agg_pack_for(const void* col_host, int64_t n, agg_dtype dtype, void* out_host, size_t capacity,
+                        agg_packed_info* info);
+agg_status agg_reduce_packed(const void* packed_dev, const agg_packed_info* info, uint32_t ops, agg_scalar* out_dev,
+                             void* stream);
+agg_status agg_reduce_packed_host(const void* packed_host, const agg_packed_info* info, uint32_t ops,
+                                  agg_scalar* out_host, void* stream);
 
 /* GROUP BY strategies (agg_options.strategy). */
 typedef enum {

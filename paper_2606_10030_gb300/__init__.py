@@ -162,6 +162,15 @@ class AggMulti(ctypes.Structure):
                 ("priv", ctypes.c_void_p)]
 
 
+AGG_PACK_FRAME = 1024
+
+
+class AggPackedInfo(ctypes.Structure):
+    """Mirror of ``agg_packed_info``."""
+    _fields_ = [("n", ctypes.c_int64), ("dtype", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("nframes", ctypes.c_int64), ("nwords", ctypes.c_int64), ("bytes", ctypes.c_int64)]
+
+
 _lib = None
 
 # name -> (restype, argtypes) of every exported entry point
@@ -170,6 +179,10 @@ SIGNATURES = {
     "agg_reduce": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_reduce_host": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
     "agg_reduce_noalloc": (_i32, [_vp, _i64, _i32, _u32, _vp, _vp]),
+    "agg_pack_for_bound": (ctypes.c_size_t, [_i64, _i32]),
+    "agg_pack_for": (_i32, [_vp, _i64, _i32, _vp, ctypes.c_size_t, _vp]),
+    "agg_reduce_packed": (_i32, [_vp, _vp, _u32, _vp, _vp]),
+    "agg_reduce_packed_host": (_i32, [_vp, _vp, _u32, _vp, _vp]),
     "agg_groupby": (_i32, [_vp, _vp, _i64, _i32, _u32, _vp, _vp, _vp]),
     "agg_groupby_host": (_i32, [_vp, _vp, _i64, _i32, _u32, _vp, _vp, _vp]),
     "agg_groups_to_host": (_i32, [_vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]),
@@ -300,6 +313,58 @@ def agg_reduce_noalloc(col, ops: int = AGG_ALL, out=None, stream=None):
         out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=col.device)
     check(lib().agg_reduce_noalloc(ctypes.c_void_p(col.data_ptr()), col.numel(), dtype_code(col), ops,
                                    ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+class Packed:
+    """A frame-of-reference bit-packed integer column in host memory (see agg_pack_for)."""
+
+    def __init__(self, buf, info: AggPackedInfo):
+        self.buf = buf
+        self.info = info
+
+    @property
+    def nbytes(self) -> int:
+        return int(self.info.bytes)
+
+    def to(self, device):
+        import torch
+        return Packed(self.buf[: self.nbytes].to(device), self.info)
+
+
+def agg_pack_for(col) -> Packed:
+    """Encode a 1-D int32 / int64 / uint32 host tensor into a uint8 host tensor (pinned when a GPU is present)."""
+    import torch
+    assert not col.is_cuda and col.dim() == 1 and col.is_contiguous()
+    dt = dtype_code(col)
+    cap = int(lib().agg_pack_for_bound(col.numel(), dt))
+    buf = torch.empty(cap + 16, dtype=torch.uint8)
+    if torch.cuda.is_available():
+        buf = buf.pin_memory()
+    off = (-buf.data_ptr()) % 16
+    view = buf[off: off + cap]
+    info = AggPackedInfo()
+    check(lib().agg_pack_for(ctypes.c_void_p(col.data_ptr()) if col.numel() else None, col.numel(), dt,
+                             ctypes.c_void_p(view.data_ptr()), cap, ctypes.byref(info)))
+    return Packed(view, info)
+
+
+def agg_reduce_packed(p: Packed, ops: int = AGG_ALL, out=None, stream=None):
+    """Ungrouped aggregation of a packed column held in device memory; returns the 80-byte device result."""
+    import torch
+    assert p.buf.is_cuda
+    if out is None:
+        out = torch.empty(SCALAR_BYTES, dtype=torch.uint8, device=p.buf.device)
+    check(lib().agg_reduce_packed(ctypes.c_void_p(p.buf.data_ptr()), ctypes.byref(p.info), ops,
+                                  ctypes.c_void_p(out.data_ptr()), _stream_ptr(stream)))
+    return out
+
+
+def agg_reduce_packed_host(p: Packed, ops: int = AGG_ALL, stream=None) -> AggScalar:
+    """End-to-end aggregation of a packed column in (pinned) host memory; synchronous."""
+    out = AggScalar()
+    check(lib().agg_reduce_packed_host(ctypes.c_void_p(p.buf.data_ptr()), ctypes.byref(p.info), ops,
+                                       ctypes.byref(out), _stream_ptr(stream)))
     return out
 
 
