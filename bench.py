@@ -536,15 +536,21 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
     plan_s = time.perf_counter() - t0
     plan.run()  # capture + first replay
     torch.cuda.synchronize()
-    agg.profile_read()
-    agg.profile_enable(True)
-    t0 = time.perf_counter()
-    for _ in range(steps):
-        plan.run()
-    torch.cuda.synchronize()
-    batch_s = (time.perf_counter() - t0) / steps
-    agg.profile_enable(False)
-    batch_gpu_ms = sum(v[0] for v in agg.profile_read().values()) / steps
+
+    def time_runs():
+        agg.profile_read()
+        agg.profile_enable(True)
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            plan.run()
+        torch.cuda.synchronize()
+        wall = (time.perf_counter() - t0) / steps
+        agg.profile_enable(False)
+        return wall, sum(v[0] for v in agg.profile_read().values()) / steps
+
+    fixed_s, fixed_gpu_ms = time_runs()  # the default 64 Ki-row work items
+    tile = plan.tune(2)  # the autotuner's tile axis: 16, 32 or 64 Ki rows
+    batch_s, batch_gpu_ms = time_runs()
     plan.free()
     o = agg.options(strat)
     for k, v, ops in cols[:8]:
@@ -565,10 +571,12 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
                         "[1, 2^20] (uniform or Zipf 0.5-1.5), mixed int32/int64/float32/float64 values and ops",
             "rows": rows, "input_bytes": in_bytes, "selector": "learned" if learned else "rule (no weights file)",
             "batched_ms": round(batch_s * 1e3, 3), "batched_GB/s": round(in_bytes / batch_s / 1e9, 1),
+            "tile_rows_tuned": tile, "batched_ms_fixed_64Ki_tile": round(fixed_s * 1e3, 3),
             "batched_plan_ms": round(plan_s * 1e3, 1),
             "plain_ms": round(plain_s * 1e3, 3), "plain_GB/s": round(in_bytes / plain_s / 1e9, 1),
             "speedup": round(plain_s / batch_s, 2),
-            "gpu_ms": {"batched": round(batch_gpu_ms, 3), "plain": round(plain_gpu_ms, 3),
+            "gpu_ms": {"batched": round(batch_gpu_ms, 3), "batched_fixed_64Ki_tile": round(fixed_gpu_ms, 3),
+                       "plain": round(plain_gpu_ms, 3),
                        "how": "sum of the library's per-phase CUDA-event times (kernels only)"},
             "steps": steps}
 
@@ -663,6 +671,89 @@ def extra_table_grid(link: dict) -> dict:
     ev["workload"] = ("GROUP BY SUM/MIN/MAX/COUNT/AVG over 2^30-row tables, uint32 keys over D = 2^4, 2^6, ..., "
                       "2^26 random keys, uniform or Zipf s in {0.5, 1.0, 1.5}, int64 values; one table per (D, s)")
     return ev
+
+
+def extra_compressed(link: dict, steps: int = 10) -> dict:
+    """The paper's scan shape (int32 uniform in [-2^20, 2^20): 21 of 32 bits) packed by frame of
+    reference: end to end from pinned host memory, plain and packed, and the on-device packed scan."""
+    import torch
+
+    import paper_2606_10030_gb300 as agg
+    from datagen import cuda as dgc
+    n = 1 << 28
+    col = dgc.values("i32", n, 0)
+    host = col.cpu()
+    raw = n * 4
+    t0 = time.perf_counter()
+    p = agg.agg_pack_for(host)
+    enc_s = time.perf_counter() - t0
+    hp = host.pin_memory()
+    del col
+    torch.cuda.empty_cache()
+
+    def timed(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return (time.perf_counter() - a) / reps
+
+    plain_s = timed(lambda: agg.agg_reduce_host(hp, agg.AGG_ALL), steps)
+    packed_s = timed(lambda: agg.agg_reduce_packed_host(p, agg.AGG_ALL), steps)
+    dev = p.to("cuda")
+    out = torch.empty(agg.SCALAR_BYTES, dtype=torch.uint8, device="cuda")
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        agg.agg_reduce_packed(dev, agg.AGG_ALL, out=out)
+    a.record()
+    for _ in range(50):
+        agg.agg_reduce_packed(dev, agg.AGG_ALL, out=out)
+    b.record()
+    torch.cuda.synchronize()
+    dev_ms = a.elapsed_time(b) / 50
+    del dev, hp
+    torch.cuda.empty_cache()
+    e2e_packed = raw / packed_s / 1e9
+    return {"workload": "ungrouped SUM/MIN/MAX/COUNT/AVG, 2^28 int32 rows uniform in [-2^20, 2^20), frame-of-reference "
+                        "bit-packed (1024-value frames)",
+            "raw_bytes": raw, "packed_bytes": p.nbytes, "ratio": round(raw / p.nbytes, 3),
+            "encode_s_host": round(enc_s, 2),
+            "e2e_plain_GB/s": round(raw / plain_s / 1e9, 1), "e2e_packed_input_GB/s": round(e2e_packed, 1),
+            "e2e_packed_frac_of_link": round(e2e_packed / link["GB/s"], 3), "link_peak_GB/s": link["GB/s"],
+            "device_packed_ms": round(dev_ms, 4), "device_packed_input_GB/s": round(raw / (dev_ms * 1e-3) / 1e9, 1),
+            "device_packed_bytes_GB/s": round(p.nbytes / (dev_ms * 1e-3) / 1e9, 1), "steps": steps}
+
+
+def extra_multi(steps: int = 10) -> dict:
+    """Fused filter -> multi-column GROUP BY: 2^26 rows, key (hi over 16, lo over 4096 random keys),
+    int64 / float32 / float64 value columns, a range filter on an int32 column keeping half."""
+    import torch
+
+    import paper_2606_10030_gb300 as agg
+    from datagen import cuda as dgc
+    n = 1 << 26
+    lo, hi = dgc.keys_uniform(n, 4096, 3), dgc.keys_uniform(n, 16, 4)
+    a, b, c, f = dgc.values("i64", n, 5), dgc.values("f32", n, 6), dgc.values("f64", n, 7), dgc.values("i32", n, 8)
+    cols = [(a, agg.AGG_ALL), (b, agg.AGG_ALL), (c, agg.AGG_SUM)]
+    filt = (f, -(2 ** 19), 2 ** 19)
+    m = agg.agg_groupby_multi(lo, hi, cols, filt)
+    groups = m.num_groups
+    m.free()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        agg.agg_groupby_multi(lo, hi, cols, filt).free()
+    torch.cuda.synchronize()
+    ms = (time.perf_counter() - t0) * 1e3 / steps
+    in_bytes = n * (4 + 4 + 8 + 4 + 8 + 4)
+    del lo, hi, a, b, c, f
+    torch.cuda.empty_cache()
+    return {"workload": "GROUP BY (hi, lo) over 2^26 rows, 3 value columns (int64 all ops, float32 all ops, float64 "
+                        "SUM), filter -2^19 <= int32 <= 2^19 (about half the rows)",
+            "groups": groups, "ms": round(ms, 3), "input_bytes": in_bytes, "GB/s": round(in_bytes / (ms * 1e-3) / 1e9, 1),
+            "steps": steps}
 
 
 def kernel_traffic(kernel: str, workload: str):
@@ -766,6 +857,8 @@ def run_ours(args):
         extra["scan"] = extra_scan(200, peaks)
         extra["zipf"] = extra_zipf(5)
         extra["batched"] = extra_batched(5)
+        extra["compressed"] = extra_compressed(link)
+        extra["multi"] = extra_multi()
         extra["table2p30_grid"] = extra_table_grid(link)
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -197,13 +197,14 @@ typedef struct agg_options {
   int32_t smem_slots;      /* shared-memory table slots (power of two, <= 8192); 0 = from the sketch */
   int64_t table_slots;     /* global table slots (power of two); 0 = from the sketch */
   uint64_t sample_offset;  /* offset of the strided key sample (pass a seeded draw) */
-  int32_t items_per_thread;/* reserved for a rows-per-thread knob; must be 0 */
+  int32_t items_per_thread;/* rows a thread folds per iteration of the build's vector loop: 4 or 8; 0 = 4 */
   int32_t partition;       /* hash-partition the rows before a hash build: 0 = automatic (when the
                               shared tables would spill or the global table exceeds half of L2; two
                               levels above ~600k distinct keys), 1 = one level (256 partitions),
                               2 = two levels (65536 partitions), -1 = never */
   int32_t flags;           /* AGG_FLAG_* bits; 0 = none */
-  int32_t reserved;        /* must be 0 */
+  int32_t tile_rows;       /* rows per tile of the hash-partitioned build (power of two in [4096, 65536]);
+                              0 = from the column */
 } agg_options;
 
 /*
@@ -429,7 +430,8 @@ agg_status agg_distinct_estimate(const uint32_t* keys_dev, int64_t n, double* es
  * host synchronisation. In a batch every query runs a hash strategy: a query
  * for which SORT is chosen runs on shared-memory tables (identical results).
  * agg_batch_run performs the device work (tables cleared, one persistent
- * build kernel over (query, 64 Ki-row tile) work items pulled from a device
+ * build kernel over (query, tile) work items, 64 Ki rows unless agg_batch_tune
+ * chose another size, pulled from a device
  * counter, batched finalisation into ascending key order) as a CUDA graph
  * captured on the first run and replayed afterwards, then reads back the group
  * counts; synchronous. A table that overflows is regrown (new graph) and the
@@ -458,16 +460,25 @@ agg_status agg_batch_result(const agg_batch_plan* plan, int i, agg_groups** out)
 int agg_batch_size(const agg_batch_plan* plan);
 void agg_batch_plan_free(agg_batch_plan* plan);
 agg_status agg_batch(const agg_query* queries, int nq, agg_groups** outs, void* stream);
+/* The autotuner's tile axis for a batch: time `reps` runs of the plan at each
+   work-item size of 16, 32 and 64 Ki rows (each captured as its own graph),
+   keep the fastest and write it to *tile_rows_out (may be NULL). Results of
+   the runs are those of agg_batch_run. Synchronous. */
+agg_status agg_batch_tune(agg_batch_plan* plan, int reps, int32_t* tile_rows_out, void* stream);
 
 /*
  * Autotuner (the paper's related work tunes the configuration
- * parameters of GPU hash group-by, Sec. 7). Candidates: SMEM with the
- * sketch-sized and the largest shared table at 256 and 512 threads, GLOBAL at
- * 256 and 512 threads, and SORT. Each is run on the actual query and timed
- * with CUDA events; the fastest is cached by query signature (value dtype,
- * ops, round(log2 n), rounded log2 of the distinct estimate, top-8 share
- * decile, sortedness half). AGG_STRAT_AUTOTUNE uses the cache and tunes on a
- * miss.
+ * parameters of GPU hash group-by, Sec. 7). Its axes: strategy, threads per
+ * block, shared table size, rows a thread folds per iteration (4 or 8) and the
+ * tile of a hash-partitioned build (16 Ki rows or the column-sized default).
+ * Candidates: SMEM (sketch-sized table at 512 threads with 4 rows, with 8 rows,
+ * with 16 Ki-row tiles, at 256 threads, and the largest table), GLOBAL at 256
+ * threads (4 rows) and 512 (8 rows), and SORT. Each is run on the actual query
+ * and timed with CUDA events; the fastest is cached by query signature (value
+ * dtype, ops, round(log2 n), rounded log2 of the distinct estimate, top-8
+ * share decile, sortedness half). AGG_STRAT_AUTOTUNE uses the cache and tunes
+ * on a miss; a batch's AGG_STRAT_AUTOTUNE queries take their strategy from the
+ * cache (the rule on a miss).
  */
 #define AGG_TUNE_MAX 8
 typedef struct agg_tune_result {
@@ -476,6 +487,8 @@ typedef struct agg_tune_result {
   int32_t strategy[AGG_TUNE_MAX];   /* AGG_STRAT_SMEM / GLOBAL / SORT */
   int32_t threads[AGG_TUNE_MAX];
   int32_t smem_slots[AGG_TUNE_MAX];
+  int32_t items_per_thread[AGG_TUNE_MAX];
+  int32_t tile_rows[AGG_TUNE_MAX];  /* 0: the column-sized default */
   float ms[AGG_TUNE_MAX];           /* device time of the whole agg_groupby call */
   float best_ms_per_strategy[3];    /* fastest SMEM, GLOBAL, SORT candidate */
   float features[16];               /* sketch of the query */

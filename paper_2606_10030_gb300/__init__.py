@@ -82,7 +82,7 @@ class AggOptions(ctypes.Structure):
         ("items_per_thread", ctypes.c_int32),
         ("partition", ctypes.c_int32),
         ("flags", ctypes.c_int32),
-        ("reserved", ctypes.c_int32),
+        ("tile_rows", ctypes.c_int32),
     ]
 
 
@@ -97,6 +97,8 @@ class AggTuneResult(ctypes.Structure):
         ("strategy", ctypes.c_int32 * AGG_TUNE_MAX),
         ("threads", ctypes.c_int32 * AGG_TUNE_MAX),
         ("smem_slots", ctypes.c_int32 * AGG_TUNE_MAX),
+        ("items_per_thread", ctypes.c_int32 * AGG_TUNE_MAX),
+        ("tile_rows", ctypes.c_int32 * AGG_TUNE_MAX),
         ("ms", ctypes.c_float * AGG_TUNE_MAX),
         ("best_ms_per_strategy", ctypes.c_float * 3),
         ("features", ctypes.c_float * 16),
@@ -214,6 +216,7 @@ SIGNATURES = {
     "agg_batch_size": (_i32, [_vp]),
     "agg_batch_plan_free": (None, [_vp]),
     "agg_batch": (_i32, [_vp, _i32, _vp, _vp]),
+    "agg_batch_tune": (_i32, [_vp, _i32, _vp, _vp]),
     "agg_launch_count": (ctypes.c_int64, []),
     "agg_stream_release": (_i32, [_vp]),
     "agg_debug_fail_alloc": (None, [_i64]),
@@ -655,6 +658,12 @@ class BatchPlan:
 
     def run(self, stream=None):
         check(lib().agg_batch_run(self._h, _stream_ptr(stream)))
+
+    def tune(self, reps: int = 2, stream=None) -> int:
+        """Pick the fastest work-item size (16, 32 or 64 Ki rows) by timing runs; returns it."""
+        t = ctypes.c_int32(0)
+        check(lib().agg_batch_tune(self._h, reps, ctypes.byref(t), _stream_ptr(stream)))
+        return int(t.value)
 
     def result(self, i) -> Groups:
         out = ctypes.c_void_p()

@@ -17,6 +17,8 @@ struct TuneChoice {
   int strategy;
   int threads;
   int smem_slots;
+  int items;  // rows a thread folds per iteration (4 or 8)
+  int tile;   // rows per tile of a hash-partitioned build (0: from the column)
 };
 
 namespace {
@@ -52,14 +54,19 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
   std::memcpy(r->features, feat, sizeof(float) * F_COUNT);
   const bool mm = ops_minmax(ops);
   const int sized = smem_slots_sized(feat, mm), maxs = mm ? 2048 : 4096;
+  // axes: strategy; block size; shared table size; rows a thread folds per
+  // iteration (4 or 8); tile of the hash-partitioned build (16 Ki rows or the
+  // column-sized default; the build runs on tiles only when it partitions)
   TuneChoice c[AGG_TUNE_MAX];
   int nc = 0;
-  c[nc++] = {AGG_STRAT_SMEM, 512, sized};
-  if (maxs != sized) c[nc++] = {AGG_STRAT_SMEM, 512, maxs};
-  c[nc++] = {AGG_STRAT_SMEM, 256, sized};
-  c[nc++] = {AGG_STRAT_GLOBAL, 256, 0};
-  c[nc++] = {AGG_STRAT_GLOBAL, 512, 0};
-  c[nc++] = {AGG_STRAT_SORT, 0, 0};
+  c[nc++] = {AGG_STRAT_SMEM, 512, sized, 4, 0};
+  if (maxs != sized) c[nc++] = {AGG_STRAT_SMEM, 512, maxs, 4, 0};
+  c[nc++] = {AGG_STRAT_SMEM, 256, sized, 4, 0};
+  c[nc++] = {AGG_STRAT_SMEM, 512, sized, 8, 0};
+  c[nc++] = {AGG_STRAT_SMEM, 512, sized, 4, 16384};
+  c[nc++] = {AGG_STRAT_GLOBAL, 256, 0, 4, 0};
+  c[nc++] = {AGG_STRAT_GLOBAL, 512, 0, 8, 0};
+  c[nc++] = {AGG_STRAT_SORT, 0, 0, 0, 0};
   cudaEvent_t a, b;
   AGG_CUDA_TRY(cudaEventCreate(&a));
   AGG_CUDA_TRY(cudaEventCreate(&b));
@@ -74,6 +81,8 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
     o.block_threads = c[i].threads;
     o.smem_slots = c[i].smem_slots;
     o.table_slots = c[i].strategy == AGG_STRAT_SORT ? 0 : tslots;
+    o.items_per_thread = c[i].items;
+    o.tile_rows = c[i].tile;
     float best = INFINITY;
     for (int rep = 0; rep < std::max(1, reps) && st == AGG_OK; ++rep) {
       agg_groups* g = nullptr;
@@ -90,6 +99,8 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
     r->strategy[i] = c[i].strategy;
     r->threads[i] = c[i].threads;
     r->smem_slots[i] = c[i].smem_slots;
+    r->items_per_thread[i] = c[i].items;
+    r->tile_rows[i] = c[i].tile;
     r->ms[i] = best;
     const int k = c[i].strategy == AGG_STRAT_SMEM ? 0 : c[i].strategy == AGG_STRAT_GLOBAL ? 1 : 2;
     r->best_ms_per_strategy[k] = std::min(r->best_ms_per_strategy[k], best);
@@ -106,9 +117,18 @@ static agg_status run_candidates(const uint32_t* keys, const void* vals, int64_t
   return AGG_OK;
 }
 
+bool autotune_cached(int vdt, uint32_t ops, const float* feat, int* strategy, int* smem_slots) {
+  std::lock_guard<std::mutex> lk(g_tmu);
+  auto it = g_cache.find(signature(vdt, ops, feat));
+  if (it == g_cache.end()) return false;
+  *strategy = it->second.strategy;
+  *smem_slots = it->second.smem_slots;
+  return true;
+}
+
 agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
                          const float* feat, double hll, cudaStream_t s, int* strategy, int* smem_slots,
-                         int64_t* table_slots) {
+                         int64_t* table_slots, int* items, int* tile_rows) {
   *table_slots = 0;
   {
     std::lock_guard<std::mutex> lk(g_tmu);
@@ -116,6 +136,8 @@ agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int 
     if (it != g_cache.end()) {
       *strategy = it->second.strategy;
       *smem_slots = it->second.smem_slots;
+      *items = it->second.items;
+      *tile_rows = it->second.tile;
       return AGG_OK;
     }
   }
@@ -124,6 +146,8 @@ agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int 
   if (st != AGG_OK) return st;
   *strategy = r.strategy[r.best];
   *smem_slots = r.smem_slots[r.best];
+  *items = r.items_per_thread[r.best];
+  *tile_rows = r.tile_rows[r.best];
   return AGG_OK;
 }
 
@@ -169,11 +193,14 @@ extern "C" agg_status agg_autotune_save(const char* path) {
   FILE* f = std::fopen(path, "w");
   AGG_CHECK_ARG(f != nullptr, "cannot open %s", path);
   std::lock_guard<std::mutex> lk(g_tmu);
-  std::fprintf(f, "# agg autotune cache: dtype ops log2n log2d top8dec sorted -> strategy threads smem_slots\n");
+  std::fprintf(f,
+               "# agg autotune cache: dtype ops log2n log2d top8dec sorted -> strategy threads smem_slots items "
+               "tile_rows\n");
   for (const auto& kv : g_cache) {
     const Sig& k = kv.first;
-    std::fprintf(f, "%d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k),
-                 std::get<4>(k), std::get<5>(k), kv.second.strategy, kv.second.threads, kv.second.smem_slots);
+    std::fprintf(f, "%d %d %d %d %d %d %d %d %d %d %d\n", std::get<0>(k), std::get<1>(k), std::get<2>(k),
+                 std::get<3>(k), std::get<4>(k), std::get<5>(k), kv.second.strategy, kv.second.threads,
+                 kv.second.smem_slots, kv.second.items, kv.second.tile);
   }
   std::fclose(f);
   return AGG_OK;
@@ -188,12 +215,14 @@ extern "C" agg_status agg_autotune_load(const char* path) {
   std::lock_guard<std::mutex> lk(g_tmu);
   while (std::fgets(line, sizeof(line), f)) {
     if (line[0] == '#') continue;
-    int v[9];
-    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
-                    &v[8]) != 9)
+    int v[11];
+    if (std::sscanf(line, "%d %d %d %d %d %d %d %d %d %d %d", &v[0], &v[1], &v[2], &v[3], &v[4], &v[5], &v[6], &v[7],
+                    &v[8], &v[9], &v[10]) != 11)
       continue;
     if (v[6] < AGG_STRAT_SMEM || v[6] > AGG_STRAT_SORT) continue;
-    g_cache[Sig(v[0], v[1], v[2], v[3], v[4], v[5])] = TuneChoice{v[6], v[7], v[8]};
+    if (v[9] != 0 && v[9] != 4 && v[9] != 8) continue;
+    if (v[10] != 0 && (v[10] < 4096 || v[10] > 65536 || (v[10] & (v[10] - 1)) != 0)) continue;
+    g_cache[Sig(v[0], v[1], v[2], v[3], v[4], v[5])] = TuneChoice{v[6], v[7], v[8], v[9], v[10]};
   }
   std::fclose(f);
   return AGG_OK;

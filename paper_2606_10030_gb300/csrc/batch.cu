@@ -33,7 +33,7 @@
 
 namespace agg {
 
-constexpr int64_t kTileRows = int64_t(1) << 16;
+constexpr int64_t kTileRows = int64_t(1) << 16;  // default rows per work item (agg_batch_tune may change it)
 constexpr int kBatchThreads = 512;
 
 struct BQ {  // one query of a batch, on the device
@@ -94,7 +94,8 @@ __device__ void batch_tile_dt(const BQ& q, int64_t r0, int64_t r1, unsigned char
 
 __global__ void __launch_bounds__(kBatchThreads) batch_build(const BQ* __restrict__ qs, int nq,
                                                              const int64_t* __restrict__ tile_prefix,
-                                                             int64_t total_tiles, unsigned long long* next_tile) {
+                                                             int64_t total_tiles, unsigned long long* next_tile,
+                                                             int64_t tile_rows) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_tile;
   __shared__ int s_q;
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(kBatchThreads) batch_build(const BQ* __restric
     __syncthreads();  // everyone has read s_tile before the next pull overwrites it
     if (t >= total_tiles) return;
     const BQ& q = qs[qi];
-    const int64_t r0 = (t - q.tile0) * kTileRows;
-    const int64_t r1 = min(r0 + kTileRows, q.n);
+    const int64_t r0 = (t - q.tile0) * tile_rows;
+    const int64_t r1 = min(r0 + tile_rows, q.n);
     switch (q.dt) {
       case AGG_I32: batch_tile_dt<AGG_I32>(q, r0, r1, smem); break;
       case AGG_I64: batch_tile_dt<AGG_I64>(q, r0, r1, smem); break;
@@ -342,6 +343,7 @@ struct agg_batch_plan {
   cudaGraphExec_t exec = nullptr;
   int64_t graph_kernels = 0;
   std::vector<int64_t> groups;
+  int64_t tile_rows = agg::kTileRows;  // rows per (query, tile) work item
 };
 
 namespace agg {
@@ -442,7 +444,7 @@ static agg_status plan_alloc(agg_batch_plan* P, cudaStream_t s) {
     b.vals = q.vals;
     b.n = q.n;
     b.tile0 = tile_prefix[i];
-    tile_prefix[i + 1] = tile_prefix[i] + (q.n + kTileRows - 1) / kTileRows;
+    tile_prefix[i + 1] = tile_prefix[i] + (q.n + P->tile_rows - 1) / P->tile_rows;
     b.table = w + qp.table_off;
     b.status = P->status + i;
     b.slot0 = qp.large ? slot_prefix[li++] : -1;
@@ -507,7 +509,7 @@ static agg_status plan_enqueue(agg_batch_plan* P, cudaStream_t s, int64_t* kerne
   AGG_CUDA_TRY(cudaMemsetAsync(P->work, 0, P->zero_bytes, s));
   if (P->total_tiles > 0) {
     batch_build<<<P->build_grid, kBatchThreads, P->build_smem, s>>>(P->dq, P->nq, P->tile_prefix, P->total_tiles,
-                                                                     P->next_tile);
+                                                                     P->next_tile, P->tile_rows);
     ++k;
   }
   if (P->nsmall > 0) {
@@ -579,7 +581,12 @@ static void plan_sizes(agg_batch_plan* P, const std::vector<int>& learned) {
     qp.mm = ops_minmax(q.ops);
     int strat = q.strategy;
     if (strat == AGG_STRAT_LEARNED) strat = learned[i] >= 0 ? learned[i] : rule_strategy(f, q.ops);
-    else if (strat == AGG_STRAT_AUTO || strat == AGG_STRAT_AUTOTUNE) strat = rule_strategy(f, q.ops);
+    else if (strat == AGG_STRAT_AUTOTUNE) {
+      int sslots = 0;  // the autotuner's cached choice for this signature, else the rule
+      if (!autotune_cached(q.dtype, q.ops, f, &strat, &sslots)) strat = rule_strategy(f, q.ops);
+    } else if (strat == AGG_STRAT_AUTO) {
+      strat = rule_strategy(f, q.ops);
+    }
     // the batch runs hash strategies only: a query the selector would sort gets
     // shared-memory tables (hot keys stay in shared memory; a global table
     // alone would serialize their atomics)
@@ -738,6 +745,69 @@ extern "C" agg_status agg_batch_run(agg_batch_plan* P, void* stream) {
     agg_status st = plan_alloc(P, s);
     if (st != AGG_OK) return st;
   }
+}
+
+// Re-tile a plan: the per-query tile prefix is rebuilt and the graph
+// re-captured at the next run; tables and outputs stay.
+static agg_status plan_retile(agg_batch_plan* P, int64_t tile_rows, cudaStream_t s) {
+  if (P->exec) cudaGraphExecDestroy(P->exec);
+  if (P->graph) cudaGraphDestroy(P->graph);
+  P->exec = nullptr;
+  P->graph = nullptr;
+  P->tile_rows = tile_rows;
+  std::vector<int64_t> tp(P->nq + 1, 0);
+  for (int i = 0; i < P->nq; ++i) {
+    P->hq[i].tile0 = tp[i];
+    tp[i + 1] = tp[i] + (P->q[i].n + tile_rows - 1) / tile_rows;
+  }
+  P->total_tiles = tp[P->nq];
+  if (P->nq > 0) {
+    AGG_CUDA_TRY(cudaMemcpyAsync(P->dq, P->hq.data(), sizeof(BQ) * P->nq, cudaMemcpyHostToDevice, s));
+    AGG_CUDA_TRY(cudaMemcpyAsync(P->tile_prefix, tp.data(), sizeof(int64_t) * (P->nq + 1), cudaMemcpyHostToDevice, s));
+  }
+  AGG_CUDA_TRY(cudaStreamSynchronize(s));
+  return AGG_OK;
+}
+
+extern "C" agg_status agg_batch_tune(agg_batch_plan* P, int reps, int32_t* tile_rows_out, void* stream) {
+  clear_error();
+  AGG_CHECK_ARG(P != nullptr, "null plan");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int64_t cand[] = {16384, 32768, 65536};
+  float best_ms = INFINITY;
+  int64_t best = P->tile_rows;
+  cudaEvent_t a, b;
+  AGG_CUDA_TRY(cudaEventCreate(&a));
+  AGG_CUDA_TRY(cudaEventCreate(&b));
+  agg_status st = AGG_OK;
+  for (int64_t t : cand) {
+    st = plan_retile(P, t, s);
+    if (st == AGG_OK) st = agg_batch_run(P, stream);  // capture (and regrow if needed)
+    if (st != AGG_OK) break;
+    float ms = INFINITY;
+    for (int r = 0; r < std::max(1, reps) && st == AGG_OK; ++r) {
+      cudaEventRecord(a, s);
+      st = agg_batch_run(P, stream);
+      cudaEventRecord(b, s);
+      cudaEventSynchronize(b);
+      float m = 0.f;
+      cudaEventElapsedTime(&m, a, b);
+      ms = std::min(ms, m);
+    }
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  if (st != AGG_OK) return st;
+  if (P->tile_rows != best) {
+    st = plan_retile(P, best, s);
+    if (st != AGG_OK) return st;
+  }
+  if (tile_rows_out) *tile_rows_out = (int32_t)best;
+  return AGG_OK;
 }
 
 extern "C" agg_status agg_batch_result(const agg_batch_plan* P, int i, agg_groups** out) {

@@ -19,27 +19,38 @@ namespace agg {
 // ---------------------------------------------------------------------------
 using KernelPtr = const void*;
 
-template <int DT, bool MM>
-static KernelPtr build_kernel(bool smem, bool vec, bool multi) {
-  if (smem) {
-    if (!vec) return (KernelPtr)gb_build<DT, MM, true, false, false>;
-    return multi ? (KernelPtr)gb_build<DT, MM, true, true, true> : (KernelPtr)gb_build<DT, MM, true, true, false>;
-  }
-  if (!vec) return (KernelPtr)gb_build<DT, MM, false, false, false>;
-  return multi ? (KernelPtr)gb_build<DT, MM, false, true, true> : (KernelPtr)gb_build<DT, MM, false, true, false>;
+// qpi: quads (4 rows) a thread folds per iteration of the vector loop, 1 or 2.
+template <int DT, bool MM, bool SMEM, bool MULTI>
+static KernelPtr build_vec(int qpi) {
+  return qpi == 2 ? (KernelPtr)gb_build<DT, MM, SMEM, true, MULTI, 2> : (KernelPtr)gb_build<DT, MM, SMEM, true, MULTI, 1>;
 }
 
-static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec, bool multi) {
+template <int DT, bool MM>
+static KernelPtr build_kernel(bool smem, bool vec, bool multi, int qpi) {
+  if (smem) {
+    if (!vec) return (KernelPtr)gb_build<DT, MM, true, false, false>;
+    return multi ? build_vec<DT, MM, true, true>(qpi) : build_vec<DT, MM, true, false>(qpi);
+  }
+  if (!vec) return (KernelPtr)gb_build<DT, MM, false, false, false>;
+  return multi ? build_vec<DT, MM, false, true>(qpi) : build_vec<DT, MM, false, false>(qpi);
+}
+
+static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec, bool multi, int qpi) {
 #define AGG_B(D) \
-  case D: return mm ? build_kernel<D, true>(smem, vec, multi) : build_kernel<D, false>(smem, vec, multi);
+  case D: return mm ? build_kernel<D, true>(smem, vec, multi, qpi) : build_kernel<D, false>(smem, vec, multi, qpi);
   switch (dt) { AGG_B(AGG_I32) AGG_B(AGG_I64) AGG_B(AGG_U32) AGG_B(AGG_F32) AGG_B(AGG_F64) }
 #undef AGG_B
   return nullptr;
 }
 
-static KernelPtr pick_tiles(int dt, bool mm) {
+template <int DT, bool MM>
+static KernelPtr tiles_kernel(int qpi) {
+  return qpi == 2 ? (KernelPtr)gb_build_tiles<DT, MM, true, 2> : (KernelPtr)gb_build_tiles<DT, MM, true, 1>;
+}
+
+static KernelPtr pick_tiles(int dt, bool mm, int qpi) {
 #define AGG_T(D) \
-  case D: return mm ? (KernelPtr)gb_build_tiles<D, true, true> : (KernelPtr)gb_build_tiles<D, false, true>;
+  case D: return mm ? tiles_kernel<D, true>(qpi) : tiles_kernel<D, false>(qpi);
   switch (dt) { AGG_T(AGG_I32) AGG_T(AGG_I64) AGG_T(AGG_U32) AGG_T(AGG_F32) AGG_T(AGG_F64) }
 #undef AGG_T
   return nullptr;
@@ -237,6 +248,8 @@ struct HashPlan {
   int threads;
   int blocks_per_sm;
   bool multi_keys = true;  // per-warp reduction of several frequent keys (see build_rows)
+  int qpi = 1;             // quads (4 rows) a thread folds per iteration: items per thread / 4
+  int64_t tile_rows = 0;   // rows per tile of the partitioned build (0: from the column)
 };
 
 // One hash aggregation: a zeroed global table, any number of build launches
@@ -294,7 +307,7 @@ class HashRun {
     a.status = status_;
     a.progress = progress_;
     if (plan_.partition && n >= kPartTileRows) return build_partitioned(a, use_smem);
-    KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec, plan_.multi_keys);
+    KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec, plan_.multi_keys, plan_.qpi);
     const size_t smem = use_smem ? stab_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;
     const int threads = plan_.threads;
     int bps = occupancy(bk, threads, smem);
@@ -324,7 +337,7 @@ class HashRun {
     const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255), vb = ((size_t)n * es + 255) & ~size_t(255);
     const int passes = plan_.partition_passes;
     void* tmp = nullptr;
-    AGG_CUDA_TRY(dev_malloc_async(&tmp, passes * (kb + vb) + radix_tmp_bytes(n), s_));
+    AGG_CUDA_TRY(dev_malloc_async(&tmp, passes * (kb + vb) + std::max(radix_tmp_bytes(n), partition_tmp_bytes()), s_));
     uint32_t* kp = (uint32_t*)tmp;
     char* vp = (char*)tmp + kb;
     uint32_t* kq = (uint32_t*)((char*)tmp + kb + vb);
@@ -363,7 +376,7 @@ class HashRun {
           set_error("partitioned build: %s", cudaGetErrorString(e));
           return AGG_ERR_CUDA;
         }
-        KernelPtr bk = pick_tiles(vdt_, mm_);
+        KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi);
         const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
         const int threads = plan_.threads;
         int bps = occupancy(bk, threads, smem);
@@ -371,14 +384,17 @@ class HashRun {
         int64_t grid = (int64_t)di.sm_count * bps;
         // tiles of up to 64 Ki rows (32 Ki after two levels), smaller (down to
         // 4 Ki) when the column would give each resident block fewer than two
-        int64_t tile_rows = plan_.partition_passes == 2 ? kPartTileRows / 2 : kPartTileRows;
-        while (tile_rows > 4096 && n < 2 * grid * tile_rows) tile_rows >>= 1;
+        int64_t tile_rows = plan_.tile_rows;
+        if (tile_rows == 0) {
+          tile_rows = plan_.partition_passes == 2 ? kPartTileRows / 2 : kPartTileRows;
+          while (tile_rows > 4096 && n < 2 * grid * tile_rows) tile_rows >>= 1;
+        }
         const int64_t tiles = (n + tile_rows - 1) / tile_rows;
         if (tiles < grid) grid = tiles;
         void* args[] = {&a, &next_tile, &tile_rows};
         e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, smem, s_);
       } else {
-        KernelPtr bk = pick_build(vdt_, mm_, false, true, true);
+        KernelPtr bk = pick_build(vdt_, mm_, false, true, true, plan_.qpi);
         const int threads = plan_.threads;
         int bps = occupancy(bk, threads, 0);
         if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
@@ -523,7 +539,7 @@ agg_status sketch_and_select(const uint32_t* keys, int64_t n, int vdt, uint32_t 
                              cudaStream_t s, float* feat, int* strategy);
 agg_status autotune_pick(const uint32_t* keys, const void* vals, int64_t n, int vdt, uint32_t ops,
                          const float* feat, double hll, cudaStream_t s, int* strategy, int* smem_slots,
-                         int64_t* table_slots);
+                         int64_t* table_slots, int* items, int* tile_rows);
 
 // Sketch the keys on the device and read the features back (one sync).
 agg_status sketch_features(const uint32_t* keys, int64_t n, int vdt, uint32_t ops, uint64_t offset,
@@ -593,12 +609,14 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   int strategy = o.strategy;
   int64_t tslots = o.table_slots;
   int sslots = o.smem_slots;
+  int items = o.items_per_thread;
+  int tile = o.tile_rows;
   if (strategy == AGG_STRAT_LEARNED) {
     bool ok = false;
     strategy = select_learned(feat, &ok);
     if (!ok) strategy = rule_strategy(feat, ops, hll);
   } else if (strategy == AGG_STRAT_AUTOTUNE) {
-    agg_status st = autotune_pick(keys, vals, n, vdt, ops, feat, hll, s, &strategy, &sslots, &tslots);
+    agg_status st = autotune_pick(keys, vals, n, vdt, ops, feat, hll, s, &strategy, &sslots, &tslots, &items, &tile);
     if (st != AGG_OK) return st;
   } else if (strategy == AGG_STRAT_AUTO) {
     strategy = have_feat ? rule_strategy(feat, ops, hll) : AGG_STRAT_GLOBAL;
@@ -613,6 +631,8 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   // the warp-level reduction of several keys pay; without a sketch, assume so
   c->plan.multi_keys = !have_feat || feat[F_TOP1] >= 0.03f || est <= 32.0;
   c->plan.blocks_per_sm = o.blocks_per_sm;
+  c->plan.qpi = items == 8 ? 2 : 1;
+  c->plan.tile_rows = tile;
   // Partition the rows by hash first when the shared tables would spill (more
   // distinct keys than a shared table admits) or the global table exceeds
   // half of L2; each partition then has about 1/256 of the keys.
@@ -985,6 +1005,11 @@ static agg_status check_groupby_args(const uint32_t* keys, const void* vals, int
                                                opt->block_threads % 32 == 0),
                   "block_threads must be 0 or a multiple of 32 in [64, 1024]");
     AGG_CHECK_ARG(opt->blocks_per_sm >= 0, "blocks_per_sm must be >= 0");
+    AGG_CHECK_ARG(opt->items_per_thread == 0 || opt->items_per_thread == 4 || opt->items_per_thread == 8,
+                  "items_per_thread must be 0, 4 or 8");
+    AGG_CHECK_ARG(opt->tile_rows == 0 || (opt->tile_rows >= 4096 && opt->tile_rows <= 65536 &&
+                                          (opt->tile_rows & (opt->tile_rows - 1)) == 0),
+                  "tile_rows must be 0 or a power of two in [4096, 65536]");
     AGG_CHECK_ARG((opt->flags & ~(AGG_FLAG_EXACT_SUM | AGG_FLAG_SUM_ERROR)) == 0, "unknown flags 0x%x",
                   (unsigned)opt->flags);
   }

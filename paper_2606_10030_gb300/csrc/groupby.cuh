@@ -62,6 +62,9 @@ int64_t table_slots_from_sketch(const float* feat, int64_t n);
 // The same from the HyperLogLog count when one was taken (hll > 0).
 int64_t table_slots_for(const float* feat, int64_t n, double hll);
 
+// The autotuner's cached choice for a query signature (no tuning on a miss).
+bool autotune_cached(int vdt, uint32_t ops, const float* feat, int* strategy, int* smem_slots);
+
 // Output block shared by the results of one batch (reference counted).
 struct SharedBlock;
 void shared_block_release(SharedBlock* b);

@@ -576,21 +576,19 @@ __device__ __forceinline__ void report_counts(const BuildArgs& a, const BlockCou
 }
 
 // Rows [0, a.n) of a column folded by threads tid, tid + nthreads, ...
-// VEC: 16-byte vector loads of 4 keys and 4 values per quad, kQuadsPerIter
-// quads per thread per iteration (all loads issued before any row is folded).
-#ifndef AGG_QUADS_PER_ITER
-#define AGG_QUADS_PER_ITER 1
-#endif
-constexpr int kQuadsPerIter = AGG_QUADS_PER_ITER;
+// VEC: 16-byte vector loads of 4 keys and 4 values per quad, QPI quads per
+// thread per iteration (all loads issued before any row is folded): 4 or 8
+// rows a thread per iteration, the autotuner's items-per-thread axis.
 
 // Returns the number of rows this thread went through (the vector body's).
 // MULTI: up to kMaxWarpKeys frequent keys per warp and quad of rows get a
 // reduced update (columns with a handful of keys or hot keys); without it
 // every row takes the per-row path (for columns whose sketch shows no
 // frequent key: the warp then never waits for its slowest lane).
-template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true>
+template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true, int QPI = 1>
 __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
                                                int64_t nthreads) {
+  constexpr int kQuadsPerIter = QPI;
   using T = typename GV<DT>::T;
   const uint32_t* keys = a.keys;
   const T* vals = (const T*)a.vals;
@@ -723,7 +721,7 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
 }
 
 // The build kernel of one query: grid-stride over all rows.
-template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI>
+template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI, int QPI = 1>
 __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlockCounts s_cnt;
@@ -735,7 +733,7 @@ __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
     st.clear(a.smem_slots);
   }
   __syncthreads();
-  const uint32_t seen = build_rows<DT, MM, SMEM, VEC, MULTI>(
+  const uint32_t seen = build_rows<DT, MM, SMEM, VEC, MULTI, QPI>(
       a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
   atomicAdd(&s_cnt.seen, seen);
   if (SMEM) {
@@ -752,7 +750,7 @@ __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
 // first and merges it into the global table at the end.
 constexpr int64_t kPartTileRows = int64_t(1) << 16;
 
-template <int DT, bool MM, bool VEC>
+template <int DT, bool MM, bool VEC, int QPI = 1>
 __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
                                                         int64_t tile_rows) {
   using T = typename GV<DT>::T;
@@ -778,7 +776,7 @@ __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned l
     b.head = 0;
     st.clear(a.smem_slots);
     __syncthreads();
-    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC>(b, st, threadIdx.x, blockDim.x));
+    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI>(b, st, threadIdx.x, blockDim.x));
     __syncthreads();
     flush_smem<DT, MM>(b, st);
     __syncthreads();

@@ -358,57 +358,75 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
 // One-level hash partition without a stable order (the hash build needs rows
 // grouped by partition, in any order within one). Two kernels:
 //   part_hist     256-bin histogram of the partition digit (top 8 bits of
-//                 fmix32(key)), per-warp counters in shared memory, merged with
-//                 one global atomic per bin and block; the last block to finish
+//                 fmix32(key)) in per-warp shared counters, merged with one
+//                 global atomic per bin and block; the last block to finish
 //                 turns the totals into each partition's start;
-//   part_scatter  per tile of kPartTile rows: every row's place within its
-//                 digit's run of the tile from a shared-memory counter (lanes
-//                 of a warp holding the same digit share one atomic, so hot
-//                 keys do not serialise), the tile's runs reserved in the output
-//                 with one global atomic per digit, the rows staged in shared
-//                 memory in digit order and written out run by run.
-// Reads 4 + 12 B and writes 12 B per row (uint32 key, 8-byte value), with no
-// per-tile count array and no ranking rounds.
+//   part_scatter  per tile of kPartTile rows (one block of 1024 threads, 8 rows
+//                 a thread, keys and values loaded up front): each row's place
+//                 among its warp's rows of the same digit from a per-warp
+//                 shared counter (a plain atomic: order within a partition is
+//                 free), the warps' counts scanned per digit, the tile's runs
+//                 reserved in the output with one global atomic per digit, the
+//                 rows staged in shared memory in digit order and written out
+//                 run by run.
+// Reads 4 + 12 B and writes 12 B per row (uint32 key, 8-byte value); no per-tile
+// count array and no ranking rounds.
 // ---------------------------------------------------------------------------
-constexpr int kPartThreads = 512;
+constexpr int kPartHistThreads = 512;
+constexpr int kPartThreads = 1024;
 constexpr int kPartTile = 8192;
+constexpr int kFillStride = 32;  // global fill counters 256 B apart (different L2 lines)
 
 __device__ __forceinline__ uint32_t part_digit(uint32_t key) { return fmix32(key) >> 24; }
 
-// fill[0..256): partition starts (written by the last block), fill[256]: ticket.
-__global__ void __launch_bounds__(kPartThreads) part_hist(const uint32_t* __restrict__ keys, int64_t n,
-                                                          unsigned long long* __restrict__ fill) {
-  constexpr int kWarps = kPartThreads / 32;
+// fill[d * kFillStride]: partition starts (written by the last block), fill[256 * kFillStride]: ticket.
+__global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __restrict__ keys, int64_t n,
+                                                              int64_t head, unsigned long long* __restrict__ fill) {
+  constexpr int kWarps = kPartHistThreads / 32;
   __shared__ uint32_t h[kWarps][256];
+  __shared__ unsigned long long tot[256];
   __shared__ int s_last;
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) (&h[0][0])[i] = 0;
+  const int w = threadIdx.x >> 5;
+  for (int i = threadIdx.x; i < kWarps * 256; i += kPartHistThreads) (&h[0][0])[i] = 0;
   __syncthreads();
-  const int64_t nthreads = (int64_t)gridDim.x * kPartThreads;
-  for (int64_t i0 = (int64_t)blockIdx.x * kPartThreads + (threadIdx.x & ~31); i0 < n; i0 += nthreads) {
-    const int64_t i = i0 + lane;
-    const bool ok = i < n;
-    const uint32_t d = ok ? part_digit(keys[i]) : 0u;
-    const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u);
-    if (ok && lane == __ffs(peers) - 1) atomicAdd(&h[w][d], (uint32_t)__popc(peers));
+  const int64_t g = (int64_t)blockIdx.x * kPartHistThreads + threadIdx.x;
+  const int64_t nthreads = (int64_t)gridDim.x * kPartHistThreads;
+  const int64_t nq = (n - head) / 4;
+  const int64_t tail0 = head + nq * 4;
+  if (g < head) atomicAdd(&h[w][part_digit(keys[g])], 1u);
+  if (g < n - tail0) atomicAdd(&h[w][part_digit(keys[tail0 + g])], 1u);
+  const uint4* kq = (const uint4*)(keys + head);
+  for (int64_t q = g; q < nq; q += 2 * nthreads) {  // two 16-byte loads in flight per thread
+    const uint4 a = ld_stream_v4(kq + q);
+    const bool two = q + nthreads < nq;
+    const uint4 b = two ? ld_stream_v4(kq + q + nthreads) : make_uint4(0, 0, 0, 0);
+    atomicAdd(&h[w][part_digit(a.x)], 1u);
+    atomicAdd(&h[w][part_digit(a.y)], 1u);
+    atomicAdd(&h[w][part_digit(a.z)], 1u);
+    atomicAdd(&h[w][part_digit(a.w)], 1u);
+    if (two) {
+      atomicAdd(&h[w][part_digit(b.x)], 1u);
+      atomicAdd(&h[w][part_digit(b.y)], 1u);
+      atomicAdd(&h[w][part_digit(b.z)], 1u);
+      atomicAdd(&h[w][part_digit(b.w)], 1u);
+    }
   }
   __syncthreads();
   if (threadIdx.x < 256) {
     uint32_t t = 0;
     for (int ww = 0; ww < kWarps; ++ww) t += h[ww][threadIdx.x];
-    if (t) atomicAdd(&fill[threadIdx.x], (unsigned long long)t);
+    if (t) atomicAdd(&fill[threadIdx.x * kFillStride], (unsigned long long)t);
   }
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&fill[256], 1ull) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(&fill[256 * kFillStride], 1ull) == gridDim.x - 1;
   __syncthreads();
   if (!s_last) return;  // the whole block leaves together
   __threadfence();
-  // exclusive scan of the 256 totals (one warp, 8 chunks of 32)
-  __shared__ unsigned long long tot[256];
-  if (threadIdx.x < 256) tot[threadIdx.x] = __ldcg(&fill[threadIdx.x]);
+  if (threadIdx.x < 256) tot[threadIdx.x] = __ldcg(&fill[threadIdx.x * kFillStride]);
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (threadIdx.x < 32) {  // exclusive scan of the 256 totals: one warp, 8 chunks of 32
+    const int lane = threadIdx.x;
     unsigned long long run = 0;
     for (int j = 0; j < 8; ++j) {
       unsigned long long x = tot[j * 32 + lane];
@@ -417,70 +435,71 @@ __global__ void __launch_bounds__(kPartThreads) part_hist(const uint32_t* __rest
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      const unsigned long long incl = x + run;
-      const unsigned long long excl = incl - tot[j * 32 + lane];
-      run = __shfl_sync(0xffffffffu, incl, 31);
-      fill[j * 32 + lane] = excl;
+      fill[(j * 32 + lane) * kFillStride] = run + x - tot[j * 32 + lane];
+      run += __shfl_sync(0xffffffffu, x, 31);
     }
   }
-  if (threadIdx.x == 0) fill[256] = 0;
 }
 
 template <class P>
-__global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* __restrict__ keys,
-                                                             const P* __restrict__ vals, uint32_t* __restrict__ okeys,
-                                                             P* __restrict__ ovals, int64_t n,
-                                                             unsigned long long* __restrict__ fill) {
+__global__ void __launch_bounds__(kPartThreads, 1) part_scatter(const uint32_t* __restrict__ keys,
+                                                                const P* __restrict__ vals,
+                                                                uint32_t* __restrict__ okeys, P* __restrict__ ovals,
+                                                                int64_t n, unsigned long long* __restrict__ fill) {
   constexpr int kRows = kPartTile / kPartThreads;  // rows per thread and tile
+  constexpr int kWarps = kPartThreads / 32;
   extern __shared__ __align__(16) unsigned char sm_raw[];
   P* stage_v = (P*)sm_raw;                                // kPartTile
   uint32_t* stage_k = (uint32_t*)(stage_v + kPartTile);  // kPartTile
-  __shared__ uint32_t cnt[256], off[256];
+  uint32_t* whist = stage_k + kPartTile;                 // kWarps x 256
+  __shared__ uint32_t off[256];
   __shared__ unsigned long long base[256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const uint32_t lt = (1u << lane) - 1u;
   const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     const int64_t r0 = t * kPartTile;
     const int rows = (int)min((int64_t)kPartTile, n - r0);
-    if (threadIdx.x < 256) cnt[threadIdx.x] = 0;
-    __syncthreads();
-    // each warp owns kRows * 32 consecutive rows; rows in registers, places in the digit runs
+    for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) whist[i] = 0;
+    // each warp owns kRows * 32 consecutive rows: every key and value load is issued first
     uint32_t kr[kRows], pr[kRows];
+    P vr[kRows];
     const int wbase = w * kRows * 32;
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
       kr[r] = j < rows ? keys[r0 + j] : 0u;
+      vr[r] = j < rows ? vals[r0 + j] : P(0);
     }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
-      const bool ok = j < rows;
-      const uint32_t d = part_digit(kr[r]);
-      const uint32_t peers = __match_any_sync(0xffffffffu, ok ? d : 0x100u);
-      const int leader = __ffs(peers) - 1;
-      uint32_t b = 0;
-      if (ok && lane == leader) b = atomicAdd(&cnt[d], (uint32_t)__popc(peers));
-      b = __shfl_sync(0xffffffffu, b, leader);
-      pr[r] = b + __popc(peers & lt);
+      if (j < rows) pr[r] = atomicAdd(&whist[w * 256 + part_digit(kr[r])], 1u);
     }
     __syncthreads();
-    // the tile's digit runs: offsets in the stage, and places in the output
-    if (threadIdx.x < 256) {
-      const uint32_t c = cnt[threadIdx.x];
-      base[threadIdx.x] = c ? atomicAdd(&fill[threadIdx.x], (unsigned long long)c) : 0ull;
+    if (threadIdx.x < 256) {  // per digit: the warps' runs, and the tile's count
+      const int d = threadIdx.x;
+      uint32_t run = 0;
+      for (int ww = 0; ww < kWarps; ++ww) {
+        const uint32_t c = whist[ww * 256 + d];
+        whist[ww * 256 + d] = run;
+        run += c;
+      }
+      off[d] = run;  // the tile's count of digit d, until the scan below
+      base[d] = run ? atomicAdd(&fill[d * kFillStride], (unsigned long long)run) : 0ull;
     }
-    if (threadIdx.x < 32) {
+    __syncthreads();
+    if (threadIdx.x < 32) {  // exclusive scan of the counts over digits
       uint32_t run = 0;
       for (int j = 0; j < 8; ++j) {
-        uint32_t x = cnt[j * 32 + lane];
+        const uint32_t c = off[j * 32 + lane];
+        uint32_t x = c;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
           const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
           if (lane >= o) x += y;
         }
-        off[j * 32 + lane] = x + run - cnt[j * 32 + lane];
+        off[j * 32 + lane] = run + x - c;
         run += __shfl_sync(0xffffffffu, x, 31);
       }
     }
@@ -489,9 +508,10 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
       if (j < rows) {
-        const uint32_t p = off[part_digit(kr[r])] + pr[r];
+        const uint32_t d = part_digit(kr[r]);
+        const uint32_t p = off[d] + whist[w * 256 + d] + pr[r];
         stage_k[p] = kr[r];
-        stage_v[p] = vals[r0 + j];
+        stage_v[p] = vr[r];
       }
     }
     __syncthreads();
@@ -508,10 +528,10 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
 
 template <class P>
 static size_t part_smem() {
-  return (size_t)kPartTile * (sizeof(P) + 4);
+  return (size_t)kPartTile * (sizeof(P) + 4) + (size_t)(kPartThreads / 32) * 256 * 4;
 }
 
-size_t partition_tmp_bytes() { return 257 * sizeof(unsigned long long) + 256; }
+size_t partition_tmp_bytes() { return (257 * kFillStride) * sizeof(unsigned long long) + 256; }
 
 template <class P>
 agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
@@ -528,18 +548,22 @@ agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P
     attr[dev] = true;
   }
   unsigned long long* fill = (unsigned long long*)tmp;
-  AGG_CUDA_TRY(cudaMemsetAsync(fill, 0, 257 * sizeof(unsigned long long), s));
+  AGG_CUDA_TRY(cudaMemsetAsync(fill, 0, (257 * kFillStride) * sizeof(unsigned long long), s));
   const DeviceInfo& di = device_info();
   int bh = 1, bs = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, part_hist, kPartThreads, 0) != cudaSuccess || bh < 1) bh = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, part_hist, kPartHistThreads, 0) != cudaSuccess || bh < 1)
+    bh = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, part_scatter<P>, kPartThreads, part_smem<P>()) !=
           cudaSuccess ||
       bs < 1)
     bs = 1;
+  int64_t head = (int64_t)(((16 - ((uintptr_t)kin & 15)) & 15) / 4);
+  if (head > n) head = n;
   const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
-  const int64_t gh = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bh, (n + kPartThreads - 1) / kPartThreads));
+  const int64_t gh = std::max<int64_t>(
+      1, std::min<int64_t>((int64_t)di.sm_count * bh, ((n - head) / 4 + 2 * kPartHistThreads - 1) / (2 * kPartHistThreads)));
   const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, ntiles));
-  part_hist<<<(unsigned)gh, kPartThreads, 0, s>>>(kin, n, fill);
+  part_hist<<<(unsigned)gh, kPartHistThreads, 0, s>>>(kin, n, head, fill);
   part_scatter<P><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kin, vin, kout, vout, n, fill);
   note_launch(2);
   AGG_CUDA_TRY(cudaGetLastError());

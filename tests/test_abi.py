@@ -83,6 +83,10 @@ def test_groupby_batch_and_network_reject_bad_arguments_without_launching(L):
     assert L.agg_groupby(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
                          None) == agg.AGG_ERR_INVALID
     assert "flags" in agg.last_error()
+    for kw in (dict(items_per_thread=5), dict(tile_rows=1000), dict(tile_rows=1 << 17)):
+        o = agg.options(**kw)
+        assert L.agg_groupby(k, v, 10, agg.AGG_I32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),
+                             None) == agg.AGG_ERR_INVALID, kw
     for f in (agg.AGG_FLAG_EXACT_SUM, agg.AGG_FLAG_SUM_ERROR):  # the exact float sums read device columns
         o = agg.options(flags=f)
         assert L.agg_groupby_host(k, v, 10, agg.AGG_F32, agg.AGG_SUM, ctypes.byref(o), ctypes.byref(out),

@@ -101,3 +101,20 @@ def test_batch_result_outlives_the_plan():
     for (k, v, ops, _), g in zip(queries, gs):
         check_groups(g.to_host(), k.cpu().numpy(), v.cpu().numpy(), ops)
         g.free()
+
+
+def test_batch_tune_picks_a_tile_and_keeps_results():
+    import oracle
+    qs = dg.batch_queries(24, 5, log2_rows=(12, 20), log2_keys=(0, 16))
+    cols = [dgc.group_column(q) for q in qs]
+    plan = agg.BatchPlan([(k, v, q.ops, agg.AGG_STRAT_AUTO) for (k, v), q in zip(cols, qs)])
+    tile = plan.tune(1)
+    assert tile in (16384, 32768, 65536)
+    plan.run()
+    for i, ((k, v), q) in enumerate(zip(cols, qs)):
+        g = plan.result(i)
+        res = g.to_host()
+        g.free()
+        ref = oracle.groupby(k.cpu().numpy(), v.cpu().numpy())
+        assert np.array_equal(res["keys"], ref.keys) and np.array_equal(res["count"], ref.count)
+    plan.free()

@@ -253,3 +253,12 @@ def test_hash_partitioned_build_parity(levels, strategy, dt, case):
     check_groups(res, keys, vals)
     res2, _ = run(keys, vals, strategy, partition=-1)
     assert np.array_equal(res["keys"], res2["keys"]) and np.array_equal(res["count"], res2["count"])
+
+
+@pytest.mark.parametrize("items", [4, 8])
+@pytest.mark.parametrize("tile", [0, 4096, 16384])
+def test_items_per_thread_and_tile_rows(items, tile):
+    keys, vals = make_case("uniform50k", "f64", seed=17)
+    for strategy, part in ((agg.AGG_STRAT_SMEM, 1), (agg.AGG_STRAT_SMEM, -1), (agg.AGG_STRAT_GLOBAL, -1)):
+        res, _ = run(keys, vals, strategy, items_per_thread=items, tile_rows=tile, partition=part)
+        check_groups(res, keys, vals)

@@ -82,7 +82,8 @@ def test_autotune_times_every_candidate_and_caches():
     keys = torch.from_numpy(dg.keys_uniform(1 << 20, 500, 0)).cuda()
     vals = torch.from_numpy(dg.values("i64", 1 << 20, 0)).cuda()
     r = agg.agg_autotune(keys, vals, agg.AGG_ALL, reps=2)
-    assert r.ncand >= 5 and 0 <= r.best < r.ncand
+    assert r.ncand >= 7 and 0 <= r.best < r.ncand
+    assert set(list(r.items_per_thread)[:r.ncand]) >= {4, 8} and 16384 in list(r.tile_rows)[:r.ncand]
     ms = np.array(list(r.ms)[:r.ncand])
     assert np.all(ms > 0) and ms[r.best] == ms.min()
     assert set(list(r.strategy)[:r.ncand]) == {agg.AGG_STRAT_SMEM, agg.AGG_STRAT_GLOBAL, agg.AGG_STRAT_SORT}
