@@ -361,8 +361,9 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
 //                 fmix32(key)) in per-warp shared counters, merged with one
 //                 global atomic per bin and block; the last block to finish
 //                 turns the totals into each partition's start;
-//   part_scatter  per tile of kPartTile rows (one block of 1024 threads, 8 rows
-//                 a thread, keys and values loaded up front): each row's place
+//   part_scatter  per tile of kPartTile rows (a block of 512 threads, 8 rows a
+//                 thread, keys and values loaded up front; two blocks a SM so
+//                 that one's barriers overlap the other's loads): each row's place
 //                 among its warp's rows of the same digit from a per-warp
 //                 shared counter (a plain atomic: order within a partition is
 //                 free), the warps' counts scanned per digit, the tile's runs
@@ -373,8 +374,8 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
 // count array and no ranking rounds.
 // ---------------------------------------------------------------------------
 constexpr int kPartHistThreads = 512;
-constexpr int kPartThreads = 1024;
-constexpr int kPartTile = 8192;
+constexpr int kPartThreads = 512;
+constexpr int kPartTile = 4096;
 constexpr int kFillStride = 32;  // global fill counters 256 B apart (different L2 lines)
 
 __device__ __forceinline__ uint32_t part_digit(uint32_t key) { return fmix32(key) >> 24; }
@@ -442,7 +443,7 @@ __global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __
 }
 
 template <class P>
-__global__ void __launch_bounds__(kPartThreads, 1) part_scatter(const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* __restrict__ keys,
                                                                 const P* __restrict__ vals,
                                                                 uint32_t* __restrict__ okeys, P* __restrict__ ovals,
                                                                 int64_t n, unsigned long long* __restrict__ fill) {

@@ -46,8 +46,11 @@ def sample_queries(count: int, seed: int, log2_rows=(16, 24), log2_keys=(0, 26),
     return out
 
 
-def label(queries, reps: int = 1, log_every: int = 0):
-    """Features, labels and per-strategy best times (ms) from the autotuner."""
+def label(queries, reps: int = 1, log_every: int = 0, checkpoint: str = ""):
+    """Features, labels and per-strategy best times (ms) from the autotuner.
+
+    With a checkpoint path, the arrays labelled so far are saved there every
+    log_every queries (a long labelling run keeps its progress)."""
     import torch
 
     from datagen import cuda as dgc
@@ -70,6 +73,8 @@ def label(queries, reps: int = 1, log_every: int = 0):
         ops_all[i] = q.ops
         if log_every and (i + 1) % log_every == 0:
             print(f"labelled {i + 1}/{len(queries)} in {time.time() - t0:.1f}s", flush=True)
+            if checkpoint:
+                np.savez(checkpoint, X=X[:i + 1], y=y[:i + 1], T=T[:i + 1], ops=ops_all[:i + 1])
     return X, y, T, ops_all
 
 
@@ -225,6 +230,8 @@ def main():
     ap.add_argument("--out", default=DEFAULT_WEIGHTS)
     ap.add_argument("--evaluate-large", default="", help="write the large-table evaluation (JSON) to this path")
     ap.add_argument("--large-log2-rows", type=int, default=30)
+    ap.add_argument("--checkpoint", default="", help="save the labelled arrays here as labelling proceeds")
+    ap.add_argument("--data", default="", help="train on labelled arrays saved earlier (skips labelling)")
     args = ap.parse_args()
     if args.evaluate_large:
         import json
@@ -234,9 +241,13 @@ def main():
             json.dump(ev, f, indent=1)
         print({k: v for k, v in ev.items() if k != "tables"})
         return
-    qs = sample_queries(args.samples + args.holdout, args.seed, log2_rows=(16, args.max_log2_rows))
-    X, y, T, ops = label(qs, log_every=200)
-    ntr = args.samples
+    if args.data:
+        d = np.load(args.data)
+        X, y, T, ops = d["X"], d["y"], d["T"], d["ops"]
+    else:
+        qs = sample_queries(args.samples + args.holdout, args.seed, log2_rows=(16, args.max_log2_rows))
+        X, y, T, ops = label(qs, log_every=500, checkpoint=args.checkpoint)
+    ntr = min(args.samples, len(X) - max(1, args.holdout))
     params, mean, std, losses = train(X[:ntr], y[:ntr], epochs=args.epochs, seed=args.seed)
     ev = evaluate(params, mean, std, X[ntr:], T[ntr:], ops[ntr:])
     print("loss first/last epoch", float(losses[0]), float(losses[-1]))
