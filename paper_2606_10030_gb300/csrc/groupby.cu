@@ -14,6 +14,59 @@
 
 namespace agg {
 
+// The tile list of a column partitioned chunk by chunk: starts[k * 257 + p] is
+// where partition p of chunk k begins (starts[k * 257 + 256] the chunk's end);
+// piece (p, k) becomes ceil(rows / tile_rows) tiles, listed partition by
+// partition (chunk order within a partition), so that neighbouring tiles
+// update one region of the global table. One block.
+__global__ void __launch_bounds__(1024) gb_piece_tiles(const unsigned long long* __restrict__ starts, int nchunks,
+                                                       int64_t tile_rows, longlong2* __restrict__ tiles,
+                                                       unsigned long long* __restrict__ ntiles) {
+  __shared__ unsigned long long warp_tot[32];
+  __shared__ unsigned long long carry;
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  const int64_t npieces = (int64_t)nchunks * 256;
+  for (int64_t q0 = 0; q0 < npieces; q0 += blockDim.x) {
+    const int64_t q = q0 + threadIdx.x;
+    int64_t a = 0, len = 0;
+    if (q < npieces) {
+      const int p = (int)(q / nchunks), k = (int)(q % nchunks);
+      a = (int64_t)starts[(int64_t)k * 257 + p];
+      len = (int64_t)starts[(int64_t)k * 257 + p + 1] - a;
+    }
+    const unsigned long long nt = (unsigned long long)((len + tile_rows - 1) / tile_rows);
+    unsigned long long x = nt;  // inclusive scan over the block
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) warp_tot[w] = x;
+    __syncthreads();
+    if (w == 0) {
+      unsigned long long v = lane < (int)(blockDim.x >> 5) ? warp_tot[lane] : 0ull;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += y;
+      }
+      if (lane < (int)(blockDim.x >> 5)) warp_tot[lane] = v;
+    }
+    __syncthreads();
+    unsigned long long first = carry + (w ? warp_tot[w - 1] : 0ull) + x - nt;
+    for (unsigned long long i = 0; i < nt; ++i) {
+      const int64_t r = a + (int64_t)i * tile_rows;
+      tiles[first + i] = make_longlong2(r, min(tile_rows, a + len - r));
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) carry += warp_tot[(blockDim.x >> 5) - 1];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *ntiles = carry;
+}
+
 // ---------------------------------------------------------------------------
 // Host side.
 // ---------------------------------------------------------------------------
@@ -190,11 +243,13 @@ int rule_strategy(const float* f, uint32_t ops, double hll) {
   const float log2n = f[F_LOG2N];
   if (coverage >= 0.97) return AGG_STRAT_SMEM;
   // with the column's HyperLogLog count: a hot head that shared tables absorb
-  // (the rest spilling to a right-sized table), or a flat column of up to 2^23
-  // keys (hash-partitioned shared tables); larger flat columns sort
+  // (the rest spilling to a right-sized table), or a flat column of up to 2^25
+  // keys (hash-partitioned shared tables); larger flat columns sort (on 2^30
+  // rows: 2^24 uniform keys 31 ms partitioned vs 43 ms sorted, 2^26 keys 59
+  // vs 45 ms)
   if (hll > 0.0) {
     if (hot_sample(f, cap) || hll <= cap) return AGG_STRAT_SMEM;
-    if (e.flat) return hll <= 8388608.0 ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
+    if (e.flat) return hll <= 33554432.0 ? AGG_STRAT_SMEM : AGG_STRAT_SORT;
   }
   if (log2n < 20.0f) return (e.plan <= cap || !e.flat) ? AGG_STRAT_SMEM : AGG_STRAT_GLOBAL;
   const double m = std::min(std::exp2((double)log2n), (double)kSketchSample);
@@ -391,7 +446,9 @@ class HashRun {
         }
         const int64_t tiles = (n + tile_rows - 1) / tile_rows;
         if (tiles < grid) grid = tiles;
-        void* args[] = {&a, &next_tile, &tile_rows};
+        const longlong2* no_tiles = nullptr;
+        const unsigned long long* no_count = nullptr;
+        void* args[] = {&a, &next_tile, &tile_rows, &no_tiles, &no_count};
         e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(threads), args, smem, s_);
       } else {
         KernelPtr bk = pick_build(vdt_, mm_, false, true, true, plan_.qpi);
@@ -409,6 +466,47 @@ class HashRun {
     cudaFreeAsync(tmp, s_);
     if (e != cudaSuccess) {
       set_error("partitioned build launch failed: %s", cudaGetErrorString(e));
+      return AGG_ERR_CUDA;
+    }
+    return AGG_OK;
+  }
+
+  // Build over a column hash-partitioned chunk by chunk (starts: nchunks x 257
+  // partition starts, device memory): a tile list in partition order, then the
+  // tile-queue build. tiles / ntiles: device scratch for the list.
+  agg_status build_pieces(const uint32_t* keys, const void* vals, int64_t n, const unsigned long long* starts,
+                          int nchunks, longlong2* tiles, unsigned long long* ntiles) {
+    if (n <= 0) return AGG_OK;
+    BuildArgs a;
+    a.keys = keys;
+    a.vals = vals;
+    a.n = n;
+    a.head = 0;
+    a.table = mem_;
+    a.mask = (uint32_t)(plan_.slots - 1);
+    a.gshift = 32 - (63 - __builtin_clzll((unsigned long long)plan_.slots));
+    a.smem_slots = plan_.smem_slots;
+    a.smem_cap = (plan_.smem_slots * 3) / 4;
+    a.status = status_;
+    a.progress = progress_;
+    int64_t tile_rows = plan_.tile_rows ? plan_.tile_rows : kPartTileRows / 2;
+    PhaseTimer pt(AGG_PHASE_BUILD, s_);
+    gb_piece_tiles<<<1, 1024, 0, s_>>>(starts, nchunks, tile_rows, tiles, ntiles);
+    note_launch();
+    unsigned long long* next_tile = (unsigned long long*)((char*)mem_ + status_off_ + 128);
+    AGG_CUDA_TRY(cudaMemsetAsync(next_tile, 0, 8, s_));
+    KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi);
+    const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
+    int bps = occupancy(bk, plan_.threads, smem);
+    if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
+    const int64_t grid = (int64_t)device_info().sm_count * bps;
+    const longlong2* tl = tiles;
+    const unsigned long long* nt = ntiles;
+    void* args[] = {&a, &next_tile, &tile_rows, &tl, &nt};
+    cudaError_t e = cudaLaunchKernel(bk, dim3((unsigned)grid), dim3(plan_.threads), args, smem, s_);
+    note_launch();
+    if (e != cudaSuccess) {
+      set_error("piecewise build launch failed: %s", cudaGetErrorString(e));
       return AGG_ERR_CUDA;
     }
     return AGG_OK;
@@ -887,22 +985,30 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
   };
   float feat[F_COUNT] = {0};
   bool have = false;
+  double hll0 = 0.0;  // distinct keys of the first chunk
+  const int64_t r0 = std::min<int64_t>(chunk, n);
   if (n > 0) {
     st = ensure_copied(GbPipe::kRing - 1);
     if (st != AGG_OK) return st;
     if (needs_sketch(o)) {
       cudaStreamWaitEvent(s, pipe->ready[0], 0);
-      const int64_t r0 = std::min<int64_t>(chunk, n);
       st = sketch_features(kbuf(0), r0, vdt, ops, o.sample_offset, s, feat);
       if (st != AGG_OK) return st;
       rescale_features(feat, r0, n, ops);
       have = true;
+      if (wants_hll(feat, n)) {
+        st = hll_estimate(kbuf(0), r0, s, &hll0);
+        if (st != AGG_OK) return st;
+      }
     }
   }
+  // The first chunk's count plans a column whose keys recur (far fewer distinct
+  // keys than rows in the chunk); one with a long tail keeps the sketch's plan.
+  const double hll_plan = hll0 > 0.0 && hll0 < 0.25 * (double)r0 ? hll0 : 0.0;
   Choice c;
   // the autotuner times candidates on a device column: give it the first chunk
   cudaStreamWaitEvent(s, pipe->ready[0], 0);
-  st = choose(kbuf(0), vbuf(0), std::min<int64_t>(chunk, n), vdt, ops, o, feat, have, 0.0, s, &c);
+  st = choose(kbuf(0), vbuf(0), r0, vdt, ops, o, feat, have, hll_plan, s, &c);
   if (st != AGG_OK) return st;
   agg_groups* g = nullptr;
   // The sort, and hash plans that partition the rows, work on the whole
@@ -912,12 +1018,78 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
   const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255);
   const size_t col_bytes = kb + (size_t)n * es + 256;
   bool whole = c.strategy == AGG_STRAT_SORT;
-  if (!whole && c.plan.partition && n > chunk) {
+  bool room = false;
+  if (c.plan.partition && n > chunk) {
     size_t free_b = 0, total_b = 0;
     const double table_b = (double)(c.plan.slots + 2) * gslot_bytes(ops_minmax(ops));
-    whole = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)free_b > 4.0 * col_bytes + 2.0 * table_b;
+    room = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)free_b > 4.0 * col_bytes + 2.0 * table_b;
   }
-  if (whole) {
+  // Streamed: a one-level hash partition of each chunk as it arrives
+  // (overlapped with the copies of the next chunks) into its own region of a
+  // column-sized buffer, a HyperLogLog count over every chunk, then one build
+  // over the pieces with the table sized from that count.
+  const bool streamed = room && hll_plan > 0.0 && c.strategy == AGG_STRAT_SMEM && c.plan.partition_passes == 1;
+  if (!whole && !streamed && c.plan.partition && n > chunk) whole = room;
+  if (streamed) {
+    const size_t starts_b = ((size_t)nchunks * 257 * 8 + 255) & ~size_t(255);
+    const int64_t max_tiles = (int64_t)nchunks * 256 + n / 4096 + 1;
+    const size_t tiles_b = ((size_t)max_tiles * 16 + 255) & ~size_t(255);
+    const size_t extra = starts_b + tiles_b + 256 + ((partition_tmp_bytes() + 255) & ~size_t(255)) + hll_state_bytes();
+    void* full = nullptr;
+    AGG_CUDA_TRY(dev_malloc_async(&full, col_bytes + extra, s));
+    Free full_free{full, s};
+    uint32_t* fk = (uint32_t*)full;
+    char* fv = (char*)full + kb;
+    char* x = (char*)full + ((col_bytes + 255) & ~size_t(255));
+    unsigned long long* starts = (unsigned long long*)x;
+    longlong2* tiles = (longlong2*)(x + starts_b);
+    unsigned long long* ntiles = (unsigned long long*)(x + starts_b + tiles_b);
+    void* ptmp = x + starts_b + tiles_b + 256;
+    uint32_t* regs = (uint32_t*)(x + starts_b + tiles_b + 256 + ((partition_tmp_bytes() + 255) & ~size_t(255)));
+    {
+      PhaseTimer pt(AGG_PHASE_SORT, s);
+      for (int64_t k = 0; k < nchunks; ++k) {
+        st = ensure_copied(k + GbPipe::kRing - 1);
+        if (st != AGG_OK) return st;
+        const int b = (int)(k % GbPipe::kRing);
+        cudaStreamWaitEvent(s, pipe->ready[b], 0);
+        const int64_t rows = std::min<int64_t>(chunk, n - k * chunk);
+        st = hll_add_chunk(kbuf(b), rows, regs, k == 0, s);
+        if (st == AGG_OK)
+          st = es == 4 ? partition_hashed<uint32_t>(kbuf(b), (const uint32_t*)vbuf(b), fk, (uint32_t*)fv, rows, ptmp,
+                                                    s, k * chunk, starts + k * 257)
+                       : partition_hashed<uint64_t>(kbuf(b), (const uint64_t*)vbuf(b), fk, (uint64_t*)fv, rows, ptmp,
+                                                    s, k * chunk, starts + k * 257);
+        cudaEventRecord(pipe->freed[b], s);
+        if (st != AGG_OK) return st;
+      }
+    }
+    double hll_all = 0.0;
+    st = hll_read(regs, s, &hll_all);
+    if (st != AGG_OK) return st;
+    HashPlan plan = c.plan;
+    plan.slots = o.table_slots ? o.table_slots : table_slots_for(feat, n, hll_all);
+    int retries = 0;
+    for (;;) {
+      uint64_t seen = 0, failed = 0;
+      {
+        HashRun run(vdt, ops, plan, s);
+        st = run.init();
+        if (st == AGG_OK) st = run.build_pieces(fk, fv, n, starts, (int)nchunks, tiles, ntiles);
+        if (st == AGG_OK) st = run.finish(&g);
+        seen = run.rows_seen();
+        failed = run.rows_failed();
+      }
+      if (st == AGG_OK) {
+        g->retries = retries;
+        break;
+      }
+      if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
+        return st;
+      ++retries;
+      plan.slots = regrow_slots(plan.slots, n, seen, failed);
+    }
+  } else if (whole) {
     void* full = nullptr;
     AGG_CUDA_TRY(dev_malloc_async(&full, col_bytes, s));
     Free full_free{full, s};

@@ -747,12 +747,15 @@ __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
 // Tile-queue build for hash-partitioned input: blocks pull 64 Ki-row tiles in
 // order from a counter, so all blocks work on neighbouring partitions and the
 // table region they update stays in L2; each tile clears its shared table
-// first and merges it into the global table at the end.
+// first and merges it into the global table at the end. With a tile list
+// (rows partitioned chunk by chunk), tile t is the row range tiles[t] =
+// (first row, rows), *ntiles of them, listed partition by partition.
 constexpr int64_t kPartTileRows = int64_t(1) << 16;
 
 template <int DT, bool MM, bool VEC, int QPI = 1>
 __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
-                                                        int64_t tile_rows) {
+                                                        int64_t tile_rows, const longlong2* tiles,
+                                                        const unsigned long long* ntiles) {
   using T = typename GV<DT>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int64_t s_t;
@@ -766,14 +769,23 @@ __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned l
     if (threadIdx.x == 0) s_t = *(volatile int*)a.status ? -1 : (int64_t)atomicAdd(next_tile, 1ull);
     __syncthreads();
     const int64_t t = s_t;
-    const int64_t r0 = t * tile_rows;
     __syncthreads();
-    if (t < 0 || r0 >= a.n) break;
+    int64_t r0, rows;
+    if (tiles) {
+      if (t < 0 || t >= (int64_t)*ntiles) break;
+      const longlong2 tl = tiles[t];
+      r0 = tl.x;
+      rows = tl.y;
+    } else {
+      r0 = t * tile_rows;
+      if (t < 0 || r0 >= a.n) break;
+      rows = min(tile_rows, a.n - r0);
+    }
     BuildArgs b = a;
     b.keys = a.keys + r0;
     b.vals = (const T*)a.vals + r0;
-    b.n = min(tile_rows, a.n - r0);
-    b.head = 0;
+    b.n = rows;
+    b.head = min((int64_t)((-r0) & 3), rows);  // rows before the next 16-byte boundary of the keys
     st.clear(a.smem_slots);
     __syncthreads();
     atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI>(b, st, threadIdx.x, blockDim.x));

@@ -113,13 +113,11 @@ __global__ void __launch_bounds__(kHllThreads) hll_kernel(const uint32_t* __rest
   }
 }
 
-agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est) {
-  *est = 0.0;
+size_t hll_state_bytes() { return (size_t)kHllM * 4 + 256; }
+
+agg_status hll_add_chunk(const uint32_t* keys, int64_t n, uint32_t* regs, bool first, cudaStream_t s) {
+  if (first) AGG_CUDA_TRY(cudaMemsetAsync(regs, 0, (size_t)kHllM * 4 + 24, s));  // registers, ticket, estimate
   if (n <= 0) return AGG_OK;
-  agg_status st = AGG_OK;
-  char* scr = (char*)stream_scratch(s, kHllScratchBytes, &st);
-  if (!scr) return st;
-  uint32_t* regs = (uint32_t*)(scr + kHllScratchOff);
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
@@ -136,19 +134,36 @@ agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double*
   int64_t grid = (int64_t)device_info().sm_count * bps;
   const int64_t need = ((n - head) / 4 + 2 * kHllThreads - 1) / (2 * kHllThreads);
   if (need < grid) grid = std::max<int64_t>(1, need);
-  AGG_CUDA_TRY(cudaMemsetAsync(regs, 0, (size_t)kHllM * 4 + 8, s));  // registers and ticket
+  if (!first) AGG_CUDA_TRY(cudaMemsetAsync(regs + kHllM, 0, 8, s));  // the ticket
   {
     PhaseTimer pt(AGG_PHASE_SKETCH, s);
     hll_kernel<<<(unsigned)grid, kHllThreads, kHllM * 4, s>>>(keys, n, head, regs);
     note_launch();
     AGG_CUDA_TRY(cudaGetLastError());
   }
+  return AGG_OK;
+}
+
+agg_status hll_read(const uint32_t* regs, cudaStream_t s, double* est) {
+  agg_status st = AGG_OK;
   double* hb = (double*)stream_pinned(s, 256, &st);
   if (!hb) return st;
   AGG_CUDA_TRY(cudaMemcpyAsync(hb, regs + kHllM + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
   AGG_CUDA_TRY(cudaStreamSynchronize(s));
   *est = hb[0];
   return AGG_OK;
+}
+
+agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est) {
+  *est = 0.0;
+  if (n <= 0) return AGG_OK;
+  agg_status st = AGG_OK;
+  char* scr = (char*)stream_scratch(s, kHllScratchBytes, &st);
+  if (!scr) return st;
+  uint32_t* regs = (uint32_t*)(scr + kHllScratchOff);
+  st = hll_add_chunk(keys, n, regs, true, s);
+  if (st != AGG_OK) return st;
+  return hll_read(regs, s, est);
 }
 
 }  // namespace agg

@@ -11,6 +11,7 @@
 //                  of the tile in shared memory in digit order, then coalesced
 //                  writes of each digit's run to its global offset.
 #include <algorithm>
+#include <vector>
 
 #include "sort.cuh"
 
@@ -381,8 +382,12 @@ constexpr int kFillStride = 32;  // global fill counters 256 B apart (different 
 __device__ __forceinline__ uint32_t part_digit(uint32_t key) { return fmix32(key) >> 24; }
 
 // fill[d * kFillStride]: partition starts (written by the last block), fill[256 * kFillStride]: ticket.
+// Starts count from row_base; with starts_out, they are also saved there (and
+// row_base + n at [256]).
 __global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __restrict__ keys, int64_t n,
-                                                              int64_t head, unsigned long long* __restrict__ fill) {
+                                                              int64_t head, unsigned long long* __restrict__ fill,
+                                                              int64_t row_base,
+                                                              unsigned long long* __restrict__ starts_out) {
   constexpr int kWarps = kPartHistThreads / 32;
   __shared__ uint32_t h[kWarps][256];
   __shared__ unsigned long long tot[256];
@@ -436,9 +441,12 @@ __global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __
         const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
         if (lane >= o) x += y;
       }
-      fill[(j * 32 + lane) * kFillStride] = run + x - tot[j * 32 + lane];
+      const unsigned long long start = (unsigned long long)row_base + run + x - tot[j * 32 + lane];
+      fill[(j * 32 + lane) * kFillStride] = start;
+      if (starts_out) starts_out[j * 32 + lane] = start;
       run += __shfl_sync(0xffffffffu, x, 31);
     }
+    if (starts_out && lane == 0) starts_out[256] = (unsigned long long)row_base + run;
   }
 }
 
@@ -536,8 +544,15 @@ size_t partition_tmp_bytes() { return (257 * kFillStride) * sizeof(unsigned long
 
 template <class P>
 agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                            cudaStream_t s) {
-  if (n <= 0) return AGG_OK;
+                            cudaStream_t s, int64_t row_base, unsigned long long* starts_out) {
+  if (n <= 0) {
+    if (starts_out) {
+      std::vector<unsigned long long> st(257, (unsigned long long)row_base);
+      AGG_CUDA_TRY(cudaMemcpyAsync(starts_out, st.data(), sizeof(unsigned long long) * 257, cudaMemcpyHostToDevice, s));
+      AGG_CUDA_TRY(cudaStreamSynchronize(s));  // the host vector goes out of scope
+    }
+    return AGG_OK;
+  }
   int dev = 0;
   cudaGetDevice(&dev);
   static bool attr[64] = {};
@@ -564,7 +579,7 @@ agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P
   const int64_t gh = std::max<int64_t>(
       1, std::min<int64_t>((int64_t)di.sm_count * bh, ((n - head) / 4 + 2 * kPartHistThreads - 1) / (2 * kPartHistThreads)));
   const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, ntiles));
-  part_hist<<<(unsigned)gh, kPartHistThreads, 0, s>>>(kin, n, head, fill);
+  part_hist<<<(unsigned)gh, kPartHistThreads, 0, s>>>(kin, n, head, fill, row_base, starts_out);
   part_scatter<P><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kin, vin, kout, vout, n, fill);
   note_launch(2);
   AGG_CUDA_TRY(cudaGetLastError());
@@ -572,9 +587,9 @@ agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P
 }
 
 template agg_status partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t, void*,
-                                               cudaStream_t);
+                                               cudaStream_t, int64_t, unsigned long long*);
 template agg_status partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t, void*,
-                                               cudaStream_t);
+                                               cudaStream_t, int64_t, unsigned long long*);
 
 template agg_status radix_partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t,
                                                      void*, cudaStream_t, int);

@@ -41,11 +41,14 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
 
 // One-level hash partition by the top 8 bits of fmix32(key), in no particular
 // order within a partition (rows of one partition are contiguous, partitions
-// in ascending digit order). tmp must hold partition_tmp_bytes() bytes.
+// in ascending digit order). The rows land at kout[row_base, row_base + n)
+// (likewise vout); with starts_out, the 256 partition starts and the end
+// (row_base + n) are written there (device memory, 257 values). tmp must hold
+// partition_tmp_bytes() bytes.
 size_t partition_tmp_bytes();
 template <class P>
 agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                            cudaStream_t s);
+                            cudaStream_t s, int64_t row_base = 0, unsigned long long* starts_out = nullptr);
 
 // Set the kernel attributes the sort needs (call before a stream capture).
 agg_status radix_prepare();
