@@ -383,10 +383,10 @@ class Table2p30Workload:
 WORKLOADS = {"table2p30": Table2p30Workload, "groupby": GroupbyWorkload, "scan": ScanWorkload}
 
 # phase of the library's event timers -> the kernels it times
-PHASE_KERNELS = {"scan": "reduce_scan", "sketch": "sketch_gather + sketch_kernel",
-                 "build": "gb_build / gb_build_tiles (hash build)",
+PHASE_KERNELS = {"scan": "reduce_scan", "sketch": "sketch_gather + sketch_kernel + hll_kernel",
+                 "build": "gb_build_tiles (hash build over partitioned tiles) or gb_build",
                  "finalize": "gb_compact + key sort + gb_gather (finalise)",
-                 "sort": "radix_hist + radix_scatter (radix partition or sort pass)",
+                 "sort": "part_hist + part_scatter (one-level partition) or radix_hist + radix_scatter",
                  "segreduce": "seg_reduce + seg_finalize", "batch": "batch_build", "mlp": "mlp kernels"}
 
 
@@ -872,7 +872,8 @@ def run_ours(args):
             "config": W.config(),
             "rows_per_s": world * W.n * args.steps / (ms * 1e-3),
             "roofline": {"bound": "hbm", "achieved": round(achieved, 2), "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                         "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": kernel_traffic(kernel, W.name),
+                         "frac": round(achieved / peaks["hbm_gbs"], 4),
+                         "traffic": kernel_traffic(W.kernel or phase, W.name),
                          "kernel": kernel, "phase": phase, "strategy": strategy,
                          "ms_per_launch": round(per_launch_ms, 4),
                          "achieved_how": "input bytes of the step / mean CUDA-event time of the phase per launch",

@@ -98,15 +98,24 @@ constexpr int kFixGuard = 47;
 
 struct Fix128 {
   uint64_t lo, hi;
+  uint32_t nneg;  // negative rows added on the fast path as ~v, each still owing +1
   int E;
   double special;
   __device__ void init() {
     lo = 0;
     hi = 0;
+    nneg = 0;
     E = 0;
     special = 0.0;
   }
+  // -v = ~v + 1: the fast path adds ~v and counts the +1s, added here.
+  __device__ __forceinline__ void fold_neg() {
+    lo += nneg;
+    hi += lo < nneg ? 1ull : 0ull;
+    nneg = 0;
+  }
   __device__ __forceinline__ void rescale(int e) {  // e > E
+    fold_neg();
     const int k = e - E;
     if (k >= 127) {
       lo = (int64_t)hi < 0 ? ~0ull : 0ull;
@@ -122,6 +131,21 @@ struct Fix128 {
   }
   __device__ __forceinline__ void add(uint64_t u) {
     const int ef = (int)(u >> 52) & 0x7FF;
+    const int d0 = E - ef;
+    if ((unsigned)d0 <= (unsigned)kFixGuard && ef != 0) {
+      // fast path: a normal value within kFixGuard binades of E. Its significand
+      // shifted into place, in one's complement when negative (the +1 counted
+      // in nneg), is added with one carry chain.
+      const uint64_t m = (u & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+      const int sh = kFixGuard - d0;  // 0 .. kFixGuard
+      const uint64_t vlo = m << sh;
+      const uint64_t vhi = (m >> 1) >> (63 - sh);  // m >> (64 - sh), 0 when sh = 0
+      const uint64_t sgn = (uint64_t)((int64_t)u >> 63);
+      asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(vlo ^ sgn), "l"(vhi ^ sgn));
+      nneg += (uint32_t)sgn & 1u;
+      return;
+    }
+    fold_neg();
     if (ef == 0x7FF) {  // infinity or NaN
       special += __longlong_as_double((long long)u);
       return;
@@ -221,8 +245,10 @@ struct Acc<DT, SUM, MM, true> {
     p.si = 0;
     p.eb = 0.0;
     if (F64 && SUM) {
-      fx.to_pair(p.hi, p.lo);
-      p.eb = fx.error_bound(rows, p.hi, p.lo);
+      Fix128 f = fx;
+      f.fold_neg();
+      f.to_pair(p.hi, p.lo);
+      p.eb = f.error_bound(rows, p.hi, p.lo);
     } else {
       p.hi = (double)s;
       p.lo = (double)c;
