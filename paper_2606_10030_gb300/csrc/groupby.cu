@@ -305,6 +305,9 @@ struct HashPlan {
   bool multi_keys = true;  // per-warp reduction of several frequent keys (see build_rows)
   int qpi = 1;             // quads (4 rows) a thread folds per iteration: items per thread / 4
   int64_t tile_rows = 0;   // rows per tile of the partitioned build (0: from the column)
+  // Rows of each one-level partition of the column (host memory, counted by
+  // the HyperLogLog pass), or null: the partition then counts them itself.
+  const unsigned long long* part_hist = nullptr;
 };
 
 // One hash aggregation: a zeroed global table, any number of build launches
@@ -392,7 +395,7 @@ class HashRun {
     const size_t kb = ((size_t)n * 4 + 255) & ~size_t(255), vb = ((size_t)n * es + 255) & ~size_t(255);
     const int passes = plan_.partition_passes;
     void* tmp = nullptr;
-    AGG_CUDA_TRY(dev_malloc_async(&tmp, passes * (kb + vb) + std::max(radix_tmp_bytes(n), partition_tmp_bytes()), s_));
+    AGG_CUDA_TRY(dev_malloc_async(&tmp, passes * (kb + vb) + partition2_tmp_bytes(), s_));
     uint32_t* kp = (uint32_t*)tmp;
     char* vp = (char*)tmp + kb;
     uint32_t* kq = (uint32_t*)((char*)tmp + kb + vb);
@@ -402,14 +405,15 @@ class HashRun {
     {
       PhaseTimer pt(AGG_PHASE_SORT, s_);
       if (passes == 1) {  // rows only need grouping by partition: no stable order
-        st = es == 4 ? partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_)
-                     : partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_);
-      } else {  // by bits 16..23, then stably by bits 24..31: ordered by the top 16 bits
-        st = es == 4 ? radix_partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kq, (uint32_t*)vq, n, rt, s_, 16)
-                     : radix_partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kq, (uint64_t*)vq, n, rt, s_, 16);
-        if (st == AGG_OK)
-          st = es == 4 ? radix_partition_hashed<uint32_t>(kq, (const uint32_t*)vq, kp, (uint32_t*)vp, n, rt, s_, 24)
-                       : radix_partition_hashed<uint64_t>(kq, (const uint64_t*)vq, kp, (uint64_t*)vp, n, rt, s_, 24);
+        st = es == 4 ? partition_hashed<uint32_t>(a.keys, (const uint32_t*)a.vals, kp, (uint32_t*)vp, n, rt, s_, 0,
+                                                  nullptr, plan_.part_hist)
+                     : partition_hashed<uint64_t>(a.keys, (const uint64_t*)a.vals, kp, (uint64_t*)vp, n, rt, s_, 0,
+                                                  nullptr, plan_.part_hist);
+      } else {  // by the top 8 bits, then each partition by bits 16..23: ordered by the top 16 bits
+        st = es == 4 ? partition_hashed2<uint32_t>(a.keys, (const uint32_t*)a.vals, kq, (uint32_t*)vq, kp,
+                                                   (uint32_t*)vp, n, rt, s_, plan_.part_hist)
+                     : partition_hashed2<uint64_t>(a.keys, (const uint64_t*)a.vals, kq, (uint64_t*)vq, kp,
+                                                   (uint64_t*)vp, n, rt, s_, plan_.part_hist);
       }
     }
     if (st != AGG_OK) {
@@ -814,6 +818,8 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
   float feat[F_COUNT] = {0};
   bool have = false;
   double hll = 0.0;
+  unsigned long long part_counts[256];  // rows per one-level partition, from the HyperLogLog pass
+  bool have_counts = false;
   agg_status st = AGG_OK;
   if (known_feat && n > 0) {
     std::memcpy(feat, known_feat, sizeof(feat));
@@ -826,14 +832,16 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
       if (st != AGG_OK) return st;
       have = true;
       if (wants_hll(feat, n)) {
-        st = hll_estimate(keys, n, s, &hll);
+        st = hll_estimate(keys, n, s, &hll, part_counts);
         if (st != AGG_OK) return st;
+        have_counts = true;
       }
       agg_options o2 = o;
       o2.strategy = learned >= 0 ? learned : rule_strategy(feat, ops, hll);
       Choice c;
       st = choose(keys, vals, n, vdt, ops, o2, feat, have, hll, s, &c);
       if (st != AGG_OK) return st;
+      if (have_counts) c.plan.part_hist = part_counts;
       agg_groups* g = nullptr;
       if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g, feat);
       else st = hash_device(keys, vals, n, vdt, ops, c.plan, s, &g);
@@ -846,13 +854,15 @@ agg_status groupby_with(const uint32_t* keys, const void* vals, int64_t n, int v
     if (st != AGG_OK) return st;
     have = true;
     if (wants_hll(feat, n)) {
-      st = hll_estimate(keys, n, s, &hll);
+      st = hll_estimate(keys, n, s, &hll, part_counts);
       if (st != AGG_OK) return st;
+      have_counts = true;
     }
   }
   Choice c;
   st = choose(keys, vals, n, vdt, ops, o, feat, have, hll, s, &c);
   if (st != AGG_OK) return st;
+  if (have_counts) c.plan.part_hist = part_counts;
   agg_groups* g = nullptr;
   if (c.strategy == AGG_STRAT_SORT) st = sort_groupby(keys, vals, n, vdt, ops, s, &g, have ? feat : nullptr);
   else st = hash_device(keys, vals, n, vdt, ops, c.plan, s, &g);

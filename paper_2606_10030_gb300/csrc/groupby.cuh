@@ -38,14 +38,19 @@ inline bool ops_minmax(uint32_t ops) { return ops & (AGG_MIN | AGG_MAX); }
 int rule_strategy(const float* feat, uint32_t ops, double hll = 0.0);
 
 // HyperLogLog estimate of the distinct keys of a device key column (one pass
-// over the keys, one read-back).
-agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est);
+// over the keys, one read-back). With hist (host, 256 values), the same pass
+// also counts the rows of each one-level hash partition (partition_hashed's
+// digit), read back with the estimate.
+agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est,
+                        unsigned long long* hist = nullptr);
 // HyperLogLog over a column that arrives in chunks: registers (hll_state_bytes()
 // of device memory) cleared by the first chunk, the estimate over all chunks
-// added so far read back by hll_read (one sync).
+// added so far read back by hll_read (one sync); hist as for hll_estimate (the
+// counts of every chunk added with hist = true).
 size_t hll_state_bytes();
-agg_status hll_add_chunk(const uint32_t* keys, int64_t n, uint32_t* regs, bool first, cudaStream_t s);
-agg_status hll_read(const uint32_t* regs, cudaStream_t s, double* est);
+agg_status hll_add_chunk(const uint32_t* keys, int64_t n, uint32_t* regs, bool first, cudaStream_t s,
+                         bool hist = false);
+agg_status hll_read(const uint32_t* regs, cudaStream_t s, double* est, unsigned long long* hist = nullptr);
 // Whether planning a GROUP BY of n rows with this sketch takes a HyperLogLog
 // count first: a large column whose sample does not cover its keys.
 bool wants_hll(const float* feat, int64_t n);

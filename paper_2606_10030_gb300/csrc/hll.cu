@@ -14,7 +14,13 @@
 // when V registers are zero; above 2^32/30, the correction for a 32-bit hash
 // space). The registers and the ticket live in the
 // stream's scratch and are cleared before every launch.
+//
+// The same pass can also count the rows of each of the 256 hash partitions
+// that the one-level partition of the GROUP BY uses (the top 8 bits of the
+// same hash), so that the partition does not read the keys once more for its
+// histogram.
 #include <cmath>
+#include <cstring>
 
 #include "groupby.cuh"
 
@@ -24,51 +30,68 @@ constexpr int kHllP = 14;
 constexpr int kHllM = 1 << kHllP;
 constexpr int kHllThreads = 512;
 constexpr size_t kHllScratchOff = 8192;  // in the stream scratch, past the scan ticket
-constexpr size_t kHllScratchBytes = kHllScratchOff + (size_t)kHllM * 4 + 256;
+// State: registers (kHllM x u32), ticket (+0 past them), estimate (+8, double),
+// partition counts (+256, 256 x u64).
+constexpr size_t kHllTicketOff = (size_t)kHllM * 4;
+constexpr size_t kHllEstOff = kHllTicketOff + 8;
+constexpr size_t kHllHistOff = kHllTicketOff + 256;
+constexpr size_t kHllStateBytes = kHllHistOff + 256 * 8;
+constexpr size_t kHllScratchBytes = kHllScratchOff + kHllStateBytes;
+constexpr int kHllWarps = kHllThreads / 32;
 
-__device__ __forceinline__ void hll_add(uint32_t* sreg, uint32_t key) {
+// whist: the warp's 256 partition counters (HIST only).
+template <bool HIST>
+__device__ __forceinline__ void hll_add(uint32_t* sreg, uint32_t* whist, uint32_t key) {
   const uint32_t h = fmix32(key);
   const uint32_t idx = h >> (32 - kHllP);
   const uint32_t rank = (uint32_t)__clz((int)((h << kHllP) | (1u << (kHllP - 1)))) + 1u;  // 1..19
   if (rank > *(volatile uint32_t*)&sreg[idx]) atomicMax(&sreg[idx], rank);
+  if (HIST) atomicAdd(&whist[h >> 24], 1u);
 }
 
-// regs[kHllM], then the ticket (+kHllM * 4) and the estimate (+kHllM * 4 + 8, double).
+template <bool HIST>
 __global__ void __launch_bounds__(kHllThreads) hll_kernel(const uint32_t* __restrict__ keys, int64_t n, int64_t head,
                                                           uint32_t* __restrict__ regs) {
-  extern __shared__ uint32_t sreg[];
+  extern __shared__ uint32_t sreg[];  // kHllM registers, then (HIST) kHllWarps x 256 counters
   __shared__ double red[33];
   __shared__ int s_last;
-  unsigned* ticket = regs + kHllM;
-  double* est = (double*)(regs + kHllM + 2);
-  for (int i = threadIdx.x; i < kHllM; i += blockDim.x) sreg[i] = 0;
+  unsigned* ticket = (unsigned*)((char*)regs + kHllTicketOff);
+  double* est = (double*)((char*)regs + kHllEstOff);
+  uint32_t* whist = sreg + kHllM + (threadIdx.x >> 5) * 256;
+  for (int i = threadIdx.x; i < kHllM + (HIST ? kHllWarps * 256 : 0); i += blockDim.x) sreg[i] = 0;
   __syncthreads();
   const int64_t g = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
   const int64_t nq = (n - head) / 4;
   const int64_t tail0 = head + nq * 4;
-  if (g < head) hll_add(sreg, keys[g]);
-  if (g < n - tail0) hll_add(sreg, keys[tail0 + g]);
+  if (g < head) hll_add<HIST>(sreg, whist, keys[g]);
+  if (g < n - tail0) hll_add<HIST>(sreg, whist, keys[tail0 + g]);
   const uint4* kq = (const uint4*)(keys + head);
   for (int64_t q = g; q < nq; q += 2 * nthreads) {
     const uint4 a = ld_stream_v4(kq + q);
     const bool two = q + nthreads < nq;
     const uint4 b = two ? ld_stream_v4(kq + q + nthreads) : make_uint4(0, 0, 0, 0);
-    hll_add(sreg, a.x);
-    hll_add(sreg, a.y);
-    hll_add(sreg, a.z);
-    hll_add(sreg, a.w);
+    hll_add<HIST>(sreg, whist, a.x);
+    hll_add<HIST>(sreg, whist, a.y);
+    hll_add<HIST>(sreg, whist, a.z);
+    hll_add<HIST>(sreg, whist, a.w);
     if (two) {
-      hll_add(sreg, b.x);
-      hll_add(sreg, b.y);
-      hll_add(sreg, b.z);
-      hll_add(sreg, b.w);
+      hll_add<HIST>(sreg, whist, b.x);
+      hll_add<HIST>(sreg, whist, b.y);
+      hll_add<HIST>(sreg, whist, b.z);
+      hll_add<HIST>(sreg, whist, b.w);
     }
   }
   __syncthreads();
   for (int i = threadIdx.x; i < kHllM; i += blockDim.x) {
     const uint32_t r = sreg[i];
     if (r != 0 && r > __ldcg(&regs[i])) atomicMax(&regs[i], r);
+  }
+  if (HIST && threadIdx.x < 256) {
+    unsigned long long* hist = (unsigned long long*)((char*)regs + kHllHistOff);
+    uint32_t t = 0;
+    for (int w = 0; w < kHllWarps; ++w) t += sreg[kHllM + w * 256 + threadIdx.x];
+    if (t) atomicAdd(&hist[threadIdx.x], (unsigned long long)t);
   }
   __threadfence();
   __syncthreads();
@@ -113,57 +136,63 @@ __global__ void __launch_bounds__(kHllThreads) hll_kernel(const uint32_t* __rest
   }
 }
 
-size_t hll_state_bytes() { return (size_t)kHllM * 4 + 256; }
+size_t hll_state_bytes() { return kHllStateBytes; }
 
-agg_status hll_add_chunk(const uint32_t* keys, int64_t n, uint32_t* regs, bool first, cudaStream_t s) {
-  if (first) AGG_CUDA_TRY(cudaMemsetAsync(regs, 0, (size_t)kHllM * 4 + 24, s));  // registers, ticket, estimate
+agg_status hll_add_chunk(const uint32_t* keys, int64_t n, uint32_t* regs, bool first, cudaStream_t s, bool hist) {
+  if (first) AGG_CUDA_TRY(cudaMemsetAsync(regs, 0, kHllStateBytes, s));  // registers, ticket, estimate, counts
   if (n <= 0) return AGG_OK;
   static bool attr_set[64] = {};
   int dev = 0;
   cudaGetDevice(&dev);
+  const int smem0 = kHllM * 4, smem1 = (kHllM + kHllWarps * 256) * 4;
   if (dev < 64 && !attr_set[dev]) {
-    AGG_CUDA_TRY(cudaFuncSetAttribute(hll_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kHllM * 4));
+    AGG_CUDA_TRY(cudaFuncSetAttribute(hll_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem0));
+    AGG_CUDA_TRY(cudaFuncSetAttribute(hll_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem1));
     attr_set[dev] = true;
   }
+  const void* kern = hist ? (const void*)hll_kernel<true> : (const void*)hll_kernel<false>;
+  const int smem = hist ? smem1 : smem0;
   int64_t head = (int64_t)(((16 - ((uintptr_t)keys & 15)) & 15) / 4);
   if (head > n) head = n;
   int bps = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, hll_kernel, kHllThreads, kHllM * 4) != cudaSuccess ||
-      bps < 1)
-    bps = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kHllThreads, smem) != cudaSuccess || bps < 1) bps = 1;
   int64_t grid = (int64_t)device_info().sm_count * bps;
   const int64_t need = ((n - head) / 4 + 2 * kHllThreads - 1) / (2 * kHllThreads);
   if (need < grid) grid = std::max<int64_t>(1, need);
-  if (!first) AGG_CUDA_TRY(cudaMemsetAsync(regs + kHllM, 0, 8, s));  // the ticket
+  if (!first) AGG_CUDA_TRY(cudaMemsetAsync((char*)regs + kHllTicketOff, 0, 8, s));  // the ticket
   {
     PhaseTimer pt(AGG_PHASE_SKETCH, s);
-    hll_kernel<<<(unsigned)grid, kHllThreads, kHllM * 4, s>>>(keys, n, head, regs);
+    if (hist) hll_kernel<true><<<(unsigned)grid, kHllThreads, smem, s>>>(keys, n, head, regs);
+    else hll_kernel<false><<<(unsigned)grid, kHllThreads, smem, s>>>(keys, n, head, regs);
     note_launch();
     AGG_CUDA_TRY(cudaGetLastError());
   }
   return AGG_OK;
 }
 
-agg_status hll_read(const uint32_t* regs, cudaStream_t s, double* est) {
+agg_status hll_read(const uint32_t* regs, cudaStream_t s, double* est, unsigned long long* hist) {
   agg_status st = AGG_OK;
-  double* hb = (double*)stream_pinned(s, 256, &st);
+  constexpr size_t kBytes = kHllStateBytes - kHllEstOff;  // the estimate through the counts
+  char* hb = (char*)stream_pinned(s, kBytes, &st);
   if (!hb) return st;
-  AGG_CUDA_TRY(cudaMemcpyAsync(hb, regs + kHllM + 2, sizeof(double), cudaMemcpyDeviceToHost, s));
+  AGG_CUDA_TRY(cudaMemcpyAsync(hb, (const char*)regs + kHllEstOff, hist ? kBytes : sizeof(double),
+                               cudaMemcpyDeviceToHost, s));
   AGG_CUDA_TRY(cudaStreamSynchronize(s));
-  *est = hb[0];
+  std::memcpy(est, hb, sizeof(double));
+  if (hist) std::memcpy(hist, hb + (kHllHistOff - kHllEstOff), 256 * sizeof(unsigned long long));
   return AGG_OK;
 }
 
-agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est) {
+agg_status hll_estimate(const uint32_t* keys, int64_t n, cudaStream_t s, double* est, unsigned long long* hist) {
   *est = 0.0;
   if (n <= 0) return AGG_OK;
   agg_status st = AGG_OK;
   char* scr = (char*)stream_scratch(s, kHllScratchBytes, &st);
   if (!scr) return st;
   uint32_t* regs = (uint32_t*)(scr + kHllScratchOff);
-  st = hll_add_chunk(keys, n, regs, true, s);
+  st = hll_add_chunk(keys, n, regs, true, s, hist != nullptr);
   if (st != AGG_OK) return st;
-  return hll_read(regs, s, est);
+  return hll_read(regs, s, est, hist);
 }
 
 }  // namespace agg

@@ -133,14 +133,11 @@ __device__ __forceinline__ int64_t rows_of(int64_t n_cap, const int64_t* n_dev) 
 }
 
 // Digit of a key: 8 bits of key - kbase (kbase <= every key, so the order is
-// the keys' order), or (HASHED) of the key's MurmurHash3 fmix32 image, which
-// spreads any key distribution evenly over the digits.
-template <bool HASHED>
+// the keys' order).
 __device__ __forceinline__ uint32_t digit_of(uint32_t key, int shift, uint32_t kbase) {
-  return ((HASHED ? fmix32(key) : key - kbase) >> shift) & 0xFFu;
+  return ((key - kbase) >> shift) & 0xFFu;
 }
 
-template <bool HASHED>
 __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __restrict__ keys, int64_t n_cap,
                                                            const int64_t* n_dev, int shift, uint32_t kbase,
                                                            int64_t ntiles, uint32_t* __restrict__ counts) {
@@ -158,7 +155,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
 #pragma unroll
   for (int i = 0; i < kSortItems; ++i) {
     const int64_t j = base + (int64_t)i * kSortThreads + threadIdx.x;
-    if (j < n) atomicAdd(&h[digit_of<HASHED>(k[i], shift, kbase)], 1u);
+    if (j < n) atomicAdd(&h[digit_of(k[i], shift, kbase)], 1u);
   }
   __syncthreads();
   if (threadIdx.x < 256) counts[(int64_t)threadIdx.x * ntiles + blockIdx.x] = h[threadIdx.x];
@@ -175,7 +172,7 @@ __global__ void __launch_bounds__(kSortThreads) radix_hist(const uint32_t* __res
 // 3. values are loaded (keys are in registers) and rows staged in shared
 //    memory in digit order;
 // 4. each digit's run is written to its global offset with coalesced stores.
-template <class P, bool HASHED>
+template <class P>
 __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t* __restrict__ keys,
                                                               const P* __restrict__ vals, uint32_t* __restrict__ okeys,
                                                               P* __restrict__ ovals, int64_t n_cap,
@@ -211,7 +208,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t*
   for (int r = 0; r < kSortItems; ++r) {
     const int64_t j = wbase + r * 32 + lane;
     const bool ok = j < n;
-    const uint32_t d = ok ? digit_of<HASHED>(kr[r], shift, kbase) : 0u;
+    const uint32_t d = ok ? digit_of(kr[r], shift, kbase) : 0u;
     // lanes holding the same digit: one ballot per digit bit
     uint32_t peers = __ballot_sync(0xffffffffu, ok);
 #pragma unroll
@@ -254,7 +251,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t*
     const int64_t j = wbase + r * 32 + lane;
     if (j < n) {
       const uint32_t key = kr[r];
-      const uint32_t d = digit_of<HASHED>(key, shift, kbase);
+      const uint32_t d = digit_of(key, shift, kbase);
       const uint32_t lp = whist[w * 256 + d] + lr[r];
       stage_k[lp] = key;
       stage_v[lp] = vals[j];
@@ -264,7 +261,7 @@ __global__ void __launch_bounds__(kSortThreads, 3) radix_scatter(const uint32_t*
   const int cnt = (int)(n - tile0 < kSortTile ? n - tile0 : kSortTile);
   for (int i = threadIdx.x; i < cnt; i += kSortThreads) {
     const uint32_t key = stage_k[i];
-    const uint32_t d = digit_of<HASHED>(key, shift, kbase);
+    const uint32_t d = digit_of(key, shift, kbase);
     const int64_t pos = (int64_t)(uint32_t)(gbase[d] + (uint32_t)i);
     okeys[pos] = key;
     ovals[pos] = stage_v[i];
@@ -303,10 +300,10 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
   for (int shift = 0; shift < bits; shift += 8, ++pass) {
     uint32_t* ko = (pass & 1) ? kb : ka;
     P* vo = (pass & 1) ? vb : va;
-    radix_hist<false><<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, kbase, ntiles, counts);
+    radix_hist<<<(unsigned)ntiles, kSortThreads, 0, s>>>(ki, n_cap, n_dev, shift, kbase, ntiles, counts);
     agg_status st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
     if (st != AGG_OK) return st;
-    radix_scatter<P, false><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, kbase,
+    radix_scatter<P><<<(unsigned)ntiles, kSortThreads, sm, s>>>(ki, vi, ko, vo, n_cap, n_dev, shift, kbase,
                                                                         ntiles, counts);
     note_launch(2);
     AGG_CUDA_TRY(cudaGetLastError());
@@ -323,35 +320,11 @@ agg_status radix_prepare() {
   cudaGetDevice(&dev);
   static bool done[64] = {};
   if (dev < 64 && done[dev]) return AGG_OK;
-  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)scatter_smem<uint32_t>()));
-  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)scatter_smem<uint64_t>()));
-  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    (int)scatter_smem<uint32_t>()));
-  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  AGG_CUDA_TRY(cudaFuncSetAttribute(radix_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                     (int)scatter_smem<uint64_t>()));
   if (dev < 64) done[dev] = true;
-  return AGG_OK;
-}
-
-template <class P>
-agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                                  cudaStream_t s, int shift) {
-  const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-  if (ntiles == 0) return AGG_OK;
-  agg_status st = radix_prepare();
-  if (st != AGG_OK) return st;
-  uint32_t* counts = (uint32_t*)tmp;
-  const size_t cbytes = ((size_t)256 * ntiles * sizeof(uint32_t) + 255) & ~size_t(255);
-  void* stmp = (char*)tmp + cbytes;
-  radix_hist<true><<<(unsigned)ntiles, kSortThreads, 0, s>>>(kin, n, nullptr, shift, 0u, ntiles, counts);
-  st = scan_exclusive_u32(counts, counts, 256 * ntiles, nullptr, stmp, s);
-  if (st != AGG_OK) return st;
-  radix_scatter<P, true><<<(unsigned)ntiles, kSortThreads, scatter_smem<P>(), s>>>(kin, vin, kout, vout, n, nullptr,
-                                                                                    shift, 0u, ntiles, counts);
-  note_launch(2);
-  AGG_CUDA_TRY(cudaGetLastError());
   return AGG_OK;
 }
 
@@ -372,14 +345,20 @@ agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* k
 //                 rows staged in shared memory in digit order and written out
 //                 run by run.
 // Reads 4 + 12 B and writes 12 B per row (uint32 key, 8-byte value); no per-tile
-// count array and no ranking rounds.
+// count array and no ranking rounds. The histogram pass is skipped when the
+// caller already holds the counts (the GROUP BY planner's HyperLogLog pass
+// counts them from the same hash).
+//
+// A second level (65536 partitions) splits each of the 256 partitions by the
+// next 8 hash bits with the same scatter over tiles that never straddle a
+// partition (seg_hist counts per (partition, digit), seg_starts scans them).
 // ---------------------------------------------------------------------------
 constexpr int kPartHistThreads = 512;
 constexpr int kPartThreads = 512;
 constexpr int kPartTile = 4096;
 constexpr int kFillStride = 32;  // global fill counters 256 B apart (different L2 lines)
 
-__device__ __forceinline__ uint32_t part_digit(uint32_t key) { return fmix32(key) >> 24; }
+__device__ __forceinline__ uint32_t part_digit(uint32_t key, int shift) { return (fmix32(key) >> shift) & 255u; }
 
 // fill[d * kFillStride]: partition starts (written by the last block), fill[256 * kFillStride]: ticket.
 // Starts count from row_base; with starts_out, they are also saved there (and
@@ -387,7 +366,7 @@ __device__ __forceinline__ uint32_t part_digit(uint32_t key) { return fmix32(key
 __global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __restrict__ keys, int64_t n,
                                                               int64_t head, unsigned long long* __restrict__ fill,
                                                               int64_t row_base,
-                                                              unsigned long long* __restrict__ starts_out) {
+                                                              unsigned long long* __restrict__ starts_out, int shift) {
   constexpr int kWarps = kPartHistThreads / 32;
   __shared__ uint32_t h[kWarps][256];
   __shared__ unsigned long long tot[256];
@@ -399,22 +378,22 @@ __global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __
   const int64_t nthreads = (int64_t)gridDim.x * kPartHistThreads;
   const int64_t nq = (n - head) / 4;
   const int64_t tail0 = head + nq * 4;
-  if (g < head) atomicAdd(&h[w][part_digit(keys[g])], 1u);
-  if (g < n - tail0) atomicAdd(&h[w][part_digit(keys[tail0 + g])], 1u);
+  if (g < head) atomicAdd(&h[w][part_digit(keys[g], shift)], 1u);
+  if (g < n - tail0) atomicAdd(&h[w][part_digit(keys[tail0 + g], shift)], 1u);
   const uint4* kq = (const uint4*)(keys + head);
   for (int64_t q = g; q < nq; q += 2 * nthreads) {  // two 16-byte loads in flight per thread
     const uint4 a = ld_stream_v4(kq + q);
     const bool two = q + nthreads < nq;
     const uint4 b = two ? ld_stream_v4(kq + q + nthreads) : make_uint4(0, 0, 0, 0);
-    atomicAdd(&h[w][part_digit(a.x)], 1u);
-    atomicAdd(&h[w][part_digit(a.y)], 1u);
-    atomicAdd(&h[w][part_digit(a.z)], 1u);
-    atomicAdd(&h[w][part_digit(a.w)], 1u);
+    atomicAdd(&h[w][part_digit(a.x, shift)], 1u);
+    atomicAdd(&h[w][part_digit(a.y, shift)], 1u);
+    atomicAdd(&h[w][part_digit(a.z, shift)], 1u);
+    atomicAdd(&h[w][part_digit(a.w, shift)], 1u);
     if (two) {
-      atomicAdd(&h[w][part_digit(b.x)], 1u);
-      atomicAdd(&h[w][part_digit(b.y)], 1u);
-      atomicAdd(&h[w][part_digit(b.z)], 1u);
-      atomicAdd(&h[w][part_digit(b.w)], 1u);
+      atomicAdd(&h[w][part_digit(b.x, shift)], 1u);
+      atomicAdd(&h[w][part_digit(b.y, shift)], 1u);
+      atomicAdd(&h[w][part_digit(b.z, shift)], 1u);
+      atomicAdd(&h[w][part_digit(b.w, shift)], 1u);
     }
   }
   __syncthreads();
@@ -450,11 +429,78 @@ __global__ void __launch_bounds__(kPartHistThreads) part_hist(const uint32_t* __
   }
 }
 
-template <class P>
+// Partition starts from counts the host already holds (one warp).
+struct PartCounts {
+  unsigned long long c[256];
+};
+__global__ void __launch_bounds__(32) part_starts(const __grid_constant__ PartCounts h,
+                                                  unsigned long long* __restrict__ fill, int64_t row_base,
+                                                  unsigned long long* __restrict__ starts_out) {
+  const int lane = threadIdx.x;
+  unsigned long long run = 0;
+  for (int j = 0; j < 8; ++j) {
+    const unsigned long long c = h.c[j * 32 + lane];
+    unsigned long long x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    const unsigned long long start = (unsigned long long)row_base + run + x - c;
+    fill[(j * 32 + lane) * kFillStride] = start;
+    if (starts_out) starts_out[j * 32 + lane] = start;
+    run += __shfl_sync(0xffffffffu, x, 31);
+  }
+  if (starts_out && lane == 0) starts_out[256] = (unsigned long long)row_base + run;
+}
+
+// Tiles of a segmented pass (rows grouped into 256 partitions, starts[0..256]):
+// first[p] = the tiles of partitions before p (kPartTile rows each, no tile
+// straddling two partitions), first[256] = all tiles. One warp computes them.
+__device__ __forceinline__ void seg_first_tiles(const unsigned long long* __restrict__ starts, int64_t* first) {
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    int64_t run = 0;
+    for (int j = 0; j < 8; ++j) {
+      const int p = j * 32 + lane;
+      const int64_t len = (int64_t)(starts[p + 1] - starts[p]);
+      const int64_t c = (len + kPartTile - 1) / kPartTile;
+      int64_t x = c;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int64_t y = __shfl_up_sync(0xffffffffu, x, o);
+        if (lane >= o) x += y;
+      }
+      first[p] = run + x - c;
+      run += __shfl_sync(0xffffffffu, x, 31);
+    }
+    if (lane == 0) first[256] = run;
+  }
+}
+
+// The partition of tile t < first[256]: the last p with first[p] <= t (it has
+// a tile, so first[p + 1] > t).
+__device__ __forceinline__ int seg_of_tile(const int64_t* first, int64_t t) {
+  int lo = 0, hi = 256;  // first[lo] <= t < first[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (first[mid] <= t) lo = mid;
+    else hi = mid;
+  }
+  return lo;
+}
+
+// SEG = false: tile t covers rows [t kPartTile, ...) of the column, fill
+// holds one counter per digit (kFillStride apart). SEG = true: tiles follow
+// the partitions of starts (see seg_first_tiles) and fill holds one counter
+// per (partition, digit), partition-major.
+template <class P, bool SEG>
 __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* __restrict__ keys,
                                                                 const P* __restrict__ vals,
                                                                 uint32_t* __restrict__ okeys, P* __restrict__ ovals,
-                                                                int64_t n, unsigned long long* __restrict__ fill) {
+                                                                int64_t n, unsigned long long* __restrict__ fill,
+                                                                int shift,
+                                                                const unsigned long long* __restrict__ starts) {
   constexpr int kRows = kPartTile / kPartThreads;  // rows per thread and tile
   constexpr int kWarps = kPartThreads / 32;
   extern __shared__ __align__(16) unsigned char sm_raw[];
@@ -463,11 +509,29 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
   uint32_t* whist = stage_k + kPartTile;                 // kWarps x 256
   __shared__ uint32_t off[256];
   __shared__ unsigned long long base[256];
+  __shared__ int64_t first[SEG ? 257 : 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+  int64_t ntiles;
+  if (SEG) {
+    seg_first_tiles(starts, first);
+    __syncthreads();
+    ntiles = first[256];
+  } else {
+    ntiles = (n + kPartTile - 1) / kPartTile;
+  }
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    const int64_t r0 = t * kPartTile;
-    const int rows = (int)min((int64_t)kPartTile, n - r0);
+    int64_t r0;
+    int rows, fbase = 0, fstride = kFillStride;
+    if (SEG) {
+      const int p = seg_of_tile(first, t);
+      r0 = (int64_t)starts[p] + (t - first[p]) * kPartTile;
+      rows = (int)min((int64_t)kPartTile, (int64_t)starts[p + 1] - r0);
+      fbase = p * 256;
+      fstride = 1;
+    } else {
+      r0 = t * kPartTile;
+      rows = (int)min((int64_t)kPartTile, n - r0);
+    }
     for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) whist[i] = 0;
     // each warp owns kRows * 32 consecutive rows: every key and value load is issued first
     uint32_t kr[kRows], pr[kRows];
@@ -483,7 +547,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
-      if (j < rows) pr[r] = atomicAdd(&whist[w * 256 + part_digit(kr[r])], 1u);
+      if (j < rows) pr[r] = atomicAdd(&whist[w * 256 + part_digit(kr[r], shift)], 1u);
     }
     __syncthreads();
     if (threadIdx.x < 256) {  // per digit: the warps' runs, and the tile's count
@@ -495,7 +559,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
         run += c;
       }
       off[d] = run;  // the tile's count of digit d, until the scan below
-      base[d] = run ? atomicAdd(&fill[d * kFillStride], (unsigned long long)run) : 0ull;
+      base[d] = run ? atomicAdd(&fill[fbase + d * fstride], (unsigned long long)run) : 0ull;
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive scan of the counts over digits
@@ -517,7 +581,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
       if (j < rows) {
-        const uint32_t d = part_digit(kr[r]);
+        const uint32_t d = part_digit(kr[r], shift);
         const uint32_t p = off[d] + whist[w * 256 + d] + pr[r];
         stage_k[p] = kr[r];
         stage_v[p] = vr[r];
@@ -526,13 +590,92 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
     __syncthreads();
     for (int p = threadIdx.x; p < rows; p += kPartThreads) {
       const uint32_t key = stage_k[p];
-      const uint32_t d = part_digit(key);
+      const uint32_t d = part_digit(key, shift);
       const unsigned long long q = base[d] + (unsigned long long)(p - (int)off[d]);
       okeys[q] = key;
       ovals[q] = stage_v[p];
     }
     __syncthreads();  // the stage and the counters are reused by the next tile
   }
+}
+
+// Second-level counts: per tile of a segmented pass, the rows of each digit
+// (per-warp shared counters), added to counts[partition * 256 + digit].
+__global__ void __launch_bounds__(kPartThreads) seg_hist(const uint32_t* __restrict__ keys,
+                                                         const unsigned long long* __restrict__ starts,
+                                                         unsigned long long* __restrict__ counts, int shift) {
+  constexpr int kRows = kPartTile / kPartThreads;
+  constexpr int kWarps = kPartThreads / 32;
+  __shared__ uint32_t h[kWarps][256];
+  __shared__ int64_t first[257];
+  const int w = threadIdx.x >> 5;
+  seg_first_tiles(starts, first);
+  __syncthreads();
+  const int64_t ntiles = first[256];
+  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) (&h[0][0])[i] = 0;
+    const int p = seg_of_tile(first, t);
+    const int64_t r0 = (int64_t)starts[p] + (t - first[p]) * kPartTile;
+    const int rows = (int)min((int64_t)kPartTile, (int64_t)starts[p + 1] - r0);
+    uint32_t kr[kRows];
+#pragma unroll
+    for (int r = 0; r < kRows; ++r) {
+      const int j = r * kPartThreads + (int)threadIdx.x;
+      kr[r] = j < rows ? keys[r0 + j] : 0u;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < kRows; ++r)
+      if (r * kPartThreads + (int)threadIdx.x < rows) atomicAdd(&h[w][part_digit(kr[r], shift)], 1u);
+    __syncthreads();
+    if (threadIdx.x < 256) {
+      uint32_t c = 0;
+      for (int ww = 0; ww < kWarps; ++ww) c += h[ww][threadIdx.x];
+      if (c) atomicAdd(&counts[p * 256 + threadIdx.x], (unsigned long long)c);
+    }
+    __syncthreads();
+  }
+}
+
+// Exclusive scan of the 65536 (partition, digit) counts in place (one block of
+// 1024 threads, 64 consecutive counts each): each count becomes the first
+// output row of its run. With sub_starts, the 65536 starts and the end (n)
+// are also written there.
+constexpr int kSegScanThreads = 1024;
+__global__ void __launch_bounds__(kSegScanThreads) seg_starts(unsigned long long* __restrict__ counts,
+                                                              unsigned long long* __restrict__ sub_starts) {
+  constexpr int kPer = 65536 / kSegScanThreads;
+  __shared__ unsigned long long warp_tot[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  unsigned long long* c = counts + threadIdx.x * kPer;
+  unsigned long long own = 0;
+  for (int i = 0; i < kPer; ++i) own += c[i];
+  unsigned long long x = own;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_tot[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    unsigned long long v = warp_tot[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
+      if (lane >= o) v += y;
+    }
+    warp_tot[lane] = v;
+  }
+  __syncthreads();
+  unsigned long long run = (w ? warp_tot[w - 1] : 0ull) + x - own;
+  for (int i = 0; i < kPer; ++i) {
+    const unsigned long long v = c[i];
+    c[i] = run;
+    if (sub_starts) sub_starts[threadIdx.x * kPer + i] = run;
+    run += v;
+  }
+  if (sub_starts && threadIdx.x == kSegScanThreads - 1) sub_starts[65536] = run;
 }
 
 template <class P>
@@ -544,7 +687,8 @@ size_t partition_tmp_bytes() { return (257 * kFillStride) * sizeof(unsigned long
 
 template <class P>
 agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                            cudaStream_t s, int64_t row_base, unsigned long long* starts_out) {
+                            cudaStream_t s, int64_t row_base, unsigned long long* starts_out,
+                            const unsigned long long* hist, int shift) {
   if (n <= 0) {
     if (starts_out) {
       std::vector<unsigned long long> st(257, (unsigned long long)row_base);
@@ -557,19 +701,37 @@ agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P
   cudaGetDevice(&dev);
   static bool attr[64] = {};
   if (dev < 64 && !attr[dev]) {
-    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint32_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint32_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)part_smem<uint32_t>()));
-    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint64_t>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint64_t, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)part_smem<uint64_t>()));
+    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)part_smem<uint32_t>()));
+    AGG_CUDA_TRY(cudaFuncSetAttribute(part_scatter<uint64_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                       (int)part_smem<uint64_t>()));
     attr[dev] = true;
   }
   unsigned long long* fill = (unsigned long long*)tmp;
-  AGG_CUDA_TRY(cudaMemsetAsync(fill, 0, (257 * kFillStride) * sizeof(unsigned long long), s));
+  PartCounts pc;
+  if (shift < 0 || shift > 24 || (hist && shift != 24)) {
+    set_error("partition digit shift %d (counts given: %d)", shift, hist != nullptr);
+    return AGG_ERR_INVALID;
+  }
+  if (hist) {
+    unsigned long long tot = 0;
+    for (int d = 0; d < 256; ++d) tot += (pc.c[d] = hist[d]);
+    if (tot != (unsigned long long)n) {
+      set_error("partition counts sum to %llu, not %lld rows", tot, (long long)n);
+      return AGG_ERR_INVALID;
+    }
+  } else {
+    AGG_CUDA_TRY(cudaMemsetAsync(fill, 0, (257 * kFillStride) * sizeof(unsigned long long), s));
+  }
   const DeviceInfo& di = device_info();
   int bh = 1, bs = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, part_hist, kPartHistThreads, 0) != cudaSuccess || bh < 1)
     bh = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, part_scatter<P>, kPartThreads, part_smem<P>()) !=
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, part_scatter<P, false>, kPartThreads, part_smem<P>()) !=
           cudaSuccess ||
       bs < 1)
     bs = 1;
@@ -579,22 +741,59 @@ agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P
   const int64_t gh = std::max<int64_t>(
       1, std::min<int64_t>((int64_t)di.sm_count * bh, ((n - head) / 4 + 2 * kPartHistThreads - 1) / (2 * kPartHistThreads)));
   const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, ntiles));
-  part_hist<<<(unsigned)gh, kPartHistThreads, 0, s>>>(kin, n, head, fill, row_base, starts_out);
-  part_scatter<P><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kin, vin, kout, vout, n, fill);
+  if (hist) part_starts<<<1, 32, 0, s>>>(pc, fill, row_base, starts_out);
+  else part_hist<<<(unsigned)gh, kPartHistThreads, 0, s>>>(kin, n, head, fill, row_base, starts_out, shift);
+  part_scatter<P, false><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kin, vin, kout, vout, n, fill, shift,
+                                                                            nullptr);
   note_launch(2);
   AGG_CUDA_TRY(cudaGetLastError());
   return AGG_OK;
 }
 
-template agg_status partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t, void*,
-                                               cudaStream_t, int64_t, unsigned long long*);
-template agg_status partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t, void*,
-                                               cudaStream_t, int64_t, unsigned long long*);
+size_t partition2_tmp_bytes() {  // level-1 counters, level-1 starts, (partition, digit) counts
+  return ((partition_tmp_bytes() + 255) & ~size_t(255)) + ((257 * 8 + 255) & ~size_t(255)) + 65536 * 8;
+}
 
-template agg_status radix_partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t,
-                                                     void*, cudaStream_t, int);
-template agg_status radix_partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t,
-                                                     void*, cudaStream_t, int);
+template <class P>
+agg_status partition_hashed2(const uint32_t* kin, const P* vin, uint32_t* kmid, P* vmid, uint32_t* kout, P* vout,
+                             int64_t n, void* tmp, cudaStream_t s, const unsigned long long* hist) {
+  if (n <= 0) return AGG_OK;
+  char* t = (char*)tmp;
+  const size_t off1 = (partition_tmp_bytes() + 255) & ~size_t(255);
+  unsigned long long* starts1 = (unsigned long long*)(t + off1);                  // 257 level-1 starts
+  unsigned long long* counts = (unsigned long long*)(t + off1 + ((257 * 8 + 255) & ~size_t(255)));  // 65536
+  agg_status st = partition_hashed<P>(kin, vin, kmid, vmid, n, tmp, s, 0, starts1, hist, 24);
+  if (st != AGG_OK) return st;
+  AGG_CUDA_TRY(cudaMemsetAsync(counts, 0, 65536 * sizeof(unsigned long long), s));
+  const DeviceInfo& di = device_info();
+  int bh = 1, bs = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, seg_hist, kPartThreads, 0) != cudaSuccess || bh < 1) bh = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, part_scatter<P, true>, kPartThreads, part_smem<P>()) !=
+          cudaSuccess ||
+      bs < 1)
+    bs = 1;
+  const int64_t tiles_max = n / kPartTile + 256;  // tiles of the segmented passes, at most
+  const int64_t gh = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bh, tiles_max));
+  const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, tiles_max));
+  seg_hist<<<(unsigned)gh, kPartThreads, 0, s>>>(kmid, starts1, counts, 16);
+  seg_starts<<<1, kSegScanThreads, 0, s>>>(counts, nullptr);
+  part_scatter<P, true><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kmid, vmid, kout, vout, n, counts, 16,
+                                                                           starts1);
+  note_launch(3);
+  AGG_CUDA_TRY(cudaGetLastError());
+  return AGG_OK;
+}
+
+template agg_status partition_hashed2<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
+                                                uint32_t*, int64_t, void*, cudaStream_t, const unsigned long long*);
+template agg_status partition_hashed2<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, uint32_t*,
+                                                uint64_t*, int64_t, void*, cudaStream_t, const unsigned long long*);
+
+template agg_status partition_hashed<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, int64_t, void*,
+                                               cudaStream_t, int64_t, unsigned long long*, const unsigned long long*, int);
+template agg_status partition_hashed<uint64_t>(const uint32_t*, const uint64_t*, uint32_t*, uint64_t*, int64_t, void*,
+                                               cudaStream_t, int64_t, unsigned long long*, const unsigned long long*, int);
+
 
 template agg_status radix_sort_pairs<uint32_t>(const uint32_t*, const uint32_t*, uint32_t*, uint32_t*, uint32_t*,
                                                uint32_t*, int64_t, const int64_t*, int, void*, cudaStream_t,

@@ -31,24 +31,29 @@ agg_status radix_sort_pairs(const uint32_t* kin, const P* vin, uint32_t* ka, P* 
                             int64_t n_cap, const int64_t* n_dev, int bits, void* tmp, cudaStream_t s,
                             uint32_t** kout, P** vout, uint32_t kbase = 0);
 
-// One stable radix pass on bits [shift, shift + 8) of fmix32(key) (shift 24:
-// the top 8 bits; a pass at 16 followed by a pass at 24 orders rows by the top
-// 16 bits). Rows come out grouped by hash partition, in input order within a
-// partition. tmp must hold radix_tmp_bytes(n).
-template <class P>
-agg_status radix_partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                                  cudaStream_t s, int shift);
-
-// One-level hash partition by the top 8 bits of fmix32(key), in no particular
-// order within a partition (rows of one partition are contiguous, partitions
-// in ascending digit order). The rows land at kout[row_base, row_base + n)
+// One-level hash partition by bits [shift, shift + 8) of fmix32(key) (shift
+// 24: the top 8 bits), in no particular order within a partition (rows of one
+// partition are contiguous, partitions in ascending digit order). The rows land at kout[row_base, row_base + n)
 // (likewise vout); with starts_out, the 256 partition starts and the end
 // (row_base + n) are written there (device memory, 257 values). tmp must hold
-// partition_tmp_bytes() bytes.
+// partition_tmp_bytes() bytes. With hist (host memory, 256 values: the rows of
+// each partition, as hll_estimate counts them for shift 24, summing to n) the
+// histogram pass is skipped.
 size_t partition_tmp_bytes();
 template <class P>
 agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P* vout, int64_t n, void* tmp,
-                            cudaStream_t s, int64_t row_base = 0, unsigned long long* starts_out = nullptr);
+                            cudaStream_t s, int64_t row_base = 0, unsigned long long* starts_out = nullptr,
+                            const unsigned long long* hist = nullptr, int shift = 24);
+
+// Two-level hash partition: by the top 8 bits of fmix32(key) (through
+// (kmid, vmid), with hist as for partition_hashed), then each of those 256
+// partitions by bits 16..23, so that rows come out ordered by the top 16 hash
+// bits (65536 partitions), in no particular order within one. tmp must hold
+// partition2_tmp_bytes() bytes.
+size_t partition2_tmp_bytes();
+template <class P>
+agg_status partition_hashed2(const uint32_t* kin, const P* vin, uint32_t* kmid, P* vmid, uint32_t* kout, P* vout,
+                             int64_t n, void* tmp, cudaStream_t s, const unsigned long long* hist = nullptr);
 
 // Set the kernel attributes the sort needs (call before a stream capture).
 agg_status radix_prepare();

@@ -53,3 +53,21 @@ def test_plans_from_the_count_need_no_regrowth(s):
         assert np.array_equal(res["keys"], ref.keys) and np.array_equal(res["count"], ref.count)
         assert np.array_equal(res["sum"], ref.sum) and np.array_equal(res["min"], ref.min)
         assert np.array_equal(res["max"], ref.max)
+
+
+@pytest.mark.parametrize("strategy", [agg.AGG_STRAT_AUTO, agg.AGG_STRAT_LEARNED, agg.AGG_STRAT_SMEM])
+@pytest.mark.parametrize("off", [0, 3])
+def test_partition_counts_from_the_count_pass(strategy, off):
+    """The distinct-count pass also counts each hash partition's rows, and the one-level
+    partition then skips its own histogram: a ragged, misaligned column of about 2^22 rows
+    over 2^17 keys (partitioned, counted) gives the oracle's groups."""
+    n, D = (1 << 22) + 7, 1 << 17
+    keys, vals = dg.keys_uniform(n, D, 11), dg.values("i64", n, 12)
+    k, v = torch.from_numpy(keys).cuda()[off:], torch.from_numpy(vals).cuda()[off:]  # off: not 16-byte aligned
+    ref = oracle.groupby(keys[off:], vals[off:])
+    g = agg.agg_groupby(k, v, agg.AGG_ALL, agg.options(strategy, partition=1))
+    res = g.to_host()
+    g.free()
+    assert np.array_equal(res["keys"], ref.keys) and np.array_equal(res["count"], ref.count)
+    assert np.array_equal(res["sum"], ref.sum) and np.array_equal(res["min"], ref.min)
+    assert np.array_equal(res["max"], ref.max)
