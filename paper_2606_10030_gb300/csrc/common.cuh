@@ -26,6 +26,7 @@ void clear_error();
     if (e_ != cudaSuccess) {                                                       \
       ::agg::set_error("%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_),     \
                        __FILE__, __LINE__);                                        \
+      (void)cudaGetLastError(); /* a later launch check must not see it again */   \
       return e_ == cudaErrorMemoryAllocation ? AGG_ERR_OOM : AGG_ERR_CUDA;         \
     }                                                                              \
   } while (0)
@@ -50,9 +51,9 @@ struct DeviceInfo {
 const DeviceInfo& device_info();  // of the current device
 
 // Stream-ordered scratch owned by the library, cached per (device, stream).
-// The returned block is at least `bytes` long; its first `zero_prefix` bytes
-// were zeroed when the block was (re)allocated and must be left zeroed by
-// every user (self-resetting counters live there).
+// The returned block is at least `bytes` long and was zeroed when it was
+// (re)allocated; self-resetting counters kept there must be left zeroed by
+// every user.
 void* stream_scratch(cudaStream_t s, size_t bytes, agg_status* st);
 void* stream_pinned(cudaStream_t s, size_t bytes, agg_status* st);
 

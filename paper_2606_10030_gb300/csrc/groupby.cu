@@ -97,13 +97,16 @@ static KernelPtr pick_build(int dt, bool mm, bool smem, bool vec, bool multi, in
 }
 
 template <int DT, bool MM>
-static KernelPtr tiles_kernel(int qpi) {
+static KernelPtr tiles_kernel(int qpi, bool home) {
+  if (home)
+    return qpi == 2 ? (KernelPtr)gb_build_tiles<DT, MM, true, 2, true> : (KernelPtr)gb_build_tiles<DT, MM, true, 1, true>;
   return qpi == 2 ? (KernelPtr)gb_build_tiles<DT, MM, true, 2> : (KernelPtr)gb_build_tiles<DT, MM, true, 1>;
 }
 
-static KernelPtr pick_tiles(int dt, bool mm, int qpi) {
+// home: the tiles' shared tables are lightly loaded (see s_find_home).
+static KernelPtr pick_tiles(int dt, bool mm, int qpi, bool home) {
 #define AGG_T(D) \
-  case D: return mm ? tiles_kernel<D, true>(qpi) : tiles_kernel<D, false>(qpi);
+  case D: return mm ? tiles_kernel<D, true>(qpi, home) : tiles_kernel<D, false>(qpi, home);
   switch (dt) { AGG_T(AGG_I32) AGG_T(AGG_I64) AGG_T(AGG_U32) AGG_T(AGG_F32) AGG_T(AGG_F64) }
 #undef AGG_T
   return nullptr;
@@ -308,7 +311,17 @@ struct HashPlan {
   // Rows of each one-level partition of the column (host memory, counted by
   // the HyperLogLog pass), or null: the partition then counts them itself.
   const unsigned long long* part_hist = nullptr;
+  double est_keys = 0.0;  // the planner's distinct-key estimate of the column
 };
+
+// Whether a partitioned build's shared tables stay lightly loaded (at most a
+// quarter of the slots): about est / P keys per tile when a tile lies within
+// one of the P partitions, proportionally more when it spans several.
+static bool tiles_lightly_loaded(double est, int64_t n, int passes, int64_t tile_rows, int smem_slots) {
+  const double parts = passes == 2 ? 65536.0 : 256.0;
+  const double span = std::max(1.0, (double)tile_rows * parts / (double)std::max<int64_t>(n, 1));
+  return est > 0.0 && (est / parts) * span <= 0.25 * (double)smem_slots;
+}
 
 // One hash aggregation: a zeroed global table, any number of build launches
 // over row ranges (one for a device column, one per chunk for a host-fed
@@ -435,10 +448,10 @@ class HashRun {
           set_error("partitioned build: %s", cudaGetErrorString(e));
           return AGG_ERR_CUDA;
         }
-        KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi);
         const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
         const int threads = plan_.threads;
-        int bps = occupancy(bk, threads, smem);
+        // both variants have the same resources: occupancy from either
+        int bps = occupancy(pick_tiles(vdt_, mm_, plan_.qpi, false), threads, smem);
         if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
         int64_t grid = (int64_t)di.sm_count * bps;
         // tiles of up to 64 Ki rows (32 Ki after two levels), smaller (down to
@@ -448,6 +461,9 @@ class HashRun {
           tile_rows = plan_.partition_passes == 2 ? kPartTileRows / 2 : kPartTileRows;
           while (tile_rows > 4096 && n < 2 * grid * tile_rows) tile_rows >>= 1;
         }
+        KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi,
+                                  tiles_lightly_loaded(plan_.est_keys, n, passes, tile_rows, plan_.smem_slots));
+        (void)occupancy(bk, threads, smem);  // sets the kernel's shared-memory limit
         const int64_t tiles = (n + tile_rows - 1) / tile_rows;
         if (tiles < grid) grid = tiles;
         const longlong2* no_tiles = nullptr;
@@ -499,7 +515,7 @@ class HashRun {
     note_launch();
     unsigned long long* next_tile = (unsigned long long*)((char*)mem_ + status_off_ + 128);
     AGG_CUDA_TRY(cudaMemsetAsync(next_tile, 0, 8, s_));
-    KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi);
+    KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi, tiles_lightly_loaded(plan_.est_keys, n, 1, 1, plan_.smem_slots));
     const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
     int bps = occupancy(bk, plan_.threads, smem);
     if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
@@ -735,6 +751,7 @@ static agg_status choose(const uint32_t* keys, const void* vals, int64_t n, int 
   c->plan.blocks_per_sm = o.blocks_per_sm;
   c->plan.qpi = items == 8 ? 2 : 1;
   c->plan.tile_rows = tile;
+  c->plan.est_keys = est;
   // Partition the rows by hash first when the shared tables would spill (more
   // distinct keys than a shared table admits) or the global table exceeds
   // half of L2; each partition then has about 1/256 of the keys.
@@ -1046,11 +1063,12 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     const size_t tiles_b = ((size_t)max_tiles * 16 + 255) & ~size_t(255);
     const size_t extra = starts_b + tiles_b + 256 + ((partition_tmp_bytes() + 255) & ~size_t(255)) + hll_state_bytes();
     void* full = nullptr;
-    AGG_CUDA_TRY(dev_malloc_async(&full, col_bytes + extra, s));
+    const size_t col_r = (col_bytes + 255) & ~size_t(255);
+    AGG_CUDA_TRY(dev_malloc_async(&full, col_r + extra, s));
     Free full_free{full, s};
     uint32_t* fk = (uint32_t*)full;
     char* fv = (char*)full + kb;
-    char* x = (char*)full + ((col_bytes + 255) & ~size_t(255));
+    char* x = (char*)full + col_r;
     unsigned long long* starts = (unsigned long long*)x;
     longlong2* tiles = (longlong2*)(x + starts_b);
     unsigned long long* ntiles = (unsigned long long*)(x + starts_b + tiles_b);

@@ -229,11 +229,16 @@ __device__ __forceinline__ ulonglong2 lds_v2_64(const void* p) {
 }
 
 // Fast path: the key's slot if it sits in its home bucket, else -1 (one
-// 16-byte shared load, no branches on the data).
-template <int DT, bool MM>
+// 16-byte shared load, no branches on the data). HOME: first one 4-byte load
+// of the key's home slot, where the insert puts it when that slot is free: a
+// lightly loaded table (a partitioned tile's few keys) then mostly needs only
+// that load; a table at load 1/2 loses more to the second load than it saves.
+template <int DT, bool MM, bool HOME = false>
 __device__ __forceinline__ int s_find_home(const STab<DT, MM>& t, int S, uint32_t key) {
   const uint32_t k1 = key + 1;
-  const uint32_t b = fmix32(key) & (uint32_t)(S - 1) & ~3u;
+  const uint32_t hs = fmix32(key) & (uint32_t)(S - 1);
+  if (HOME && key != 0xFFFFFFFFu && *(volatile uint32_t*)&t.key1[hs] == k1) return (int)hs;
+  const uint32_t b = hs & ~3u;
   const uint4 q = lds_v4(&t.key1[b]);
   int j = -1;
   j = q.w == k1 ? (int)b + 3 : j;
@@ -244,7 +249,11 @@ __device__ __forceinline__ int s_find_home(const STab<DT, MM>& t, int S, uint32_
 }
 
 // Slot of key in the shared table (inserting it if there is room), or -1.
-template <int DT, bool MM>
+// HOME: a new key takes its home slot when that is free (for the HOME fast
+// path of s_find_home), else the bucket's first free slot. The two orders are
+// separate instances: the plain build measured twice as slow with the
+// home-first code in its (rarely taken) insert path, the tile build faster.
+template <int DT, bool MM, bool HOME = false>
 __device__ __noinline__ int s_lookup(const STab<DT, MM>& t, int S, int cap, uint32_t key) {
   if (key == 0xFFFFFFFFu) return S;
   const uint32_t k1 = key + 1;
@@ -256,11 +265,21 @@ __device__ __noinline__ int s_lookup(const STab<DT, MM>& t, int S, int cap, uint
     if (q.y == k1) return (int)b + 1;
     if (q.z == k1) return (int)b + 2;
     if (q.w == k1) return (int)b + 3;
-    // claim an empty slot of this bucket; each failed claim fills a slot, so
-    // this loop runs at most 4 times
+    // claim an empty slot of this bucket (HOME: in the first bucket, the key's
+    // home slot first); each failed claim fills a slot, so this loop runs at
+    // most 4 times
+    const uint32_t h0 = HOME && p == 0 ? (fmix32(key) & 3u) : 0u;
 #pragma unroll 1
     for (int tries = 0; tries < 4; ++tries) {
-      const int e = q.x == 0 ? 0 : q.y == 0 ? 1 : q.z == 0 ? 2 : q.w == 0 ? 3 : -1;
+      int e;
+      if (HOME) {  // empty slots as a 4-bit mask, rotated so that bit 0 is position h0
+        const uint32_t em =
+            (q.x == 0u ? 1u : 0u) | (q.y == 0u ? 2u : 0u) | (q.z == 0u ? 4u : 0u) | (q.w == 0u ? 8u : 0u);
+        const uint32_t rot = ((em >> h0) | (em << (4u - h0))) & 15u;
+        e = rot ? (int)((h0 + (uint32_t)(__ffs(rot) - 1)) & 3u) : -1;
+      } else {
+        e = q.x == 0 ? 0 : q.y == 0 ? 1 : q.z == 0 ? 2 : q.w == 0 ? 3 : -1;
+      }
       if (e < 0) break;
       if (*(volatile int*)t.used >= cap) return -1;  // full enough: no new keys
       const uint32_t old = atomicCAS(&t.key1[b + e], 0u, k1);
@@ -322,7 +341,7 @@ __device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename
 }
 
 // Fold a batch of N rows (valid[r] false = skip).
-template <int DT, bool MM, bool SMEM, int N>
+template <int DT, bool MM, bool SMEM, int N, bool HOME = false>
 __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
                                            const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
   using T = typename GV<DT>::T;
@@ -335,10 +354,10 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
   }
   int j[N];
 #pragma unroll
-  for (int r = 0; r < N; ++r) j[r] = valid[r] ? s_find_home<DT, MM>(st, a.smem_slots, key[r]) : -2;
+  for (int r = 0; r < N; ++r) j[r] = valid[r] ? s_find_home<DT, MM, HOME>(st, a.smem_slots, key[r]) : -2;
 #pragma unroll
   for (int r = 0; r < N; ++r)
-    if (j[r] == -1) j[r] = s_lookup<DT, MM>(st, a.smem_slots, a.smem_cap, key[r]);
+    if (j[r] == -1) j[r] = s_lookup<DT, MM, HOME>(st, a.smem_slots, a.smem_cap, key[r]);
 #pragma unroll
   for (int r = 0; r < N; ++r)
     if (j[r] >= 0) atomicAdd(&st.cnt[j[r]], 1u);
@@ -527,15 +546,15 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
 
 // The warp reduces the rows marked in take (a 4-bit mask per lane; all of
 // one key) and lane 0 folds the partial into the tables.
-template <int DT, bool MM, bool SMEM>
+template <int DT, bool MM, bool SMEM, bool HOME = false>
 __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
                                               const typename GV<DT>::T (&v)[4], uint32_t take) {
   Partial4<DT> p = partial_of<DT, MM>(v, take);
   warp_reduce_partial<DT, MM>(p);
   if ((threadIdx.x & 31) != 0) return;
   if (SMEM) {
-    int j = s_find_home<DT, MM>(st, a.smem_slots, key);
-    if (j < 0) j = s_lookup<DT, MM>(st, a.smem_slots, a.smem_cap, key);
+    int j = s_find_home<DT, MM, HOME>(st, a.smem_slots, key);
+    if (j < 0) j = s_lookup<DT, MM, HOME>(st, a.smem_slots, a.smem_cap, key);
     if (j >= 0) {
       s_add_partial<DT, MM>(st, j, p);
       return;
@@ -585,7 +604,7 @@ __device__ __forceinline__ void report_counts(const BuildArgs& a, const BlockCou
 // reduced update (columns with a handful of keys or hot keys); without it
 // every row takes the per-row path (for columns whose sketch shows no
 // frequent key: the warp then never waits for its slowest lane).
-template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true, int QPI = 1>
+template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true, int QPI = 1, bool HOME = false>
 __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
                                                int64_t nthreads) {
   constexpr int kQuadsPerIter = QPI;
@@ -602,11 +621,11 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
       ok1[0] = tid < a.head;
       k1[0] = ok1[0] ? keys[tid] : 0u;
       v1[0] = ok1[0] ? vals[tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME>(a, st, k1, v1, ok1);
       ok1[0] = tid < a.n - tail0;
       k1[0] = ok1[0] ? keys[tail0 + tid] : 0u;
       v1[0] = ok1[0] ? vals[tail0 + tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME>(a, st, k1, v1, ok1);
     }
     const uint4* kq = (const uint4*)(keys + a.head);
     const uint4* vq = (const uint4*)(vals + a.head);
@@ -648,7 +667,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
 #pragma unroll
             for (int r = 0; r < 4; ++r) take |= (((rem >> r) & 1u) && key[r] == k0) ? (1u << r) : 0u;
             if (__reduce_add_sync(0xffffffffu, (unsigned)__popc(take)) < (unsigned)kDominantRows) break;
-            fold_warp_key<DT, MM, SMEM>(a, st, k0, val, take);
+            fold_warp_key<DT, MM, SMEM, HOME>(a, st, k0, val, take);
             rem &= ~take;
             if (w + 1 == kKeys) break;
             const uint32_t lanes = __ballot_sync(0xffffffffu, rem != 0u);
@@ -666,7 +685,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
           bool ok[1] = {((rem >> r) & 1u) != 0u};
-          fold_batch<DT, MM, SMEM, 1>(a, st, kb, vv, ok);
+          fold_batch<DT, MM, SMEM, 1, HOME>(a, st, kb, vv, ok);
         }
       }
       // table full: the build is redone (status read by lane 0, so the whole warp leaves)
@@ -679,7 +698,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
       uint32_t k1[1] = {keys[i]};
       T v1[1] = {vals[i]};
       bool ok1[1] = {true};
-      fold_batch<DT, MM, SMEM, 1>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME>(a, st, k1, v1, ok1);
       if ((++it & 63) == 0 && *(volatile int*)a.status) break;
     }
     return (uint32_t)it;
@@ -752,7 +771,7 @@ __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
 // (first row, rows), *ntiles of them, listed partition by partition.
 constexpr int64_t kPartTileRows = int64_t(1) << 16;
 
-template <int DT, bool MM, bool VEC, int QPI = 1>
+template <int DT, bool MM, bool VEC, int QPI = 1, bool HOME = false>
 __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
                                                         int64_t tile_rows, const longlong2* tiles,
                                                         const unsigned long long* ntiles) {
@@ -788,7 +807,7 @@ __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned l
     b.head = min((int64_t)((-r0) & 3), rows);  // rows before the next 16-byte boundary of the keys
     st.clear(a.smem_slots);
     __syncthreads();
-    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI>(b, st, threadIdx.x, blockDim.x));
+    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI, HOME>(b, st, threadIdx.x, blockDim.x));
     __syncthreads();
     flush_smem<DT, MM>(b, st);
     __syncthreads();

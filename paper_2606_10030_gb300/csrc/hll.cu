@@ -38,6 +38,7 @@ constexpr size_t kHllHistOff = kHllTicketOff + 256;
 constexpr size_t kHllStateBytes = kHllHistOff + 256 * 8;
 constexpr size_t kHllScratchBytes = kHllScratchOff + kHllStateBytes;
 constexpr int kHllWarps = kHllThreads / 32;
+constexpr int kHllLoads = 4;  // 16-byte key loads a thread keeps in flight
 
 // whist: the warp's 256 partition counters (HIST only).
 template <bool HIST>
@@ -67,19 +68,19 @@ __global__ void __launch_bounds__(kHllThreads) hll_kernel(const uint32_t* __rest
   if (g < head) hll_add<HIST>(sreg, whist, keys[g]);
   if (g < n - tail0) hll_add<HIST>(sreg, whist, keys[tail0 + g]);
   const uint4* kq = (const uint4*)(keys + head);
-  for (int64_t q = g; q < nq; q += 2 * nthreads) {
-    const uint4 a = ld_stream_v4(kq + q);
-    const bool two = q + nthreads < nq;
-    const uint4 b = two ? ld_stream_v4(kq + q + nthreads) : make_uint4(0, 0, 0, 0);
-    hll_add<HIST>(sreg, whist, a.x);
-    hll_add<HIST>(sreg, whist, a.y);
-    hll_add<HIST>(sreg, whist, a.z);
-    hll_add<HIST>(sreg, whist, a.w);
-    if (two) {
-      hll_add<HIST>(sreg, whist, b.x);
-      hll_add<HIST>(sreg, whist, b.y);
-      hll_add<HIST>(sreg, whist, b.z);
-      hll_add<HIST>(sreg, whist, b.w);
+  for (int64_t q = g; q < nq; q += kHllLoads * nthreads) {  // kHllLoads 16-byte loads in flight per thread
+    uint4 x[kHllLoads];
+#pragma unroll
+    for (int u = 0; u < kHllLoads; ++u)
+      x[u] = q + u * nthreads < nq ? ld_stream_v4(kq + q + u * nthreads) : make_uint4(0, 0, 0, 0);
+#pragma unroll
+    for (int u = 0; u < kHllLoads; ++u) {
+      if (q + u * nthreads < nq) {
+        hll_add<HIST>(sreg, whist, x[u].x);
+        hll_add<HIST>(sreg, whist, x[u].y);
+        hll_add<HIST>(sreg, whist, x[u].z);
+        hll_add<HIST>(sreg, whist, x[u].w);
+      }
     }
   }
   __syncthreads();
@@ -157,7 +158,7 @@ agg_status hll_add_chunk(const uint32_t* keys, int64_t n, uint32_t* regs, bool f
   int bps = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, kern, kHllThreads, smem) != cudaSuccess || bps < 1) bps = 1;
   int64_t grid = (int64_t)device_info().sm_count * bps;
-  const int64_t need = ((n - head) / 4 + 2 * kHllThreads - 1) / (2 * kHllThreads);
+  const int64_t need = ((n - head) / 4 + kHllLoads * kHllThreads - 1) / (kHllLoads * kHllThreads);
   if (need < grid) grid = std::max<int64_t>(1, need);
   if (!first) AGG_CUDA_TRY(cudaMemsetAsync((char*)regs + kHllTicketOff, 0, 8, s));  // the ticket
   {

@@ -335,13 +335,14 @@ agg_status radix_prepare() {
 //                 fmix32(key)) in per-warp shared counters, merged with one
 //                 global atomic per bin and block; the last block to finish
 //                 turns the totals into each partition's start;
-//   part_scatter  per tile of kPartTile rows (a block of 512 threads, 8 rows a
-//                 thread, keys and values loaded up front; two blocks a SM so
-//                 that one's barriers overlap the other's loads): each row's place
+//   part_scatter  per tile of 6144 or 8192 rows (a block of 512 threads, 12 or
+//                 16 rows a thread, the next tile's keys and values loaded
+//                 while the current one is written out): each row's place
 //                 among its warp's rows of the same digit from a per-warp
 //                 shared counter (a plain atomic: order within a partition is
 //                 free), the warps' counts scanned per digit, the tile's runs
-//                 reserved in the output with one global atomic per digit, the
+//                 reserved in the output with one global atomic per digit
+//                 (whose latency overlaps the scan and the staging), the
 //                 rows staged in shared memory in digit order and written out
 //                 run by run.
 // Reads 4 + 12 B and writes 12 B per row (uint32 key, 8-byte value); no per-tile
@@ -351,11 +352,20 @@ agg_status radix_prepare() {
 //
 // A second level (65536 partitions) splits each of the 256 partitions by the
 // next 8 hash bits with the same scatter over tiles that never straddle a
-// partition (seg_hist counts per (partition, digit), seg_starts scans them).
+// partition (seg_hist counts per (partition, digit), seg_starts scans each
+// partition's counts from its start).
 // ---------------------------------------------------------------------------
 constexpr int kPartHistThreads = 512;
 constexpr int kPartThreads = 512;
-constexpr int kPartTile = 4096;
+// Rows per scatter tile and blocks per SM by payload: 8-byte values take
+// 8192-row tiles, one block a SM (112 KB of stage); 4-byte values 6144-row
+// tiles, two blocks a SM (longer runs per partition and fewer per-tile scans
+// than 4096-row tiles; measured on the 2^30-row partition: 5.6 vs 6.1 ms).
+template <class P>
+struct PartCfg {
+  static constexpr int kTile = sizeof(P) == 8 ? 8192 : 6144;
+  static constexpr int kBlocks = sizeof(P) == 8 ? 1 : 2;
+};
 constexpr int kFillStride = 32;  // global fill counters 256 B apart (different L2 lines)
 
 __device__ __forceinline__ uint32_t part_digit(uint32_t key, int shift) { return (fmix32(key) >> shift) & 255u; }
@@ -455,8 +465,9 @@ __global__ void __launch_bounds__(32) part_starts(const __grid_constant__ PartCo
 }
 
 // Tiles of a segmented pass (rows grouped into 256 partitions, starts[0..256]):
-// first[p] = the tiles of partitions before p (kPartTile rows each, no tile
+// first[p] = the tiles of partitions before p (TILE rows each, no tile
 // straddling two partitions), first[256] = all tiles. One warp computes them.
+template <int TILE>
 __device__ __forceinline__ void seg_first_tiles(const unsigned long long* __restrict__ starts, int64_t* first) {
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
@@ -464,7 +475,7 @@ __device__ __forceinline__ void seg_first_tiles(const unsigned long long* __rest
     for (int j = 0; j < 8; ++j) {
       const int p = j * 32 + lane;
       const int64_t len = (int64_t)(starts[p + 1] - starts[p]);
-      const int64_t c = (len + kPartTile - 1) / kPartTile;
+      const int64_t c = (len + TILE - 1) / TILE;
       int64_t x = c;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -490,67 +501,84 @@ __device__ __forceinline__ int seg_of_tile(const int64_t* first, int64_t t) {
   return lo;
 }
 
-// SEG = false: tile t covers rows [t kPartTile, ...) of the column, fill
+// SEG = false: tile t covers rows [t kTile, ...) of the column, fill
 // holds one counter per digit (kFillStride apart). SEG = true: tiles follow
 // the partitions of starts (see seg_first_tiles) and fill holds one counter
 // per (partition, digit), partition-major.
 template <class P, bool SEG>
-__global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* __restrict__ keys,
+__global__ void __launch_bounds__(kPartThreads, PartCfg<P>::kBlocks) part_scatter(const uint32_t* __restrict__ keys,
                                                                 const P* __restrict__ vals,
                                                                 uint32_t* __restrict__ okeys, P* __restrict__ ovals,
                                                                 int64_t n, unsigned long long* __restrict__ fill,
                                                                 int shift,
                                                                 const unsigned long long* __restrict__ starts) {
-  constexpr int kRows = kPartTile / kPartThreads;  // rows per thread and tile
+  constexpr int kTile = PartCfg<P>::kTile;
+  constexpr int kRows = kTile / kPartThreads;  // rows per thread and tile
   constexpr int kWarps = kPartThreads / 32;
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  P* stage_v = (P*)sm_raw;                                // kPartTile
-  uint32_t* stage_k = (uint32_t*)(stage_v + kPartTile);  // kPartTile
-  uint32_t* whist = stage_k + kPartTile;                 // kWarps x 256
+  P* stage_v = (P*)sm_raw;                            // kTile
+  uint32_t* stage_k = (uint32_t*)(stage_v + kTile);  // kTile
+  uint32_t* whist = stage_k + kTile;                 // kWarps x 256
   __shared__ uint32_t off[256];
   __shared__ unsigned long long base[256];
   __shared__ int64_t first[SEG ? 257 : 1];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   int64_t ntiles;
   if (SEG) {
-    seg_first_tiles(starts, first);
+    seg_first_tiles<kTile>(starts, first);
     __syncthreads();
     ntiles = first[256];
   } else {
-    ntiles = (n + kPartTile - 1) / kPartTile;
+    ntiles = (n + kTile - 1) / kTile;
   }
-  for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-    int64_t r0;
-    int rows, fbase = 0, fstride = kFillStride;
+  // tile t: its first row, its rows, and where its digits' counters are
+  auto tile_of = [&](int64_t t, int64_t& r0, int& rows, int& fbase) {
     if (SEG) {
       const int p = seg_of_tile(first, t);
-      r0 = (int64_t)starts[p] + (t - first[p]) * kPartTile;
-      rows = (int)min((int64_t)kPartTile, (int64_t)starts[p + 1] - r0);
+      r0 = (int64_t)starts[p] + (t - first[p]) * kTile;
+      rows = (int)min((int64_t)kTile, (int64_t)starts[p + 1] - r0);
       fbase = p * 256;
-      fstride = 1;
     } else {
-      r0 = t * kPartTile;
-      rows = (int)min((int64_t)kPartTile, n - r0);
+      r0 = t * kTile;
+      rows = (int)min((int64_t)kTile, n - r0);
+      fbase = 0;
     }
-    for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) whist[i] = 0;
-    // each warp owns kRows * 32 consecutive rows: every key and value load is issued first
-    uint32_t kr[kRows], pr[kRows];
-    P vr[kRows];
-    const int wbase = w * kRows * 32;
+  };
+  constexpr int kStride = SEG ? 1 : kFillStride;
+  // each warp owns kRows * 32 consecutive rows of a tile; the next tile's keys
+  // and values are loaded while the current one is written out
+  uint32_t kr[kRows];
+  P vr[kRows];
+  const int wbase = w * kRows * 32;
+  auto load = [&](int64_t r0, int rows) {
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
       kr[r] = j < rows ? keys[r0 + j] : 0u;
       vr[r] = j < rows ? vals[r0 + j] : P(0);
     }
-    __syncthreads();
+  };
+  int64_t t = blockIdx.x, r0 = 0;
+  int rows = 0, fbase = 0;
+  if (t < ntiles) {
+    tile_of(t, r0, rows, fbase);
+    load(r0, rows);
+  }
+  for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) whist[i] = 0;
+  __syncthreads();
+  for (; t < ntiles; t += gridDim.x) {
+    uint32_t pr[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
       const int j = wbase + r * 32 + lane;
       if (j < rows) pr[r] = atomicAdd(&whist[w * 256 + part_digit(kr[r], shift)], 1u);
     }
     __syncthreads();
-    if (threadIdx.x < 256) {  // per digit: the warps' runs, and the tile's count
+    // per digit: the warps' runs and the tile's count; the tile's run in the
+    // output is reserved now, its offset stored only after the staging (the
+    // atomic's latency overlaps the scan and the staging)
+    unsigned long long my_base = 0;
+    if (threadIdx.x < 256) {
       const int d = threadIdx.x;
       uint32_t run = 0;
       for (int ww = 0; ww < kWarps; ++ww) {
@@ -559,7 +587,7 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
         run += c;
       }
       off[d] = run;  // the tile's count of digit d, until the scan below
-      base[d] = run ? atomicAdd(&fill[fbase + d * fstride], (unsigned long long)run) : 0ull;
+      if (run) my_base = atomicAdd(&fill[fbase + d * kStride], (unsigned long long)run);
     }
     __syncthreads();
     if (threadIdx.x < 32) {  // exclusive scan of the counts over digits
@@ -587,36 +615,45 @@ __global__ void __launch_bounds__(kPartThreads, 2) part_scatter(const uint32_t* 
         stage_v[p] = vr[r];
       }
     }
+    // a row at stage position p goes to base[d] + p (mod 2^64)
+    if (threadIdx.x < 256) base[threadIdx.x] = my_base - (unsigned long long)off[threadIdx.x];
+    const int rows_now = rows;
+    if (t + gridDim.x < ntiles) {
+      tile_of(t + gridDim.x, r0, rows, fbase);
+      load(r0, rows);
+    }
     __syncthreads();
-    for (int p = threadIdx.x; p < rows; p += kPartThreads) {
+    for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) whist[i] = 0;  // for the next tile
+    for (int p = threadIdx.x; p < rows_now; p += kPartThreads) {
       const uint32_t key = stage_k[p];
       const uint32_t d = part_digit(key, shift);
-      const unsigned long long q = base[d] + (unsigned long long)(p - (int)off[d]);
+      const unsigned long long q = base[d] + (unsigned long long)p;
       okeys[q] = key;
       ovals[q] = stage_v[p];
     }
-    __syncthreads();  // the stage and the counters are reused by the next tile
+    __syncthreads();  // the stage and base are reused by the next tile
   }
 }
 
 // Second-level counts: per tile of a segmented pass, the rows of each digit
 // (per-warp shared counters), added to counts[partition * 256 + digit].
+template <int TILE>
 __global__ void __launch_bounds__(kPartThreads) seg_hist(const uint32_t* __restrict__ keys,
                                                          const unsigned long long* __restrict__ starts,
                                                          unsigned long long* __restrict__ counts, int shift) {
-  constexpr int kRows = kPartTile / kPartThreads;
+  constexpr int kRows = TILE / kPartThreads;
   constexpr int kWarps = kPartThreads / 32;
   __shared__ uint32_t h[kWarps][256];
   __shared__ int64_t first[257];
   const int w = threadIdx.x >> 5;
-  seg_first_tiles(starts, first);
+  seg_first_tiles<TILE>(starts, first);
   __syncthreads();
   const int64_t ntiles = first[256];
   for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
     for (int i = threadIdx.x; i < kWarps * 256; i += kPartThreads) (&h[0][0])[i] = 0;
     const int p = seg_of_tile(first, t);
-    const int64_t r0 = (int64_t)starts[p] + (t - first[p]) * kPartTile;
-    const int rows = (int)min((int64_t)kPartTile, (int64_t)starts[p + 1] - r0);
+    const int64_t r0 = (int64_t)starts[p] + (t - first[p]) * TILE;
+    const int rows = (int)min((int64_t)TILE, (int64_t)starts[p + 1] - r0);
     uint32_t kr[kRows];
 #pragma unroll
     for (int r = 0; r < kRows; ++r) {
@@ -637,19 +674,15 @@ __global__ void __launch_bounds__(kPartThreads) seg_hist(const uint32_t* __restr
   }
 }
 
-// Exclusive scan of the 65536 (partition, digit) counts in place (one block of
-// 1024 threads, 64 consecutive counts each): each count becomes the first
-// output row of its run. With sub_starts, the 65536 starts and the end (n)
-// are also written there.
-constexpr int kSegScanThreads = 1024;
-__global__ void __launch_bounds__(kSegScanThreads) seg_starts(unsigned long long* __restrict__ counts,
-                                                              unsigned long long* __restrict__ sub_starts) {
-  constexpr int kPer = 65536 / kSegScanThreads;
-  __shared__ unsigned long long warp_tot[32];
+// The 65536 (partition, digit) counts become the first output row of each
+// run, in place: block p scans partition p's 256 counts (one per thread) and
+// adds the partition's start (its rows are starts[p] .. starts[p + 1]).
+__global__ void __launch_bounds__(256) seg_starts(unsigned long long* __restrict__ counts,
+                                                  const unsigned long long* __restrict__ starts) {
+  __shared__ unsigned long long warp_tot[8];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  unsigned long long* c = counts + threadIdx.x * kPer;
-  unsigned long long own = 0;
-  for (int i = 0; i < kPer; ++i) own += c[i];
+  unsigned long long* c = counts + (size_t)blockIdx.x * 256;
+  const unsigned long long own = c[threadIdx.x];
   unsigned long long x = own;
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
@@ -658,29 +691,14 @@ __global__ void __launch_bounds__(kSegScanThreads) seg_starts(unsigned long long
   }
   if (lane == 31) warp_tot[w] = x;
   __syncthreads();
-  if (w == 0) {
-    unsigned long long v = warp_tot[lane];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const unsigned long long y = __shfl_up_sync(0xffffffffu, v, o);
-      if (lane >= o) v += y;
-    }
-    warp_tot[lane] = v;
-  }
-  __syncthreads();
-  unsigned long long run = (w ? warp_tot[w - 1] : 0ull) + x - own;
-  for (int i = 0; i < kPer; ++i) {
-    const unsigned long long v = c[i];
-    c[i] = run;
-    if (sub_starts) sub_starts[threadIdx.x * kPer + i] = run;
-    run += v;
-  }
-  if (sub_starts && threadIdx.x == kSegScanThreads - 1) sub_starts[65536] = run;
+  unsigned long long before = starts[blockIdx.x];
+  for (int k = 0; k < w; ++k) before += warp_tot[k];
+  c[threadIdx.x] = before + x - own;
 }
 
 template <class P>
 static size_t part_smem() {
-  return (size_t)kPartTile * (sizeof(P) + 4) + (size_t)(kPartThreads / 32) * 256 * 4;
+  return (size_t)PartCfg<P>::kTile * (sizeof(P) + 4) + (size_t)(kPartThreads / 32) * 256 * 4;
 }
 
 size_t partition_tmp_bytes() { return (257 * kFillStride) * sizeof(unsigned long long) + 256; }
@@ -737,7 +755,7 @@ agg_status partition_hashed(const uint32_t* kin, const P* vin, uint32_t* kout, P
     bs = 1;
   int64_t head = (int64_t)(((16 - ((uintptr_t)kin & 15)) & 15) / 4);
   if (head > n) head = n;
-  const int64_t ntiles = (n + kPartTile - 1) / kPartTile;
+  const int64_t ntiles = (n + PartCfg<P>::kTile - 1) / PartCfg<P>::kTile;
   const int64_t gh = std::max<int64_t>(
       1, std::min<int64_t>((int64_t)di.sm_count * bh, ((n - head) / 4 + 2 * kPartHistThreads - 1) / (2 * kPartHistThreads)));
   const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, ntiles));
@@ -767,16 +785,18 @@ agg_status partition_hashed2(const uint32_t* kin, const P* vin, uint32_t* kmid, 
   AGG_CUDA_TRY(cudaMemsetAsync(counts, 0, 65536 * sizeof(unsigned long long), s));
   const DeviceInfo& di = device_info();
   int bh = 1, bs = 1;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, seg_hist, kPartThreads, 0) != cudaSuccess || bh < 1) bh = 1;
+  constexpr int kTile = PartCfg<P>::kTile;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bh, seg_hist<kTile>, kPartThreads, 0) != cudaSuccess || bh < 1)
+    bh = 1;
   if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, part_scatter<P, true>, kPartThreads, part_smem<P>()) !=
           cudaSuccess ||
       bs < 1)
     bs = 1;
-  const int64_t tiles_max = n / kPartTile + 256;  // tiles of the segmented passes, at most
+  const int64_t tiles_max = n / kTile + 256;  // tiles of the segmented passes, at most
   const int64_t gh = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bh, tiles_max));
   const int64_t gs = std::max<int64_t>(1, std::min<int64_t>((int64_t)di.sm_count * bs, tiles_max));
-  seg_hist<<<(unsigned)gh, kPartThreads, 0, s>>>(kmid, starts1, counts, 16);
-  seg_starts<<<1, kSegScanThreads, 0, s>>>(counts, nullptr);
+  seg_hist<kTile><<<(unsigned)gh, kPartThreads, 0, s>>>(kmid, starts1, counts, 16);
+  seg_starts<<<256, 256, 0, s>>>(counts, starts1);
   part_scatter<P, true><<<(unsigned)gs, kPartThreads, part_smem<P>(), s>>>(kmid, vmid, kout, vout, n, counts, 16,
                                                                            starts1);
   note_launch(3);
