@@ -203,8 +203,8 @@ typedef struct agg_options {
                               levels above ~600k distinct keys), 1 = one level (256 partitions),
                               2 = two levels (65536 partitions), -1 = never */
   int32_t flags;           /* AGG_FLAG_* bits; 0 = none */
-  int32_t tile_rows;       /* rows per tile of the hash-partitioned build (power of two in [4096, 65536]);
-                              0 = from the column */
+  int32_t tile_rows;       /* rows per tile of the hash-partitioned build (power of two in [4096, 65536];
+                              65536 runs as 65532-row tiles); 0 = from the column */
 } agg_options;
 
 /*
