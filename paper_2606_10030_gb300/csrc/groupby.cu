@@ -461,6 +461,7 @@ class HashRun {
           tile_rows = plan_.partition_passes == 2 ? kPartTileRows / 2 : kPartTileRows;
           while (tile_rows > 4096 && n < 2 * grid * tile_rows) tile_rows >>= 1;
         }
+        tile_rows = std::min(tile_rows, kTileRowsMax);
         KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi,
                                   tiles_lightly_loaded(plan_.est_keys, n, passes, tile_rows, plan_.smem_slots));
         (void)occupancy(bk, threads, smem);  // sets the kernel's shared-memory limit
@@ -509,7 +510,7 @@ class HashRun {
     a.smem_cap = (plan_.smem_slots * 3) / 4;
     a.status = status_;
     a.progress = progress_;
-    int64_t tile_rows = plan_.tile_rows ? plan_.tile_rows : kPartTileRows / 2;
+    int64_t tile_rows = std::min(plan_.tile_rows ? (int64_t)plan_.tile_rows : kPartTileRows / 2, kTileRowsMax);
     PhaseTimer pt(AGG_PHASE_BUILD, s_);
     gb_piece_tiles<<<1, 1024, 0, s_>>>(starts, nchunks, tile_rows, tiles, ntiles);
     note_launch();

@@ -341,7 +341,7 @@ __device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename
 }
 
 // Fold a batch of N rows (valid[r] false = skip).
-template <int DT, bool MM, bool SMEM, int N, bool HOME = false>
+template <int DT, bool MM, bool SMEM, int N, bool HOME = false, bool PACK = false>
 __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
                                            const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
   using T = typename GV<DT>::T;
@@ -358,9 +358,12 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
 #pragma unroll
   for (int r = 0; r < N; ++r)
     if (j[r] == -1) j[r] = s_lookup<DT, MM, HOME>(st, a.smem_slots, a.smem_cap, key[r]);
+  constexpr bool kPack = PACK && DT != AGG_F32 && DT != AGG_F64;
+  if (!kPack) {
 #pragma unroll
-  for (int r = 0; r < N; ++r)
-    if (j[r] >= 0) atomicAdd(&st.cnt[j[r]], 1u);
+    for (int r = 0; r < N; ++r)
+      if (j[r] >= 0) atomicAdd(&st.cnt[j[r]], 1u);
+  }
   if (DT == AGG_F32) {
     float old[N];
 #pragma unroll
@@ -388,8 +391,14 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
       if (j[r] >= 0) {
         const uint64_t u = (uint64_t)(int64_t)val[r];
         const uint32_t lo = (uint32_t)u;
-        const uint32_t hi = (uint32_t)(u >> 32) + ((uint32_t)(old[r] + lo) < old[r] ? 1u : 0u);
-        if (hi) atomicAdd((uint32_t*)&st.sum[j[r]] + 1, hi);
+        const uint32_t carry = (uint32_t)(old[r] + lo) < old[r] ? 1u : 0u;
+        if (kPack) {  // the count and the carry in one word; the high part only when nonzero
+          atomicAdd(&st.cnt[j[r]], 1u + (carry << 16));
+          if ((uint32_t)(u >> 32)) atomicAdd((uint32_t*)&st.sum[j[r]] + 1, (uint32_t)(u >> 32));
+        } else {
+          const uint32_t hi = (uint32_t)(u >> 32) + carry;
+          if (hi) atomicAdd((uint32_t*)&st.sum[j[r]] + 1, hi);
+        }
       }
     }
   }
@@ -498,10 +507,11 @@ __device__ __forceinline__ void warp_reduce_partial(Partial4<DT>& p) {
 }
 
 // Apply a partial aggregate to a shared slot (same encodings as s_add via fold_batch).
-template <int DT, bool MM>
+template <int DT, bool MM, bool PACK = false>
 __device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, const Partial4<DT>& p) {
   using U = typename SImg<DT>::U;
-  atomicAdd(&st.cnt[j], p.cnt);
+  constexpr bool kPack = PACK && DT != AGG_F32 && DT != AGG_F64;
+  if (!kPack) atomicAdd(&st.cnt[j], p.cnt);
   uint32_t* w = (uint32_t*)&st.sum[j];
   if (DT == AGG_F32) {
     const float old = atomicAdd((float*)&w[0], p.fs);
@@ -514,8 +524,14 @@ __device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, con
   } else {
     const uint32_t lo = (uint32_t)p.isum;
     const uint32_t old = atomicAdd(&w[0], lo);
-    const uint32_t hi = (uint32_t)(p.isum >> 32) + ((uint32_t)(old + lo) < old ? 1u : 0u);
-    if (hi) atomicAdd(&w[1], hi);
+    const uint32_t carry = (uint32_t)(old + lo) < old ? 1u : 0u;
+    if (kPack) {
+      atomicAdd(&st.cnt[j], p.cnt + (carry << 16));
+      if ((uint32_t)(p.isum >> 32)) atomicAdd(&w[1], (uint32_t)(p.isum >> 32));
+    } else {
+      const uint32_t hi = (uint32_t)(p.isum >> 32) + carry;
+      if (hi) atomicAdd(&w[1], hi);
+    }
   }
   if (MM) {
     if (p.mn < *(volatile U*)&st.mm[2 * j]) atomicMin(&st.mm[2 * j], p.mn);
@@ -546,7 +562,7 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
 
 // The warp reduces the rows marked in take (a 4-bit mask per lane; all of
 // one key) and lane 0 folds the partial into the tables.
-template <int DT, bool MM, bool SMEM, bool HOME = false>
+template <int DT, bool MM, bool SMEM, bool HOME = false, bool PACK = false>
 __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
                                               const typename GV<DT>::T (&v)[4], uint32_t take) {
   Partial4<DT> p = partial_of<DT, MM>(v, take);
@@ -556,7 +572,7 @@ __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT,
     int j = s_find_home<DT, MM, HOME>(st, a.smem_slots, key);
     if (j < 0) j = s_lookup<DT, MM, HOME>(st, a.smem_slots, a.smem_cap, key);
     if (j >= 0) {
-      s_add_partial<DT, MM>(st, j, p);
+      s_add_partial<DT, MM, PACK>(st, j, p);
       return;
     }
   }
@@ -604,7 +620,8 @@ __device__ __forceinline__ void report_counts(const BuildArgs& a, const BlockCou
 // reduced update (columns with a handful of keys or hot keys); without it
 // every row takes the per-row path (for columns whose sketch shows no
 // frequent key: the warp then never waits for its slowest lane).
-template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true, int QPI = 1, bool HOME = false>
+template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true, int QPI = 1, bool HOME = false,
+          bool PACK = false>
 __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
                                                int64_t nthreads) {
   constexpr int kQuadsPerIter = QPI;
@@ -621,11 +638,11 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
       ok1[0] = tid < a.head;
       k1[0] = ok1[0] ? keys[tid] : 0u;
       v1[0] = ok1[0] ? vals[tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1, HOME>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, k1, v1, ok1);
       ok1[0] = tid < a.n - tail0;
       k1[0] = ok1[0] ? keys[tail0 + tid] : 0u;
       v1[0] = ok1[0] ? vals[tail0 + tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1, HOME>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, k1, v1, ok1);
     }
     const uint4* kq = (const uint4*)(keys + a.head);
     const uint4* vq = (const uint4*)(vals + a.head);
@@ -667,7 +684,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
 #pragma unroll
             for (int r = 0; r < 4; ++r) take |= (((rem >> r) & 1u) && key[r] == k0) ? (1u << r) : 0u;
             if (__reduce_add_sync(0xffffffffu, (unsigned)__popc(take)) < (unsigned)kDominantRows) break;
-            fold_warp_key<DT, MM, SMEM, HOME>(a, st, k0, val, take);
+            fold_warp_key<DT, MM, SMEM, HOME, PACK>(a, st, k0, val, take);
             rem &= ~take;
             if (w + 1 == kKeys) break;
             const uint32_t lanes = __ballot_sync(0xffffffffu, rem != 0u);
@@ -685,7 +702,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
           bool ok[1] = {((rem >> r) & 1u) != 0u};
-          fold_batch<DT, MM, SMEM, 1, HOME>(a, st, kb, vv, ok);
+          fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, kb, vv, ok);
         }
       }
       // table full: the build is redone (status read by lane 0, so the whole warp leaves)
@@ -698,7 +715,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
       uint32_t k1[1] = {keys[i]};
       T v1[1] = {vals[i]};
       bool ok1[1] = {true};
-      fold_batch<DT, MM, SMEM, 1, HOME>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, k1, v1, ok1);
       if ((++it & 63) == 0 && *(volatile int*)a.status) break;
     }
     return (uint32_t)it;
@@ -706,13 +723,15 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
 }
 
 // Merge a block's shared table into the global table (after a barrier).
-template <int DT, bool MM>
+template <int DT, bool MM, bool PACK = false>
 __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM>& st) {
+  constexpr bool kPack = PACK && DT != AGG_F32 && DT != AGG_F64;
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
   const int S = a.smem_slots;
   for (int j = threadIdx.x; j <= S; j += blockDim.x) {
-    const uint32_t c = st.cnt[j];
-    if (c == 0) continue;
+    const uint32_t w = st.cnt[j];
+    if (w == 0) continue;
+    const uint32_t c = kPack ? (w & 0xFFFFu) : w;  // PACK: count, and the low word's carries above it
     const uint32_t key = j == S ? 0xFFFFFFFFu : st.key1[j] - 1;
     const int64_t g = g_slot<MM>(tab, a.mask, a.gshift, key);
     if (g < 0) {
@@ -728,13 +747,13 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     } else if (DT == AGG_F64) {
       atomicAdd((double*)&gs.sum, __longlong_as_double((long long)sv));
     } else {
-      atomicAdd(&gs.sum, sv);
+      atomicAdd(&gs.sum, kPack ? sv + ((unsigned long long)(w >> 16) << 32) : sv);
     }
     if (MM) {
-      GSlot<true>& w = (GSlot<true>&)gs;
+      GSlot<true>& gw = (GSlot<true>&)gs;
       const uint64_t mn = g_img_of<DT>(st.mm[2 * j]), mx = g_img_of<DT>(st.mm[2 * j + 1]);
-      if (~mn > *(volatile unsigned long long*)&w.minc) atomicMax(&w.minc, (unsigned long long)~mn);
-      if (mx > *(volatile unsigned long long*)&w.mx) atomicMax(&w.mx, (unsigned long long)mx);
+      if (~mn > *(volatile unsigned long long*)&gw.minc) atomicMax(&gw.minc, (unsigned long long)~mn);
+      if (mx > *(volatile unsigned long long*)&gw.mx) atomicMax(&gw.mx, (unsigned long long)mx);
     }
   }
 }
@@ -763,13 +782,17 @@ __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
   report_counts(a, s_cnt);
 }
 
-// Tile-queue build for hash-partitioned input: blocks pull 64 Ki-row tiles in
-// order from a counter, so all blocks work on neighbouring partitions and the
+// Tile-queue build for hash-partitioned input: blocks pull tiles of up to
+// 65532 rows in order from a counter, so all blocks work on neighbouring partitions and the
 // table region they update stays in L2; each tile clears its shared table
 // first and merges it into the global table at the end. With a tile list
 // (rows partitioned chunk by chunk), tile t is the row range tiles[t] =
 // (first row, rows), *ntiles of them, listed partition by partition.
 constexpr int64_t kPartTileRows = int64_t(1) << 16;
+// Integer sums in a tile build keep a slot's count and its low word's carries
+// in the two 16-bit halves of one shared word (one atomic instead of two), so
+// a tile has at most 65532 rows (a multiple of 4).
+constexpr int64_t kTileRowsMax = 65532;
 
 template <int DT, bool MM, bool VEC, int QPI = 1, bool HOME = false>
 __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
@@ -807,9 +830,9 @@ __global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned l
     b.head = min((int64_t)((-r0) & 3), rows);  // rows before the next 16-byte boundary of the keys
     st.clear(a.smem_slots);
     __syncthreads();
-    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI, HOME>(b, st, threadIdx.x, blockDim.x));
+    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI, HOME, true>(b, st, threadIdx.x, blockDim.x));
     __syncthreads();
-    flush_smem<DT, MM>(b, st);
+    flush_smem<DT, MM, true>(b, st);
     __syncthreads();
   }
   report_counts(a, s_cnt);
