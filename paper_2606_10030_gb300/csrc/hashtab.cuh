@@ -485,6 +485,34 @@ __device__ __forceinline__ Partial4<DT> partial_of(const typename GV<DT>::T (&v)
 
 template <int DT, bool MM>
 __device__ __forceinline__ void warp_reduce_partial(Partial4<DT>& p) {
+  if (DT == AGG_I32 || DT == AGG_U32 || DT == AGG_I64) {
+    // integers: warp reductions of 32-bit words. The sum mod 2^64 from the
+    // low word's two 16-bit halves (each total below 2^21) and the high word
+    // (mod 2^32); a 64-bit minimum from the high words' minimum, then the low
+    // words of the lanes holding it (likewise the maximum).
+    constexpr unsigned kAll = 0xffffffffu;
+    p.cnt = __reduce_add_sync(kAll, p.cnt);
+    const uint32_t lo = (uint32_t)p.isum;
+    const uint32_t s0 = __reduce_add_sync(kAll, lo & 0xFFFFu);
+    const uint32_t s1 = __reduce_add_sync(kAll, lo >> 16);
+    const uint32_t sh = __reduce_add_sync(kAll, (uint32_t)(p.isum >> 32));
+    p.isum = ((unsigned long long)sh << 32) + ((unsigned long long)s1 << 16) + (unsigned long long)s0;
+    if (MM) {
+      if (sizeof(p.mn) == 4) {
+        p.mn = __reduce_min_sync(kAll, (uint32_t)p.mn);
+        p.mx = __reduce_max_sync(kAll, (uint32_t)p.mx);
+      } else {
+        const uint64_t mn = (uint64_t)p.mn, mx = (uint64_t)p.mx;
+        const uint32_t mnh = __reduce_min_sync(kAll, (uint32_t)(mn >> 32));
+        const uint32_t mnl = __reduce_min_sync(kAll, (uint32_t)(mn >> 32) == mnh ? (uint32_t)mn : 0xFFFFFFFFu);
+        const uint32_t mxh = __reduce_max_sync(kAll, (uint32_t)(mx >> 32));
+        const uint32_t mxl = __reduce_max_sync(kAll, (uint32_t)(mx >> 32) == mxh ? (uint32_t)mx : 0u);
+        p.mn = (typename SImg<DT>::U)(((uint64_t)mnh << 32) | mnl);
+        p.mx = (typename SImg<DT>::U)(((uint64_t)mxh << 32) | mxl);
+      }
+    }
+    return;
+  }
 #pragma unroll
   for (int o = 16; o >= 1; o >>= 1) {
     p.cnt += __shfl_xor_sync(0xffffffffu, p.cnt, o);
