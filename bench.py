@@ -587,6 +587,7 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
     time_runs()  # warm-up replays (the first replays after a capture run slower)
     fixed_s, fixed_gpu_ms = time_runs()  # the default 64 Ki-row work items
     tile = plan.tune(2)  # the autotuner's tile axis: 16, 32 or 64 Ki rows
+    time_runs()  # warm-up replays of the re-planned graph
     batch_s, batch_gpu_ms = time_runs()
     plan.free()
     o = agg.options(strat)
