@@ -305,7 +305,8 @@ agg_status agg_groups_to_host(const agg_groups* g, uint32_t* keys, int64_t* coun
                               void* max, double* avg, double* sum_err);
 
 /*
- * Release a result (NULL is allowed). The result's device memory is returned
+ * Release a result (NULL is allowed; result ownership has no counterpart in
+ * the paper, whose aggregation returns one scalar). The result's device memory is returned
  * in stream order on the stream passed to the call that produced it, so the
  * call does not wait for the GPU: that stream must still exist, and work the
  * caller queued on other streams that reads the arrays must be ordered before
@@ -422,7 +423,9 @@ agg_status agg_distinct_estimate(const uint32_t* keys_dev, int64_t n, double* es
 
 /*
  * Batched GROUP BY: many independent queries in one persistent
- * kernel captured in a CUDA graph.
+ * kernel captured in a CUDA graph (the unified framework of Sec. 2.2 schedules
+ * a group of tasks as one unit; here a group of aggregation queries shares one
+ * launch).
  *
  * agg_batch_plan_create sketches every query (one batched launch), picks each
  * query's strategy (query.strategy: AUTO = the rule, LEARNED = the installed

@@ -262,3 +262,24 @@ def test_items_per_thread_and_tile_rows(items, tile):
     for strategy, part in ((agg.AGG_STRAT_SMEM, 1), (agg.AGG_STRAT_SMEM, -1), (agg.AGG_STRAT_GLOBAL, -1)):
         res, _ = run(keys, vals, strategy, items_per_thread=items, tile_rows=tile, partition=part)
         check_groups(res, keys, vals)
+
+
+@pytest.mark.parametrize("dt", ["i32", "i64"])
+@pytest.mark.parametrize("pattern", ["all_carry", "negative", "mixed"])
+@pytest.mark.parametrize("tile", [0, 65536])
+def test_tile_count_word_at_its_limits(dt, pattern, tile):
+    """Tile builds keep a slot's count and its low word's carries in one 32-bit word: tiles of the
+    largest size (65536 asks for 65532 rows) where one key takes every row and nearly every add
+    carries, with values whose high words are zero, all ones (negative), or both."""
+    n = 3 * 65536 + 11
+    rng = np.random.default_rng(7)
+    keys = np.where(rng.random(n) < 0.97, 12345, rng.integers(0, 2 ** 32, n)).astype(np.uint32)
+    if pattern == "all_carry":
+        v = np.full(n, 0xFFFFFFFF if dt == "i64" else 2 ** 31 - 1, np.int64)
+    elif pattern == "negative":
+        v = -rng.integers(1, 2 ** 31, n).astype(np.int64)
+    else:
+        v = rng.integers(-(2 ** 31), 2 ** 31 if dt == "i32" else 2 ** 40, n).astype(np.int64)
+    vals = v.astype(np.int32 if dt == "i32" else np.int64)
+    res, meta = run(keys, vals, agg.AGG_STRAT_SMEM, partition=1, tile_rows=tile)
+    check_groups(res, keys, vals)

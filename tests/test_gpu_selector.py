@@ -143,3 +143,17 @@ def test_trained_selector_gain_over_the_method_without_it():
     fixed_best = min(ev[k]["total_ms"] for k in ("smem", "global", "sort"))
     assert ev["learned"]["total_ms"] <= fixed_best
     assert ev["learned"]["mean_regret"] <= ev["rule"]["mean_regret"] + 0.05
+
+
+def test_shipped_selector_beats_the_rule_on_fresh_distributions():
+    """The installed network (trained on 20000 autotuner-labelled distributions) on 96 distributions
+    it never saw (another seed; 2^16-2^24 rows): its choices cost no more in total than the best
+    fixed strategy, and its mean regret is below the AUTO rule's."""
+    params, mean, std = selector.load(selector.DEFAULT_WEIGHTS)
+    qs = selector.sample_queries(96, seed=424242, log2_rows=(16, 24))
+    X, y, T, ops = selector.label(qs)
+    ev = selector.evaluate(params, mean, std, X, T, ops)
+    print("shipped selector on fresh distributions", ev)
+    fixed_best = min(ev[k]["total_ms"] for k in ("smem", "global", "sort"))
+    assert ev["learned"]["total_ms"] <= fixed_best
+    assert ev["learned"]["mean_regret"] < ev["rule"]["mean_regret"]
