@@ -822,8 +822,18 @@ constexpr int64_t kPartTileRows = int64_t(1) << 16;
 // a tile has at most 65532 rows (a multiple of 4).
 constexpr int64_t kTileRowsMax = 65532;
 
+// Blocks a SM the tile build is compiled for: float32 sums without MIN/MAX
+// (a 4096-slot table of 16-byte slots, compare-and-swap loops for the float
+// atomics) run three, at 40 registers (the 2^28-row Zipf build: 4.15 -> 3.41
+// ms); the integer and MIN/MAX builds keep two at 64 registers (three cost
+// them 40 %).
+template <int DT, bool MM>
+struct TileBlocks {
+  static constexpr int kValue = DT == AGG_F32 && !MM ? 3 : 2;
+};
+
 template <int DT, bool MM, bool VEC, int QPI = 1, bool HOME = false>
-__global__ void __launch_bounds__(512, 2) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
+__global__ void __launch_bounds__(512, TileBlocks<DT, MM>::kValue) gb_build_tiles(BuildArgs a, unsigned long long* next_tile,
                                                         int64_t tile_rows, const longlong2* tiles,
                                                         const unsigned long long* ntiles) {
   using T = typename GV<DT>::T;
