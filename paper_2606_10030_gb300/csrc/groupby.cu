@@ -454,7 +454,7 @@ class HashRun {
         int bps = occupancy(pick_tiles(vdt_, mm_, plan_.qpi, false), threads, smem);
         if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
         int64_t grid = (int64_t)di.sm_count * bps;
-        // tiles of up to 64 Ki rows (32 Ki after two levels), smaller (down to
+        // tiles of up to 65532 rows (32 Ki after two levels), smaller (down to
         // 4 Ki) when the column would give each resident block fewer than two
         int64_t tile_rows = plan_.tile_rows;
         if (tile_rows == 0) {
@@ -1052,10 +1052,10 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     const double table_b = (double)(c.plan.slots + 2) * gslot_bytes(ops_minmax(ops));
     room = cudaMemGetInfo(&free_b, &total_b) == cudaSuccess && (double)free_b > 4.0 * col_bytes + 2.0 * table_b;
   }
-  // Streamed: a one-level hash partition of each chunk as it arrives
-  // (overlapped with the copies of the next chunks) into its own region of a
-  // column-sized buffer, a HyperLogLog count over every chunk, then one build
-  // over the pieces with the table sized from that count.
+  // Streamed: a one-level hash partition of each chunk as it arrives into its
+  // own region of a column-sized buffer and a build of its pieces, both
+  // overlapped with the copies of the next chunks; a HyperLogLog count over
+  // every chunk sizes the table again if the first chunk's count undersized it.
   const bool streamed = room && hll_plan > 0.0 && c.strategy == AGG_STRAT_SMEM && c.plan.partition_passes == 1;
   if (!whole && !streamed && c.plan.partition && n > chunk) whole = room;
   if (streamed) {
@@ -1075,48 +1075,70 @@ static agg_status groupby_host_impl(const uint32_t* keys, const void* vals, int6
     unsigned long long* ntiles = (unsigned long long*)(x + starts_b + tiles_b);
     void* ptmp = x + starts_b + tiles_b + 256;
     uint32_t* regs = (uint32_t*)(x + starts_b + tiles_b + 256 + ((partition_tmp_bytes() + 255) & ~size_t(255)));
+    // Each chunk's pieces are built as soon as it is partitioned (overlapped
+    // with the copies of the next chunks), into a table sized from the first
+    // chunk's count with room for twice as many keys. A table that fills is
+    // rebuilt after the last chunk over every piece, sized from the count of
+    // all chunks.
+    HashPlan plan = c.plan;
+    plan.slots = o.table_slots ? o.table_slots : table_slots_for(feat, n, 2.0 * hll_plan);
+    uint64_t seen = 0, failed = 0;
     {
-      PhaseTimer pt(AGG_PHASE_SORT, s);
+      HashRun early(vdt, ops, plan, s);
+      st = early.init();
+      if (st != AGG_OK) return st;
       for (int64_t k = 0; k < nchunks; ++k) {
         st = ensure_copied(k + GbPipe::kRing - 1);
         if (st != AGG_OK) return st;
         const int b = (int)(k % GbPipe::kRing);
         cudaStreamWaitEvent(s, pipe->ready[b], 0);
         const int64_t rows = std::min<int64_t>(chunk, n - k * chunk);
-        st = hll_add_chunk(kbuf(b), rows, regs, k == 0, s);
-        if (st == AGG_OK)
-          st = es == 4 ? partition_hashed<uint32_t>(kbuf(b), (const uint32_t*)vbuf(b), fk, (uint32_t*)fv, rows, ptmp,
-                                                    s, k * chunk, starts + k * 257)
-                       : partition_hashed<uint64_t>(kbuf(b), (const uint64_t*)vbuf(b), fk, (uint64_t*)fv, rows, ptmp,
-                                                    s, k * chunk, starts + k * 257);
+        {
+          PhaseTimer pt(AGG_PHASE_SORT, s);
+          st = hll_add_chunk(kbuf(b), rows, regs, k == 0, s);
+          if (st == AGG_OK)
+            st = es == 4 ? partition_hashed<uint32_t>(kbuf(b), (const uint32_t*)vbuf(b), fk, (uint32_t*)fv, rows,
+                                                      ptmp, s, k * chunk, starts + k * 257)
+                         : partition_hashed<uint64_t>(kbuf(b), (const uint64_t*)vbuf(b), fk, (uint64_t*)fv, rows,
+                                                      ptmp, s, k * chunk, starts + k * 257);
+        }
         cudaEventRecord(pipe->freed[b], s);
+        if (st == AGG_OK) st = early.build_pieces(fk, fv, n, starts + k * 257, 1, tiles, ntiles);
         if (st != AGG_OK) return st;
       }
+      st = early.finish(&g);
+      seen = early.rows_seen();
+      failed = early.rows_failed();
     }
-    double hll_all = 0.0;
-    st = hll_read(regs, s, &hll_all);
-    if (st != AGG_OK) return st;
-    HashPlan plan = c.plan;
-    plan.slots = o.table_slots ? o.table_slots : table_slots_for(feat, n, hll_all);
-    int retries = 0;
-    for (;;) {
-      uint64_t seen = 0, failed = 0;
-      {
-        HashRun run(vdt, ops, plan, s);
-        st = run.init();
-        if (st == AGG_OK) st = run.build_pieces(fk, fv, n, starts, (int)nchunks, tiles, ntiles);
-        if (st == AGG_OK) st = run.finish(&g);
-        seen = run.rows_seen();
-        failed = run.rows_failed();
+    if (st == AGG_OK) {
+      g->retries = 0;
+    } else if (st != AGG_ERR_TABLE_FULL) {
+      return st;
+    } else {
+      double hll_all = 0.0;
+      st = hll_read(regs, s, &hll_all);
+      if (st != AGG_OK) return st;
+      const int64_t grown = regrow_slots(plan.slots, n, seen, failed);
+      plan.slots = o.table_slots ? grown : std::max(table_slots_for(feat, n, hll_all), grown);
+      int retries = 1;
+      for (;;) {
+        {
+          HashRun run(vdt, ops, plan, s);
+          st = run.init();
+          if (st == AGG_OK) st = run.build_pieces(fk, fv, n, starts, (int)nchunks, tiles, ntiles);
+          if (st == AGG_OK) st = run.finish(&g);
+          seen = run.rows_seen();
+          failed = run.rows_failed();
+        }
+        if (st == AGG_OK) {
+          g->retries = retries;
+          break;
+        }
+        if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
+          return st;
+        ++retries;
+        plan.slots = regrow_slots(plan.slots, n, seen, failed);
       }
-      if (st == AGG_OK) {
-        g->retries = retries;
-        break;
-      }
-      if (st != AGG_ERR_TABLE_FULL || plan.slots >= (int64_t(1) << 31) || plan.slots >= 4 * std::max<int64_t>(n, 1))
-        return st;
-      ++retries;
-      plan.slots = regrow_slots(plan.slots, n, seen, failed);
     }
   } else if (whole) {
     void* full = nullptr;

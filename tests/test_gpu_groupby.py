@@ -283,3 +283,24 @@ def test_tile_count_word_at_its_limits(dt, pattern, tile):
     vals = v.astype(np.int32 if dt == "i32" else np.int64)
     res, meta = run(keys, vals, agg.AGG_STRAT_SMEM, partition=1, tile_rows=tile)
     check_groups(res, keys, vals)
+
+
+@pytest.mark.parametrize("later", ["same_keys", "new_keys"])
+def test_host_fed_streamed_builds(later):
+    """A host-fed column of two 2^23-row chunks whose first chunk recurs over 2^16 keys: each chunk is
+    partitioned and built as it arrives into a table sized from the first chunk's count. With the
+    same keys later the table holds; with 2^20 new keys in the second chunk it fills and the column
+    is rebuilt over every piece from the count of all chunks. Both match the oracle."""
+    n0, n1 = 1 << 23, 1 << 22
+    k0 = dg.keys_uniform(n0, 1 << 16, 31)
+    k1 = dg.keys_uniform(n1, 1 << 16, 31) if later == "same_keys" else \
+        (dg.keys_uniform(n1, 1 << 20, 32) ^ np.uint32(0x9E3779B9))
+    keys = np.concatenate([k0, k1]).astype(np.uint32)
+    vals = dg.values("i64", n0 + n1, 33)
+    g = agg.agg_groupby_host(torch.from_numpy(keys).pin_memory(), torch.from_numpy(vals).pin_memory(),
+                             agg.AGG_ALL, agg.options(agg.AGG_STRAT_SMEM))
+    res = g.to_host()
+    retries = g.retries
+    g.free()
+    check_groups(res, keys, vals)
+    assert (retries > 0) == (later == "new_keys")
