@@ -805,11 +805,23 @@ def kernel_traffic(kernel: str, workload: str):
         return None
     if not d:
         return None
-    import hashlib
     src = os.path.join(ROOT, d["source"])
-    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != d["source_sha256"]:
+    if not os.path.exists(src) or code_sha256(src) != d["code_sha256"]:
         return None
     return d["dram_bytes_per_launch"]
+
+
+def code_sha256(path: str) -> str:
+    """sha256 of a source file's code: // comments, trailing blanks and empty lines removed (a
+    comment edit does not change the kernel the recorded counters describe)."""
+    import hashlib
+    import re
+    lines = []
+    for line in open(path, encoding="utf-8").read().splitlines():
+        line = re.sub(r"//.*$", "", line).rstrip()
+        if line:
+            lines.append(line)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
 
 
 def run_ours(args):

@@ -139,6 +139,11 @@ __device__ __forceinline__ void g_add_row(GSlot<MM>& s, typename GV<DT>::T v) {
 //   MIN/MAX   an adjacent (min, max) pair of order-preserving images (32-bit
 //             for 4-byte values); an atomic is issued only when the value
 //             improves the current extreme.
+// In tile builds (at most 65532 rows per tile) integer sums count the low
+// word's carries in the high half of the count word instead (one atomic adds
+// the row and its carry; the high word is updated only for a nonzero high
+// part), and lightly loaded tables are probed first at the key's exact home
+// slot (4 bytes) before the bucket.
 // Rows are handled in batches: all lookups first, then all count updates,
 // all sum updates and all min/max updates, so that shared-memory latencies
 // overlap instead of forming one dependent chain per row.
