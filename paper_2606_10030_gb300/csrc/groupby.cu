@@ -149,6 +149,14 @@ static size_t stab_bytes_dt(int dt, bool mm, int S) {
   return 0;
 }
 
+static size_t tile_smem_bytes_dt(int dt, bool mm, int S) {
+#define AGG_SB(D) \
+  case D: return mm ? tile_smem_bytes<D, true>(S) : tile_smem_bytes<D, false>(S);
+  switch (dt) { AGG_SB(AGG_I32) AGG_SB(AGG_I64) AGG_SB(AGG_U32) AGG_SB(AGG_F32) AGG_SB(AGG_F64) }
+#undef AGG_SB
+  return 0;
+}
+
 // Resident blocks per SM of a kernel for (threads, dynamic smem), cached.
 static int occupancy(KernelPtr fn, int threads, size_t smem) {
   static std::mutex mu;
@@ -448,7 +456,7 @@ class HashRun {
           set_error("partitioned build: %s", cudaGetErrorString(e));
           return AGG_ERR_CUDA;
         }
-        const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
+        const size_t smem = tile_smem_bytes_dt(vdt_, mm_, plan_.smem_slots);
         const int threads = plan_.threads;
         // both variants have the same resources: occupancy from either
         int bps = occupancy(pick_tiles(vdt_, mm_, plan_.qpi, false), threads, smem);
@@ -517,7 +525,7 @@ class HashRun {
     unsigned long long* next_tile = (unsigned long long*)((char*)mem_ + status_off_ + 128);
     AGG_CUDA_TRY(cudaMemsetAsync(next_tile, 0, 8, s_));
     KernelPtr bk = pick_tiles(vdt_, mm_, plan_.qpi, tiles_lightly_loaded(plan_.est_keys, n, 1, 1, plan_.smem_slots));
-    const size_t smem = stab_bytes_dt(vdt_, mm_, plan_.smem_slots);
+    const size_t smem = tile_smem_bytes_dt(vdt_, mm_, plan_.smem_slots);
     int bps = occupancy(bk, plan_.threads, smem);
     if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;
     const int64_t grid = (int64_t)device_info().sm_count * bps;

@@ -84,6 +84,10 @@ struct BuildArgs {
   unsigned long long* progress;  // [0] rows gone through, [1] rows that found no slot, counted
                                  // when a full table stopped the build (or null)
   uint32_t* block_fails;         // this block's count of rows that found no slot (shared memory, or null)
+  // int64 MIN/MAX in tile builds: the low words of the images whose high word
+  // is the tile's (one (min, max) u32 pair a slot, shared memory), or null
+  uint32_t* mm32 = nullptr;
+  uint32_t tile_hi = 0;
 };
 
 // Global slot of key (insert if absent); -1 if no slot within the probe bound.
@@ -205,8 +209,14 @@ struct STab {
 template <int DT, bool MM>
 __host__ __device__ inline size_t stab_bytes(int S) {
   const size_t img = (DT == AGG_I64 || DT == AGG_F64) ? 8 : 4;
-  return (size_t)(S + 1) * 8 + 16 + (MM ? 2 * img * (S + 1) + 16 : 0) + (size_t)(S + 4) * 4 + (size_t)(S + 1) * 4 +
-         16;
+  return ((size_t)(S + 1) * 8 + 16 + (MM ? 2 * img * (S + 1) + 16 : 0) + (size_t)(S + 4) * 4 +
+          (size_t)(S + 1) * 4 + 16 + 15) & ~size_t(15);
+}
+// Shared memory of a tile build: the table, and for int64 MIN/MAX the 32-bit
+// (min, max) pairs after it.
+template <int DT, bool MM>
+__host__ __device__ inline size_t tile_smem_bytes(int S) {
+  return stab_bytes<DT, MM>(S) + (MM && DT == AGG_I64 ? (size_t)(S + 1) * 8 : 0);
 }
 
 constexpr int kSmemBuckets = 4;  // buckets of 4 slots probed before a row spills
@@ -407,7 +417,27 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
       }
     }
   }
-  if (MM) {
+  if (MM && PACK && DT == AGG_I64) {
+    // tile builds: a value whose image shares the tile's high word is checked
+    // and applied on the 32-bit (min, max) pair of its low words (8 bytes
+    // instead of 16, native 32-bit atomics); others on the 64-bit pair
+#pragma unroll
+    for (int r = 0; r < N; ++r) {
+      if (j[r] >= 0) {
+        const U m = s_img<DT>(val[r]);
+        if ((uint32_t)((uint64_t)m >> 32) == a.tile_hi) {
+          const uint32_t ml = (uint32_t)m;
+          const uint2 q = lds_v2(&a.mm32[2 * j[r]]);
+          if (ml < q.x) atomicMin(&a.mm32[2 * j[r]], ml);
+          if (ml > q.y) atomicMax(&a.mm32[2 * j[r] + 1], ml);
+        } else {
+          const ulonglong2 q = lds_v2_64(&st.mm[2 * j[r]]);
+          if (m < (U)q.x) atomicMin(&st.mm[2 * j[r]], m);
+          if (m > (U)q.y) atomicMax(&st.mm[2 * j[r] + 1], m);
+        }
+      }
+    }
+  } else if (MM) {
     U cur_mn[N], cur_mx[N];
 #pragma unroll
     for (int r = 0; r < N; ++r) {
@@ -541,7 +571,8 @@ __device__ __forceinline__ void warp_reduce_partial(Partial4<DT>& p) {
 
 // Apply a partial aggregate to a shared slot (same encodings as s_add via fold_batch).
 template <int DT, bool MM, bool PACK = false>
-__device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, const Partial4<DT>& p) {
+__device__ __forceinline__ void s_add_partial(const BuildArgs& a, const STab<DT, MM>& st, int j,
+                                              const Partial4<DT>& p) {
   using U = typename SImg<DT>::U;
   constexpr bool kPack = PACK && DT != AGG_F32 && DT != AGG_F64;
   if (!kPack) atomicAdd(&st.cnt[j], p.cnt);
@@ -566,7 +597,12 @@ __device__ __forceinline__ void s_add_partial(const STab<DT, MM>& st, int j, con
       if (hi) atomicAdd(&w[1], hi);
     }
   }
-  if (MM) {
+  if (MM && PACK && DT == AGG_I64 && (uint32_t)((uint64_t)p.mn >> 32) == a.tile_hi &&
+      (uint32_t)((uint64_t)p.mx >> 32) == a.tile_hi) {  // both bounds on the 32-bit pair (see fold_batch)
+    const uint32_t mnl = (uint32_t)p.mn, mxl = (uint32_t)p.mx;
+    if (mnl < *(volatile uint32_t*)&a.mm32[2 * j]) atomicMin(&a.mm32[2 * j], mnl);
+    if (mxl > *(volatile uint32_t*)&a.mm32[2 * j + 1]) atomicMax(&a.mm32[2 * j + 1], mxl);
+  } else if (MM) {
     if (p.mn < *(volatile U*)&st.mm[2 * j]) atomicMin(&st.mm[2 * j], p.mn);
     if (p.mx > *(volatile U*)&st.mm[2 * j + 1]) atomicMax(&st.mm[2 * j + 1], p.mx);
   }
@@ -605,7 +641,7 @@ __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT,
     int j = s_find_home<DT, MM, HOME>(st, a.smem_slots, key);
     if (j < 0) j = s_lookup<DT, MM, HOME>(st, a.smem_slots, a.smem_cap, key);
     if (j >= 0) {
-      s_add_partial<DT, MM, PACK>(st, j, p);
+      s_add_partial<DT, MM, PACK>(a, st, j, p);
       return;
     }
   }
@@ -784,7 +820,15 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     }
     if (MM) {
       GSlot<true>& gw = (GSlot<true>&)gs;
-      const uint64_t mn = g_img_of<DT>(st.mm[2 * j]), mx = g_img_of<DT>(st.mm[2 * j + 1]);
+      uint64_t mn = g_img_of<DT>(st.mm[2 * j]), mx = g_img_of<DT>(st.mm[2 * j + 1]);
+      if (PACK && DT == AGG_I64) {
+        // the 32-bit pair took at least one update iff its min is at most its max
+        const uint32_t lo = a.mm32[2 * j], hi = a.mm32[2 * j + 1];
+        if (lo <= hi) {
+          mn = min(mn, ((uint64_t)a.tile_hi << 32) | lo);
+          mx = max(mx, ((uint64_t)a.tile_hi << 32) | hi);
+        }
+      }
       if (~mn > *(volatile unsigned long long*)&gw.minc) atomicMax(&gw.minc, (unsigned long long)~mn);
       if (mx > *(volatile unsigned long long*)&gw.mx) atomicMax(&gw.mx, (unsigned long long)mx);
     }
@@ -849,6 +893,9 @@ __global__ void __launch_bounds__(512, TileBlocks<DT, MM>::kValue) gb_build_tile
   a.block_fails = &s_cnt.fails;
   STab<DT, MM> st;
   st.carve(smem, a.smem_slots);
+  constexpr bool kMM32 = MM && DT == AGG_I64;
+  __shared__ uint32_t s_hi;
+  if (kMM32) a.mm32 = (uint32_t*)(smem + stab_bytes<DT, MM>(a.smem_slots));  // after the table (16-byte aligned)
   for (;;) {
     // no new tile once the table is full (the build is redone with a larger one)
     if (threadIdx.x == 0) s_t = *(volatile int*)a.status ? -1 : (int64_t)atomicAdd(next_tile, 1ull);
@@ -872,7 +919,15 @@ __global__ void __launch_bounds__(512, TileBlocks<DT, MM>::kValue) gb_build_tile
     b.n = rows;
     b.head = min((int64_t)((-r0) & 3), rows);  // rows before the next 16-byte boundary of the keys
     st.clear(a.smem_slots);
+    if (kMM32) {  // the tile's high word: that of its first row's image
+      for (int i = threadIdx.x; i <= a.smem_slots; i += blockDim.x) {
+        b.mm32[2 * i] = 0xFFFFFFFFu;
+        b.mm32[2 * i + 1] = 0u;
+      }
+      if (threadIdx.x == 0) s_hi = (uint32_t)((uint64_t)s_img<DT>(((const T*)b.vals)[0]) >> 32);
+    }
     __syncthreads();
+    if (kMM32) b.tile_hi = s_hi;
     atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI, HOME, true>(b, st, threadIdx.x, blockDim.x));
     __syncthreads();
     flush_smem<DT, MM, true>(b, st);
