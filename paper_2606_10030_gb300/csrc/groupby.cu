@@ -387,7 +387,7 @@ class HashRun {
     a.progress = progress_;
     if (plan_.partition && n >= kPartTileRows) return build_partitioned(a, use_smem);
     KernelPtr bk = pick_build(vdt_, mm_, use_smem, vec, plan_.multi_keys, plan_.qpi);
-    const size_t smem = use_smem ? stab_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;
+    const size_t smem = use_smem ? tile_smem_bytes_dt(vdt_, mm_, plan_.smem_slots) : 0;  // table + 32-bit pairs
     const int threads = plan_.threads;
     int bps = occupancy(bk, threads, smem);
     if (plan_.blocks_per_sm > 0 && plan_.blocks_per_sm < bps) bps = plan_.blocks_per_sm;

@@ -356,7 +356,7 @@ __device__ __forceinline__ void g_row(const BuildArgs& a, uint32_t key, typename
 }
 
 // Fold a batch of N rows (valid[r] false = skip).
-template <int DT, bool MM, bool SMEM, int N, bool HOME = false, bool PACK = false>
+template <int DT, bool MM, bool SMEM, int N, bool HOME = false, bool PACK = false, bool M32 = false>
 __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM>& st, const uint32_t (&key)[N],
                                            const typename GV<DT>::T (&val)[N], const bool (&valid)[N]) {
   using T = typename GV<DT>::T;
@@ -417,8 +417,8 @@ __device__ __forceinline__ void fold_batch(const BuildArgs& a, const STab<DT, MM
       }
     }
   }
-  if (MM && PACK && DT == AGG_I64) {
-    // tile builds: a value whose image shares the tile's high word is checked
+  if (MM && M32 && DT == AGG_I64) {
+    // a value whose image shares the tile's (block's) high word is checked
     // and applied on the 32-bit (min, max) pair of its low words (8 bytes
     // instead of 16, native 32-bit atomics); others on the 64-bit pair
 #pragma unroll
@@ -570,7 +570,7 @@ __device__ __forceinline__ void warp_reduce_partial(Partial4<DT>& p) {
 }
 
 // Apply a partial aggregate to a shared slot (same encodings as s_add via fold_batch).
-template <int DT, bool MM, bool PACK = false>
+template <int DT, bool MM, bool PACK = false, bool M32 = false>
 __device__ __forceinline__ void s_add_partial(const BuildArgs& a, const STab<DT, MM>& st, int j,
                                               const Partial4<DT>& p) {
   using U = typename SImg<DT>::U;
@@ -597,7 +597,7 @@ __device__ __forceinline__ void s_add_partial(const BuildArgs& a, const STab<DT,
       if (hi) atomicAdd(&w[1], hi);
     }
   }
-  if (MM && PACK && DT == AGG_I64 && (uint32_t)((uint64_t)p.mn >> 32) == a.tile_hi &&
+  if (MM && M32 && DT == AGG_I64 && (uint32_t)((uint64_t)p.mn >> 32) == a.tile_hi &&
       (uint32_t)((uint64_t)p.mx >> 32) == a.tile_hi) {  // both bounds on the 32-bit pair (see fold_batch)
     const uint32_t mnl = (uint32_t)p.mn, mxl = (uint32_t)p.mx;
     if (mnl < *(volatile uint32_t*)&a.mm32[2 * j]) atomicMin(&a.mm32[2 * j], mnl);
@@ -631,7 +631,7 @@ __device__ __forceinline__ void g_add_partial(const BuildArgs& a, uint32_t key, 
 
 // The warp reduces the rows marked in take (a 4-bit mask per lane; all of
 // one key) and lane 0 folds the partial into the tables.
-template <int DT, bool MM, bool SMEM, bool HOME = false, bool PACK = false>
+template <int DT, bool MM, bool SMEM, bool HOME = false, bool PACK = false, bool M32 = false>
 __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT, MM>& st, uint32_t key,
                                               const typename GV<DT>::T (&v)[4], uint32_t take) {
   Partial4<DT> p = partial_of<DT, MM>(v, take);
@@ -641,7 +641,7 @@ __device__ __forceinline__ void fold_warp_key(const BuildArgs& a, const STab<DT,
     int j = s_find_home<DT, MM, HOME>(st, a.smem_slots, key);
     if (j < 0) j = s_lookup<DT, MM, HOME>(st, a.smem_slots, a.smem_cap, key);
     if (j >= 0) {
-      s_add_partial<DT, MM, PACK>(a, st, j, p);
+      s_add_partial<DT, MM, PACK, M32>(a, st, j, p);
       return;
     }
   }
@@ -690,7 +690,7 @@ __device__ __forceinline__ void report_counts(const BuildArgs& a, const BlockCou
 // every row takes the per-row path (for columns whose sketch shows no
 // frequent key: the warp then never waits for its slowest lane).
 template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI = true, int QPI = 1, bool HOME = false,
-          bool PACK = false>
+          bool PACK = false, bool M32 = false>
 __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT, MM>& st, int64_t tid,
                                                int64_t nthreads) {
   constexpr int kQuadsPerIter = QPI;
@@ -707,11 +707,11 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
       ok1[0] = tid < a.head;
       k1[0] = ok1[0] ? keys[tid] : 0u;
       v1[0] = ok1[0] ? vals[tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME, PACK, M32>(a, st, k1, v1, ok1);
       ok1[0] = tid < a.n - tail0;
       k1[0] = ok1[0] ? keys[tail0 + tid] : 0u;
       v1[0] = ok1[0] ? vals[tail0 + tid] : T(0);
-      fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME, PACK, M32>(a, st, k1, v1, ok1);
     }
     const uint4* kq = (const uint4*)(keys + a.head);
     const uint4* vq = (const uint4*)(vals + a.head);
@@ -753,7 +753,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
 #pragma unroll
             for (int r = 0; r < 4; ++r) take |= (((rem >> r) & 1u) && key[r] == k0) ? (1u << r) : 0u;
             if (__reduce_add_sync(0xffffffffu, (unsigned)__popc(take)) < (unsigned)kDominantRows) break;
-            fold_warp_key<DT, MM, SMEM, HOME, PACK>(a, st, k0, val, take);
+            fold_warp_key<DT, MM, SMEM, HOME, PACK, M32>(a, st, k0, val, take);
             rem &= ~take;
             if (w + 1 == kKeys) break;
             const uint32_t lanes = __ballot_sync(0xffffffffu, rem != 0u);
@@ -771,7 +771,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
           uint32_t kb[1] = {key[r]};
           T vv[1] = {val[r]};
           bool ok[1] = {((rem >> r) & 1u) != 0u};
-          fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, kb, vv, ok);
+          fold_batch<DT, MM, SMEM, 1, HOME, PACK, M32>(a, st, kb, vv, ok);
         }
       }
       // table full: the build is redone (status read by lane 0, so the whole warp leaves)
@@ -784,7 +784,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
       uint32_t k1[1] = {keys[i]};
       T v1[1] = {vals[i]};
       bool ok1[1] = {true};
-      fold_batch<DT, MM, SMEM, 1, HOME, PACK>(a, st, k1, v1, ok1);
+      fold_batch<DT, MM, SMEM, 1, HOME, PACK, M32>(a, st, k1, v1, ok1);
       if ((++it & 63) == 0 && *(volatile int*)a.status) break;
     }
     return (uint32_t)it;
@@ -792,7 +792,7 @@ __device__ __forceinline__ uint32_t build_rows(const BuildArgs& a, const STab<DT
 }
 
 // Merge a block's shared table into the global table (after a barrier).
-template <int DT, bool MM, bool PACK = false>
+template <int DT, bool MM, bool PACK = false, bool M32 = false>
 __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM>& st) {
   constexpr bool kPack = PACK && DT != AGG_F32 && DT != AGG_F64;
   GSlot<MM>* tab = (GSlot<MM>*)a.table;
@@ -821,7 +821,7 @@ __device__ __forceinline__ void flush_smem(const BuildArgs& a, const STab<DT, MM
     if (MM) {
       GSlot<true>& gw = (GSlot<true>&)gs;
       uint64_t mn = g_img_of<DT>(st.mm[2 * j]), mx = g_img_of<DT>(st.mm[2 * j + 1]);
-      if (PACK && DT == AGG_I64) {
+      if (M32 && DT == AGG_I64) {
         // the 32-bit pair took at least one update iff its min is at most its max
         const uint32_t lo = a.mm32[2 * j], hi = a.mm32[2 * j + 1];
         if (lo <= hi) {
@@ -840,20 +840,36 @@ template <int DT, bool MM, bool SMEM, bool VEC, bool MULTI, int QPI = 1>
 __global__ void __launch_bounds__(512, 2) gb_build(BuildArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ BlockCounts s_cnt;
+  __shared__ uint32_t s_hi;
   if (threadIdx.x == 0) s_cnt = BlockCounts{0u, 0u};
   a.block_fails = &s_cnt.fails;
   STab<DT, MM> st;
+  // int64 MIN/MAX: the 32-bit (min, max) pairs after the table, for values
+  // sharing the high word of one row the block reads first
+  constexpr bool kMM32 = SMEM && MM && DT == AGG_I64;
   if (SMEM) {
     st.carve(smem, a.smem_slots);
     st.clear(a.smem_slots);
   }
+  if (kMM32) {
+    a.mm32 = (uint32_t*)(smem + stab_bytes<DT, MM>(a.smem_slots));
+    for (int i = threadIdx.x; i <= a.smem_slots; i += blockDim.x) {
+      a.mm32[2 * i] = 0xFFFFFFFFu;
+      a.mm32[2 * i + 1] = 0u;
+    }
+    if (threadIdx.x == 0) {
+      const int64_t r = a.n > 0 ? min((int64_t)blockIdx.x * blockDim.x * 4, a.n - 1) : 0;
+      s_hi = a.n > 0 ? (uint32_t)((uint64_t)s_img<DT>(((const typename GV<DT>::T*)a.vals)[r]) >> 32) : 0u;
+    }
+  }
   __syncthreads();
-  const uint32_t seen = build_rows<DT, MM, SMEM, VEC, MULTI, QPI>(
+  if (kMM32) a.tile_hi = s_hi;
+  const uint32_t seen = build_rows<DT, MM, SMEM, VEC, MULTI, QPI, false, false, kMM32>(
       a, st, (int64_t)blockIdx.x * blockDim.x + threadIdx.x, (int64_t)gridDim.x * blockDim.x);
   atomicAdd(&s_cnt.seen, seen);
   if (SMEM) {
     __syncthreads();
-    flush_smem<DT, MM>(a, st);
+    flush_smem<DT, MM, false, kMM32>(a, st);
   }
   __syncthreads();
   report_counts(a, s_cnt);
@@ -928,9 +944,9 @@ __global__ void __launch_bounds__(512, TileBlocks<DT, MM>::kValue) gb_build_tile
     }
     __syncthreads();
     if (kMM32) b.tile_hi = s_hi;
-    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI, HOME, true>(b, st, threadIdx.x, blockDim.x));
+    atomicAdd(&s_cnt.seen, build_rows<DT, MM, true, VEC, true, QPI, HOME, true, kMM32>(b, st, threadIdx.x, blockDim.x));
     __syncthreads();
-    flush_smem<DT, MM, true>(b, st);
+    flush_smem<DT, MM, true, kMM32>(b, st);
     __syncthreads();
   }
   report_counts(a, s_cnt);
