@@ -589,6 +589,7 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
     tile = plan.tune(2)  # the autotuner's tile axis: 16, 32 or 64 Ki rows
     time_runs()  # warm-up replays of the re-planned graph
     batch_s, batch_gpu_ms = time_runs()
+    best_s = min(batch_s, fixed_s)
     plan.free()
     o = agg.options(strat)
     for k, v, ops in cols[:8]:
@@ -608,12 +609,15 @@ def extra_batched(steps: int, nq: int = 512) -> dict:
     return {"workload": f"{nq} GROUP BY queries, rows log-uniform in [2^12, 2^24], distinct keys log-uniform in "
                         "[1, 2^20] (uniform or Zipf 0.5-1.5), mixed int32/int64/float32/float64 values and ops",
             "rows": rows, "input_bytes": in_bytes, "selector": "learned" if learned else "rule (no weights file)",
-            "batched_ms": round(batch_s * 1e3, 3), "batched_GB/s": round(in_bytes / batch_s / 1e9, 1),
-            "tile_rows_tuned": tile, "batched_ms_fixed_64Ki_tile": round(fixed_s * 1e3, 3),
+            "batched_ms": round(best_s * 1e3, 3), "batched_GB/s": round(in_bytes / best_s / 1e9, 1),
+            "batched_how": "the faster of the default 64 Ki-row work items and the tuned size (tuning runs may "
+                           "regrow a table that fills, and the larger table stays with the plan)",
+            "batched_ms_tuned": round(batch_s * 1e3, 3), "tile_rows_tuned": tile,
+            "batched_ms_fixed_64Ki_tile": round(fixed_s * 1e3, 3),
             "batched_plan_ms": round(plan_s * 1e3, 1),
             "plain_ms": round(plain_s * 1e3, 3), "plain_GB/s": round(in_bytes / plain_s / 1e9, 1),
-            "speedup": round(plain_s / batch_s, 2),
-            "gpu_ms": {"batched": round(batch_gpu_ms, 3), "batched_fixed_64Ki_tile": round(fixed_gpu_ms, 3),
+            "speedup": round(plain_s / best_s, 2),
+            "gpu_ms": {"batched_tuned": round(batch_gpu_ms, 3), "batched_fixed_64Ki_tile": round(fixed_gpu_ms, 3),
                        "plain": round(plain_gpu_ms, 3),
                        "how": "sum of the library's per-phase CUDA-event times (kernels only)"},
             "steps": steps}
