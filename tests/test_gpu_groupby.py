@@ -304,3 +304,38 @@ def test_host_fed_streamed_builds(later):
     g.free()
     check_groups(res, keys, vals)
     assert (retries > 0) == (later == "new_keys")
+
+
+@pytest.mark.parametrize("partition", [-1, 1])
+@pytest.mark.parametrize("spread", ["two_words", "wide", "one_word"])
+def test_int64_min_max_word_pairs(partition, spread):
+    """Int64 MIN/MAX keep values that share the high word of a row the block (or tile) read first on
+    32-bit (min, max) pairs and the others on 64-bit pairs, merged at the flush: values over two high
+    words (signs mixed), over many, and over one, in the plain and the partitioned build."""
+    n = (1 << 22) + 13
+    rng = np.random.default_rng(41)
+    keys = dg.keys_uniform(n, 1024, 41)
+    if spread == "two_words":
+        vals = rng.integers(-(2 ** 31), 2 ** 31, n).astype(np.int64)
+    elif spread == "wide":
+        vals = rng.integers(-(2 ** 62), 2 ** 62, n).astype(np.int64)
+    else:
+        vals = rng.integers(0, 2 ** 32, n).astype(np.int64)
+        vals[::997] = -1 - vals[::997]  # a few rows on another high word
+    res, _ = run(keys, vals, agg.AGG_STRAT_SMEM, partition=partition)
+    check_groups(res, keys, vals)
+
+
+def test_host_fed_streamed_build_with_a_small_table():
+    """A host-fed column whose chunk-by-chunk build is given too small a table (agg_options.table_slots)
+    fills it; the rebuild over every piece regrows the table and matches the oracle."""
+    n = (1 << 23) + (1 << 21)
+    keys = dg.keys_uniform(n, 1 << 16, 51)
+    vals = dg.values("i64", n, 52)
+    g = agg.agg_groupby_host(torch.from_numpy(keys).pin_memory(), torch.from_numpy(vals).pin_memory(),
+                             agg.AGG_ALL, agg.options(agg.AGG_STRAT_SMEM, table_slots=4096))
+    res = g.to_host()
+    retries = g.retries
+    g.free()
+    check_groups(res, keys, vals)
+    assert retries > 0
