@@ -197,7 +197,9 @@ typedef struct agg_options {
   int32_t smem_slots;      /* shared-memory table slots (power of two, <= 8192); 0 = from the sketch */
   int64_t table_slots;     /* global table slots (power of two); 0 = from the sketch */
   uint64_t sample_offset;  /* offset of the strided key sample (pass a seeded draw) */
-  int32_t items_per_thread;/* rows a thread folds per iteration of the build's vector loop: 4 or 8; 0 = 4 */
+  int32_t items_per_thread;/* rows a thread folds per iteration of the build's vector loop: 4 or 8; 0 = 8
+                              for the unpartitioned shared-memory build of an integer column without
+                              frequent keys, else 4 */
   int32_t partition;       /* hash-partition the rows before a hash build: 0 = automatic (when the
                               shared tables would spill or the global table exceeds half of L2; two
                               levels above ~600k distinct keys), 1 = one level (256 partitions),
