@@ -100,12 +100,14 @@ struct Fix128 {
   uint64_t lo, hi;
   uint32_t nneg;  // negative rows added on the fast path as ~v, each still owing +1
   int E;
+  int base;       // E - kFixGuard: a row of exponent field e sits e - base bits up
   double special;
   __device__ void init() {
     lo = 0;
     hi = 0;
     nneg = 0;
     E = 0;
+    base = -kFixGuard;
     special = 0.0;
   }
   // -v = ~v + 1: the fast path adds ~v and counts the +1s, added here.
@@ -128,21 +130,40 @@ struct Fix128 {
       hi = (uint64_t)((int64_t)hi >> k);
     }
     E = e;
+    base = e - kFixGuard;
   }
   __device__ __forceinline__ void add(uint64_t u) {
-    const int ef = (int)(u >> 52) & 0x7FF;
-    const int d0 = E - ef;
-    if ((unsigned)d0 <= (unsigned)kFixGuard && ef != 0) {
-      // fast path: a normal value within kFixGuard binades of E. Its significand
-      // shifted into place, in one's complement when negative (the +1 counted
-      // in nneg), is added with one carry chain.
-      const uint64_t m = (u & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
-      const int sh = kFixGuard - d0;  // 0 .. kFixGuard
-      const uint64_t vlo = m << sh;
-      const uint64_t vhi = (m >> 1) >> (63 - sh);  // m >> (64 - sh), 0 when sh = 0
-      const uint64_t sgn = (uint64_t)((int64_t)u >> 63);
-      asm("add.cc.u64 %0, %0, %2;\n\taddc.u64 %1, %1, %3;" : "+l"(lo), "+l"(hi) : "l"(vlo ^ sgn), "l"(vhi ^ sgn));
-      nneg += (uint32_t)sgn & 1u;
+    const uint32_t uh = (uint32_t)(u >> 32), ul = (uint32_t)u;
+    const int ef = (int)((uh >> 20) & 0x7FFu);
+    const int sh = ef - base;  // E - ef binades below E: sh = kFixGuard - (E - ef)
+    if ((unsigned)sh <= (unsigned)kFixGuard && ef != 0) {
+      // fast path: a normal value within kFixGuard binades of E. Its 53-bit
+      // significand m shifted left by sh (< 48) on 32-bit words: m << (sh mod
+      // 32) in three words by funnel shifts, placed one word further up when
+      // sh >= 32, in one's complement when negative (the +1 counted in nneg),
+      // and added with one carry chain.
+      const uint32_t mh = (uh & 0x000FFFFFu) | 0x00100000u;  // m's high 21 bits (implicit bit included)
+      const uint32_t w0 = __funnelshift_l(0u, ul, (unsigned)sh);
+      const uint32_t w1 = __funnelshift_l(ul, mh, (unsigned)sh);
+      const uint32_t w2 = __funnelshift_l(mh, 0u, (unsigned)sh);  // 0 when sh mod 32 = 0
+      const bool up = sh >= 32;
+      const uint32_t s = (uint32_t)((int32_t)uh >> 31);  // all ones for a negative row
+      const uint32_t x0 = (up ? 0u : w0) ^ s;
+      const uint32_t x1 = (up ? w0 : w1) ^ s;
+      const uint32_t x2 = (up ? w1 : w2) ^ s;
+      const uint32_t x3 = (up ? w2 : 0u) ^ s;
+      asm("{\n\t.reg .u32 a0, a1, a2, a3;\n\t"
+          "mov.b64 {a0, a1}, %0;\n\t"
+          "mov.b64 {a2, a3}, %1;\n\t"
+          "add.cc.u32 a0, a0, %2;\n\t"
+          "addc.cc.u32 a1, a1, %3;\n\t"
+          "addc.cc.u32 a2, a2, %4;\n\t"
+          "addc.u32 a3, a3, %5;\n\t"
+          "mov.b64 %0, {a0, a1};\n\t"
+          "mov.b64 %1, {a2, a3};\n\t}"
+          : "+l"(lo), "+l"(hi)
+          : "r"(x0), "r"(x1), "r"(x2), "r"(x3));
+      nneg -= s;
       return;
     }
     fold_neg();
@@ -226,9 +247,22 @@ struct Acc<DT, SUM, MM, true> {
       }
     }
     if (MM) {
-      U m = FpImg<T>::img(v);
-      mn = min(mn, m);
-      mx = max(mx, m);
+      if (F64) {
+        // the image's high word decides unless it ties with an extreme's:
+        // the 64-bit compares run only for a row that may move min or max
+        const uint64_t b = (uint64_t)__double_as_longlong((double)v);
+        const uint32_t s = (uint32_t)((int32_t)(b >> 32) >> 31);
+        const uint32_t ih = (uint32_t)(b >> 32) ^ (s | 0x80000000u);
+        if (ih <= (uint32_t)((uint64_t)mn >> 32) || ih >= (uint32_t)((uint64_t)mx >> 32)) {
+          const U m = (U)(((uint64_t)ih << 32) | ((uint32_t)b ^ s));
+          mn = min(mn, m);
+          mx = max(mx, m);
+        }
+      } else {
+        U m = FpImg<T>::img(v);
+        mn = min(mn, m);
+        mx = max(mx, m);
+      }
     }
   }
   __device__ __forceinline__ void fold_vec(const uint4& r) {
