@@ -87,14 +87,15 @@ template <> struct FpImg<double> {
 // implicit bit included) and exponent field e >= 1 is worth m x 2^(e - 1075),
 // i.e. m shifted left by kFixGuard - (E - e) units. Rows more than kFixGuard
 // binades below E keep their bits above the unit (each loses less than
-// 2^(E - 1075 - kFixGuard)); a row with a larger exponent shifts the sum right
-// (again less than a unit lost). Sums of up to 2^27 rows per thread cannot
-// overflow (|m x 2^kFixGuard| < 2^100). Infinities and NaNs are added in
+// 2^(E - 1075 - kFixGuard), 2^-83 of the largest row); a row with a larger
+// exponent shifts the sum right (again less than a unit lost). Sums of up to
+// 2^43 rows per thread cannot overflow (|m x 2^kFixGuard| < 2^84). A guard of
+// 31 bits keeps the fast path's shift below one word. Infinities and NaNs are added in
 // float64 on the side, so that a column holding one sums to a non-finite
 // value (which one is unspecified, as for the other float paths).
 // GB300 issues few float64 operations per clock (a TwoSum per row held the
 // float64 scan to 0.6 TB/s); this takes only integer operations per row.
-constexpr int kFixGuard = 47;
+constexpr int kFixGuard = 31;
 
 struct Fix128 {
   uint64_t lo, hi;
@@ -138,20 +139,16 @@ struct Fix128 {
     const int sh = ef - base;  // E - ef binades below E: sh = kFixGuard - (E - ef)
     if ((unsigned)sh <= (unsigned)kFixGuard && ef != 0) {
       // fast path: a normal value within kFixGuard binades of E. Its 53-bit
-      // significand m shifted left by sh (< 48) on 32-bit words: m << (sh mod
-      // 32) in three words by funnel shifts, placed one word further up when
-      // sh >= 32, in one's complement when negative (the +1 counted in nneg),
-      // and added with one carry chain.
+      // significand m shifted left by sh (< 32) on 32-bit words (three funnel
+      // shifts), in one's complement when negative (the +1 counted in nneg),
+      // added with one carry chain.
+      static_assert(kFixGuard < 32, "the fast path shifts by less than one word");
       const uint32_t mh = (uh & 0x000FFFFFu) | 0x00100000u;  // m's high 21 bits (implicit bit included)
-      const uint32_t w0 = __funnelshift_l(0u, ul, (unsigned)sh);
-      const uint32_t w1 = __funnelshift_l(ul, mh, (unsigned)sh);
-      const uint32_t w2 = __funnelshift_l(mh, 0u, (unsigned)sh);  // 0 when sh mod 32 = 0
-      const bool up = sh >= 32;
-      const uint32_t s = (uint32_t)((int32_t)uh >> 31);  // all ones for a negative row
-      const uint32_t x0 = (up ? 0u : w0) ^ s;
-      const uint32_t x1 = (up ? w0 : w1) ^ s;
-      const uint32_t x2 = (up ? w1 : w2) ^ s;
-      const uint32_t x3 = (up ? w2 : 0u) ^ s;
+      const uint32_t s = (uint32_t)((int32_t)uh >> 31);      // all ones for a negative row
+      const uint32_t x0 = __funnelshift_l(0u, ul, (unsigned)sh) ^ s;
+      const uint32_t x1 = __funnelshift_l(ul, mh, (unsigned)sh) ^ s;
+      const uint32_t x2 = __funnelshift_l(mh, 0u, (unsigned)sh) ^ s;  // m >> (32 - sh), 0 when sh = 0
+      const uint32_t x3 = s;
       asm("{\n\t.reg .u32 a0, a1, a2, a3;\n\t"
           "mov.b64 {a0, a1}, %0;\n\t"
           "mov.b64 {a2, a3}, %1;\n\t"
